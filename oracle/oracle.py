@@ -1,0 +1,305 @@
+"""ctypes binding of the FP64 CPU oracle (lbm_oracle.cpp).
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, by the smoke check and by the benchmark's CPU
+baseline leg. It never imports the CUDA package and the CUDA package never imports it.
+
+Array conventions (same as the C ABI of the CUDA library, but implemented independently):
+  cell index n = x + nx*(y + ny*z); populations f[i*N + n]; velocities u[a*N + n];
+  inlet velocity uin[a*ny*nz + y + ny*z].
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+FACE_PERIODIC, FACE_WALL, FACE_SLIP, FACE_OPEN = 0, 1, 2, 3
+MASK_FLUID, MASK_SOLID, MASK_INFLOW, MASK_OUTFLOW = 0, 1, 3, 4
+KIND_FLUID, KIND_SOLID, KIND_WALL, KIND_INFLOW, KIND_OUTFLOW = 0, 1, 2, 3, 4
+
+_d = ctypes.c_double
+_i = ctypes.c_int
+_p = ctypes.c_void_p
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        sig = {
+            "orc_create": (_p, [_i, _i, _i, _i, _d, _d]),
+            "orc_destroy": (None, [_p]),
+            "orc_last_error": (ctypes.c_char_p, []),
+            "orc_lattice": (_i, [_i, _p, _p, _p, _p, _p]),
+            "orc_set_faces": (_i, [_p, _p]),
+            "orc_set_geometry": (_i, [_p, _p, _p]),
+            "orc_set_force": (None, [_p, _d, _d, _d]),
+            "orc_set_inflow": (None, [_p, _p]),
+            "orc_set_outflow": (None, [_p, _d]),
+            "orc_set_porosity": (None, [_p, _p]),
+            "orc_set_wall_model": (None, [_p, _i, _d, _d]),
+            "orc_set_storage": (None, [_p, _i]),
+            "orc_init_equilibrium": (None, [_p, _p, _p]),
+            "orc_set_populations": (None, [_p, _p]),
+            "orc_get_populations": (None, [_p, _p]),
+            "orc_get_refbuf": (None, [_p, _p]),
+            "orc_step": (None, [_p, _i]),
+            "orc_moments": (None, [_p, _p, _p]),
+            "orc_reduce": (None, [_p, _p, _p]),
+            "orc_classification": (None, [_p, _p, _p, _p, _p]),
+            "orc_source_map": (None, [_p, _p, _p]),
+            "orc_spalding_yplus": (_d, [_d, _d, _d]),
+            "orc_spalding_dyplus": (_d, [_d, _d, _d]),
+            "orc_solve_uplus_re": (_d, [_d, _d, _d, _p]),
+            "orc_solve_uplus_yplus": (_d, [_d, _d, _d, _p]),
+            "orc_tau_smagorinsky": (_d, [_d, _d, _p, _d]),
+            "orc_feq": (None, [_i, _d, _p, _p]),
+            "orc_bc": (None, [_i, _i, _p, _p, _d]),
+            "orc_wall_state": (_i, [_p, ctypes.c_longlong, _p, _p]),
+            "orc_f16_encode": (ctypes.c_uint16, [_d]),
+            "orc_f16_decode": (_d, [ctypes.c_uint16]),
+            "orc_bf16_encode": (ctypes.c_uint16, [_d]),
+            "orc_bf16_decode": (_d, [ctypes.c_uint16]),
+            "orc_jvp_step": (None, [_p, _p, _p, _p, _p]),
+            "orc_vjp_step": (None, [_p, _p, _p, _p, _p]),
+            "orc_objective_run": (_i, [_p, _i, _i, _i, _i, _p]),
+            "orc_adjoint": (_i, [_p, _p, _p]),
+            "orc_set_threads": (None, [_i]),
+            "orc_get_threads": (_i, []),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def lattice(q):
+    """Velocity set of the oracle: c (q,3) int, w (q,), opp (q,), integer weights W, denominator."""
+    c = np.zeros((q, 3), np.int32)
+    w = np.zeros(q)
+    opp = np.zeros(q, np.int32)
+    W = np.zeros(q, np.int32)
+    den = ctypes.c_int()
+    if lib().orc_lattice(q, _ptr(c), _ptr(w), _ptr(opp), _ptr(W), ctypes.byref(den)):
+        raise ValueError("lattice must be 19 or 27")
+    return c, w, opp, W, den.value
+
+
+def set_threads(n):
+    lib().orc_set_threads(int(n))
+
+
+def get_threads():
+    return lib().orc_get_threads()
+
+
+def spalding_yplus(up, kappa=0.41, E=9.52):
+    return lib().orc_spalding_yplus(up, kappa, E)
+
+
+def spalding_dyplus(up, kappa=0.41, E=9.52):
+    return lib().orc_spalding_dyplus(up, kappa, E)
+
+
+def solve_uplus_re(Re, kappa=0.41, E=9.52):
+    it = ctypes.c_int()
+    u = lib().orc_solve_uplus_re(Re, kappa, E, ctypes.byref(it))
+    return u, it.value
+
+
+def solve_uplus_yplus(yp, kappa=0.41, E=9.52):
+    it = ctypes.c_int()
+    u = lib().orc_solve_uplus_yplus(yp, kappa, E, ctypes.byref(it))
+    return u, it.value
+
+
+def tau_smagorinsky(tau0, cs, Pi, rho):
+    Pi = _f64(np.asarray(Pi).reshape(9))
+    return lib().orc_tau_smagorinsky(tau0, cs, _ptr(Pi), rho)
+
+
+def feq(q, rho, u):
+    u = _f64(u)
+    out = np.zeros(q)
+    lib().orc_feq(q, rho, _ptr(u), _ptr(out))
+    return out
+
+
+def bc(q, kind, f, ub=(0.0, 0.0, 0.0), rho_out=1.0):
+    f = _f64(f).copy()
+    ub = _f64(ub)
+    lib().orc_bc(q, kind, _ptr(f), _ptr(ub), rho_out)
+    return f
+
+
+def f16_encode(x):
+    return lib().orc_f16_encode(float(x))
+
+
+def f16_decode(b):
+    return lib().orc_f16_decode(int(b))
+
+
+def bf16_encode(x):
+    return lib().orc_bf16_encode(float(x))
+
+
+def bf16_decode(b):
+    return lib().orc_bf16_decode(int(b))
+
+
+class Oracle:
+    """One FP64 lattice: populations, geometry and boundary settings."""
+
+    def __init__(self, q, nx, ny, nz, tau, cs=0.0):
+        self.q, self.nx, self.ny, self.nz = q, nx, ny, nz
+        self.N = nx * ny * nz
+        self.h = lib().orc_create(q, nx, ny, nz, tau, cs)
+        if not self.h:
+            raise ValueError(lib().orc_last_error().decode())
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().orc_destroy(self.h)
+            self.h = None
+
+    def _chk(self, rc):
+        if rc:
+            raise ValueError(lib().orc_last_error().decode())
+
+    def set_faces(self, kinds):
+        k = np.ascontiguousarray(kinds, dtype=np.int32)
+        assert k.size == 6
+        self._chk(lib().orc_set_faces(self.h, _ptr(k)))
+
+    def set_geometry(self, mask, ywall=None):
+        m = np.ascontiguousarray(mask, dtype=np.uint8).reshape(-1)
+        assert m.size == self.N
+        y = _f64(None if ywall is None else np.asarray(ywall).reshape(-1))
+        self._chk(lib().orc_set_geometry(self.h, _ptr(m), _ptr(y)))
+
+    def set_force(self, fx, fy, fz):
+        lib().orc_set_force(self.h, fx, fy, fz)
+
+    def set_inflow(self, uin):
+        u = _f64(np.asarray(uin).reshape(-1))
+        assert u.size == 3 * self.ny * self.nz
+        lib().orc_set_inflow(self.h, _ptr(u))
+
+    def set_outflow(self, rho):
+        lib().orc_set_outflow(self.h, rho)
+
+    def set_porosity(self, gamma):
+        g = _f64(None if gamma is None else np.asarray(gamma).reshape(-1))
+        lib().orc_set_porosity(self.h, _ptr(g))
+
+    def set_wall_model(self, on=True, kappa=0.41, E=9.52):
+        lib().orc_set_wall_model(self.h, int(on), kappa, E)
+
+    def set_storage(self, mode):
+        lib().orc_set_storage(self.h, int(mode))
+
+    def init_equilibrium(self, rho, u):
+        r = _f64(np.asarray(rho).reshape(-1))
+        uu = _f64(np.asarray(u).reshape(-1))
+        lib().orc_init_equilibrium(self.h, _ptr(r), _ptr(uu))
+
+    def set_populations(self, f):
+        f = _f64(np.asarray(f).reshape(-1))
+        lib().orc_set_populations(self.h, _ptr(f))
+
+    def populations(self):
+        f = np.zeros(self.q * self.N)
+        lib().orc_get_populations(self.h, _ptr(f))
+        return f.reshape(self.q, self.N)
+
+    def refbuf(self):
+        u = np.zeros(3 * self.N)
+        lib().orc_get_refbuf(self.h, _ptr(u))
+        return u.reshape(self.N, 3)
+
+    def step(self, n=1):
+        lib().orc_step(self.h, int(n))
+
+    def moments(self):
+        rho = np.zeros(self.N)
+        u = np.zeros(3 * self.N)
+        lib().orc_moments(self.h, _ptr(rho), _ptr(u))
+        return rho, u.reshape(3, self.N)
+
+    def reduce(self):
+        m = np.zeros(1)
+        p = np.zeros(3)
+        lib().orc_reduce(self.h, _ptr(m), _ptr(p))
+        return m[0], p
+
+    def classification(self):
+        kind = np.zeros(self.N, np.uint8)
+        isref = np.zeros(self.N, np.uint8)
+        nsum = np.zeros(3 * self.N, np.int32)
+        ref = np.zeros(self.N, np.int64)
+        lib().orc_classification(self.h, _ptr(kind), _ptr(isref), _ptr(nsum), _ptr(ref))
+        return kind, isref, nsum.reshape(self.N, 3), ref
+
+    def boundary_list(self):
+        """Sorted cell indices handled by the boundary-cell pass: WALL, INFLOW, OUTFLOW or reference
+        cells; and for each entry the list position of its reference cell (-1 if none)."""
+        kind, isref, _, ref = self.classification()
+        sel = (kind == KIND_WALL) | (kind == KIND_INFLOW) | (kind == KIND_OUTFLOW) | (isref == 1)
+        cells = np.nonzero(sel)[0].astype(np.int64)
+        pos = {int(c): k for k, c in enumerate(cells)}
+        refpos = np.array([pos[int(ref[c])] if ref[c] >= 0 else -1 for c in cells], dtype=np.int64)
+        return cells, refpos
+
+    def source_map(self):
+        d = np.zeros(self.q * self.N, np.int32)
+        c = np.zeros(self.q * self.N, np.int64)
+        lib().orc_source_map(self.h, _ptr(d), _ptr(c))
+        return d.reshape(self.q, self.N), c.reshape(self.q, self.N)
+
+    def wall_state(self, n):
+        uB = np.zeros(3)
+        d = np.zeros(1)
+        self._chk(lib().orc_wall_state(self.h, int(n), _ptr(uB), _ptr(d)))
+        return uB, d[0]
+
+    def jvp_step(self, vf, vg=None, vu=None):
+        vf = _f64(np.asarray(vf).reshape(-1))
+        vg = _f64(None if vg is None else np.asarray(vg).reshape(-1))
+        vu = _f64(None if vu is None else np.asarray(vu).reshape(-1))
+        out = np.zeros(self.q * self.N)
+        lib().orc_jvp_step(self.h, _ptr(vf), _ptr(vg), _ptr(vu), _ptr(out))
+        return out.reshape(self.q, self.N)
+
+    def vjp_step(self, w):
+        w = _f64(np.asarray(w).reshape(-1))
+        of = np.zeros(self.q * self.N)
+        og = np.zeros(self.N)
+        ou = np.zeros(3 * self.ny * self.nz)
+        lib().orc_vjp_step(self.h, _ptr(w), _ptr(of), _ptr(og), _ptr(ou))
+        return of.reshape(self.q, self.N), og, ou
+
+    def objective_run(self, T, W, xa, xb):
+        J = np.zeros(1)
+        self._chk(lib().orc_objective_run(self.h, int(T), int(W), int(xa), int(xb), _ptr(J)))
+        return J[0]
+
+    def adjoint(self):
+        g = np.zeros(self.N)
+        u = np.zeros(3 * self.ny * self.nz)
+        self._chk(lib().orc_adjoint(self.h, _ptr(g), _ptr(u)))
+        return g, u.reshape(3, self.ny * self.nz)
