@@ -1,0 +1,169 @@
+/* GB300-native wall-modelled lattice Boltzmann LES: C ABI of liblbm.so.
+ *
+ * The library advances a lattice Boltzmann (LB) flow on one CUDA device with one fused
+ * collide-and-stream kernel pass per time step. Method (Kummerländer et al., "Large-Scale
+ * Simulations of Turbulent Flows using Lattice Boltzmann Methods on Heterogeneous High Performance
+ * Computers"):
+ *   - homogenised LB update, Eq. (hlbm): f_i(x + c_i, t + 1) = f_i^eq(rho, u_hat)
+ *     + (1 - 1/tau_eff) f~_i^(1), read for BGK as f~^(1) = f - f^eq(rho, u) (Sec. 2.2);
+ *   - homogenised velocity, Eq. (convexVelocity): u_hat = gamma u + (1 - gamma) u^B, with the
+ *     per-cell porosity gamma = 1 - d (1 = fluid);
+ *   - Smagorinsky effective relaxation time, Eq. (tauEff) with Eqs. (sgsStress),(turbVisc):
+ *     tau_eff = (tau0 + sqrt(tau0^2 + 18 sqrt(2) C_S^2 |Pi^neq| / rho)) / 2;
+ *   - Spalding wall function, Eq. (spaldingfunct), on cells next to solids (Sec. 2.2.1): solid
+ *     velocity u^B from the wall law and the sigma = 0 finite-difference non-equilibrium part;
+ *   - regularised velocity inlet (Sec. 2.2.2), fixed-pressure outlet and full-slip faces (Sec. 3.2),
+ *     half-way bounce-back on solid cells;
+ *   - body force through the exact-difference shift u_hat += F/rho.
+ *
+ * Conventions.
+ *   Cell index n = x + nx*(y + ny*z), N = nx*ny*nz. Populations i = 0..q-1 in the order
+ *   D3Q19: 0 rest; 1..9 = (1,0,0),(0,1,0),(0,0,1),(1,1,0),(1,-1,0),(1,0,1),(1,0,-1),(0,1,1),(0,1,-1);
+ *          10..18 their opposites in the same order.
+ *   D3Q27: 0 rest; 1..13 = the nine D3Q19 speeds followed by (1,1,1),(1,1,-1),(1,-1,1),(1,-1,-1);
+ *          14..26 their opposites.
+ *   Population arrays f[i*N + n]; velocity arrays u[a*N + n] (a = 0,1,2 for x,y,z); inlet velocity
+ *   uin[a*ny*nz + y + ny*z]. Lattice units: dx = dt = 1, cs^2 = 1/3, nu = (tau - 1/2)/3.
+ *   Faces in the order x-, x+, y-, y+, z-, z+.
+ *
+ * Memory. The context owns every device buffer it allocates (cudaMalloc on the current device at
+ * lbm_create) and frees them in lbm_destroy. Caller buffers are never retained after a call returns.
+ * Array arguments may be host or device pointers (detected with cudaPointerGetAttributes); a call
+ * that reads or writes host memory synchronises the context's stream before it returns, a call on
+ * device memory is ordered on that stream.
+ *
+ * Errors. Every int-returning call returns LBM_OK or an error code and leaves a message for
+ * lbm_last_error() (thread-local). Invalid sizes, codes or pointers give LBM_EINVAL and change
+ * nothing. Device-side problems (a non-finite density or momentum seen by a step, an invalid mask
+ * code in device memory) set a sticky status word on the device; it is read back by synchronising
+ * calls (lbm_sync, lbm_moments, lbm_reduce, ...) which then return LBM_ENAN / LBM_EINVAL.
+ */
+#ifndef LBM_H_
+#define LBM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx;
+
+enum { LBM_D3Q19 = 19, LBM_D3Q27 = 27 };
+/* Population storage. Arithmetic is FP32 for LBM_F32/F16/BF16 and FP64 for LBM_F64. Every form
+ * stores the deviation f_i - w_i from the rest-state weights; LBM_F16/LBM_BF16 round it to
+ * nearest-even on each store. */
+enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16 = 2, LBM_BF16 = 3 };
+enum { LBM_OK = 0, LBM_EINVAL = 1, LBM_ENOMEM = 2, LBM_ECUDA = 3, LBM_ENAN = 4, LBM_ETIMEOUT = 5, LBM_ESTATE = 6 };
+/* Mask codes accepted by lbm_set_geometry. */
+enum { LBM_CELL_FLUID = 0, LBM_CELL_SOLID = 1, LBM_CELL_INFLOW = 3, LBM_CELL_OUTFLOW = 4 };
+/* Classified kinds (low 3 bits of the type byte, see lbm_debug_dump). WALL = non-solid cell with a
+ * solid neighbour (or a neighbour beyond a bounce-back face); precedence
+ * SOLID > INFLOW > OUTFLOW > WALL > FLUID. */
+enum { LBM_KIND_FLUID = 0, LBM_KIND_SOLID = 1, LBM_KIND_WALL = 2, LBM_KIND_INFLOW = 3, LBM_KIND_OUTFLOW = 4 };
+/* Face kinds. PERIODIC faces come in pairs. WALL: half-way bounce-back, counts as a solid layer
+ * beyond the face. SLIP: specular reflection (Sec. 3.2 full slip). OPEN: populations entering
+ * through the face are the unknowns of the INFLOW/OUTFLOW cells on it. */
+enum { LBM_FACE_PERIODIC = 0, LBM_FACE_WALL = 1, LBM_FACE_SLIP = 2, LBM_FACE_OPEN = 3 };
+/* dtype codes of host/device array arguments of the *_ex calls. */
+enum { LBM_DTYPE_F32 = 1, LBM_DTYPE_F64 = 0 };
+
+/* Create a lattice of nx*ny*nz cells with molecular relaxation time tau (> 1/2) and Smagorinsky
+ * constant c_smag >= 0 (C_S of Eq. turbVisc; 0 gives plain BGK). Storage LBM_F32, all faces
+ * periodic, all cells fluid at rest (f = w). Returns NULL on error (lbm_last_error). */
+lbm_ctx* lbm_create(int lattice, int nx, int ny, int nz, double tau, double c_smag);
+void lbm_destroy(lbm_ctx* ctx);
+const char* lbm_last_error(void);
+
+/* Population storage form; reallocates and resets the state to rest. */
+int lbm_set_precision(lbm_ctx* ctx, int storage);
+/* Face kinds: px/py/pz != 0 makes both faces of that axis periodic, 0 makes them bounce-back. */
+int lbm_set_periodic(lbm_ctx* ctx, int px, int py, int pz);
+/* Face kinds, six entries in the order x-, x+, y-, y+, z-, z+ (periodic ones must pair). */
+int lbm_set_faces(lbm_ctx* ctx, const int kinds[6]);
+/* Geometry: mask (N bytes, codes LBM_CELL_*), wall_dist (N floats, distance of a WALL cell centre
+ * from the wall, nullable = 0.5). Runs the classification and builds the boundary-cell list
+ * (WALL, INFLOW, OUTFLOW and wall-model reference cells, ascending cell index). Resets to rest. */
+int lbm_set_geometry(lbm_ctx* ctx, const uint8_t* mask, const float* wall_dist);
+/* Body force per unit volume (lattice units). */
+int lbm_set_force(lbm_ctx* ctx, double fx, double fy, double fz);
+/* Inlet velocity of INFLOW cells, 3*ny*nz values (inward normal +x). */
+int lbm_set_inflow(lbm_ctx* ctx, const float* u_in);
+int lbm_set_inflow_ex(lbm_ctx* ctx, const void* u_in, int dtype);
+/* Outlet density of OUTFLOW cells (inward normal -x). */
+int lbm_set_outflow(lbm_ctx* ctx, double rho_out);
+/* Per-cell porosity gamma (N values in [0,1], 1 = fluid); NULL removes it. */
+int lbm_set_porosity(lbm_ctx* ctx, const float* gamma);
+int lbm_set_porosity_ex(lbm_ctx* ctx, const void* gamma, int dtype);
+/* Spalding wall function on WALL cells with von Karman constant kappa and wall constant E
+ * (kappa <= 0 switches it off: WALL cells then collide like fluid cells with bounce-back). */
+int lbm_set_wall_model(lbm_ctx* ctx, double kappa, double E);
+/* Equilibrium state f_i = f_i^eq(rho, u) (rho: N values, u: 3*N values); step counter to 0; the
+ * wall-model reference buffer is filled with this state's velocity. */
+int lbm_init_equilibrium(lbm_ctx* ctx, const float* rho, const float* u);
+int lbm_init_equilibrium_ex(lbm_ctx* ctx, const void* rho, const void* u, int dtype);
+
+/* Advance n time steps (stream-ordered, asynchronous). Returns the sticky status seen so far. */
+int lbm_step(lbm_ctx* ctx, int n);
+/* Same (n >= 1), timed with CUDA events on the context stream around each launch: adds the device
+ * time of the interior-cell kernels to ms[0], of the boundary-list kernels to ms[1], and the time
+ * from the first launch's start to the last launch's end to ms[2]. Synchronises. */
+int lbm_step_timed(lbm_ctx* ctx, int n, double ms[3]);
+/* Wait for the context stream; returns LBM_ENAN if a step has seen a non-finite density. */
+int lbm_sync(lbm_ctx* ctx);
+
+/* Macroscopic fields of the current (pre-collision) state: rho (N), u (3*N) with
+ * u = j/rho + F/(2 rho); INFLOW/OUTFLOW cells report their reconstructed state; SOLID cells 0. */
+int lbm_moments(lbm_ctx* ctx, float* rho, float* u);
+int lbm_moments_ex(lbm_ctx* ctx, void* rho, void* u, int dtype);
+/* FP64 reductions over non-solid cells: mass = sum rho, mom = sum rho u. */
+int lbm_reduce(lbm_ctx* ctx, double* mass, double mom[3]);
+/* Populations f_i (not deviations) of the current state, q*N values. */
+int lbm_get_populations(lbm_ctx* ctx, void* f, int dtype);
+/* Replace the state by the given populations (q*N values, natural layout); refreshes the
+ * wall-model reference buffer from it. */
+int lbm_set_populations(lbm_ctx* ctx, const void* f, int dtype);
+
+/* Discrete adjoint (differentiation extension; the paper cites OpenLB as differentiable, Sec. 1).
+ * Objective: J = (1/W) sum over the last W of T steps of cs^2 (<rho>_{x=xa} - <rho>_{x=xb}),
+ * plane means over non-solid cells of the state after each step.
+ * lbm_objective_forward runs T steps from the current state, keeping a copy of the state every
+ * ckpt steps (ckpt even), and returns J. lbm_objective_backward then recomputes each segment from
+ * its checkpoint into a ring of states and sweeps the adjoint kernel backwards, accumulating
+ * dJ/dgamma (N values, FP64) and dJ/du_in (3*ny*nz values, FP64); either may be NULL. The wall
+ * model is not differentiated (LBM_ESTATE if it is on). After backward the state is the one at the
+ * end of the forward run. */
+int lbm_objective_forward(lbm_ctx* ctx, int T, int W, int xa, int xb, int ckpt, double* J);
+int lbm_objective_backward(lbm_ctx* ctx, double* dJ_dgamma, double* dJ_duin);
+/* One reverse step at the current state: lam_out = (dS_{t+1}/dS_t)^T lam_in (q*N values each,
+ * natural layout, dtype LBM_DTYPE_*), and adds (dS_{t+1}/dgamma)^T lam_in to dgamma (N, FP64) and
+ * (dS_{t+1}/du_in)^T lam_in to duin (3*ny*nz, FP64); both nullable. */
+int lbm_adjoint_step(lbm_ctx* ctx, const void* lam_in, void* lam_out, int dtype, double* dgamma, double* duin);
+/* Device time of the adjoint kernels of the last backward: ms[0] recompute, ms[1] reverse. */
+int lbm_adjoint_timing(lbm_ctx* ctx, double ms[2]);
+
+/* Checkpoint of the whole state (populations, step counter, reference buffer). With buf == NULL,
+ * *len receives the size needed. lbm_load restores a buffer written by lbm_save of a context with
+ * the same lattice, size, storage and geometry. */
+int lbm_save(lbm_ctx* ctx, void* buf, size_t* len);
+int lbm_load(lbm_ctx* ctx, const void* buf, size_t len);
+
+/* Stream for all work of the context (e.g. torch.cuda.current_stream().cuda_stream); 0 = default. */
+int lbm_set_stream(lbm_ctx* ctx, void* cuda_stream);
+
+/* Counters: out[0] N, [1] boundary-list length, [2] WALL, [3] reference cells, [4] INFLOW,
+ * [5] OUTFLOW, [6] SOLID, [7] steps done, [8] storage, [9] lattice q. */
+int lbm_info(lbm_ctx* ctx, int64_t out[10]);
+/* Integer maps for bit-exact tests: which = 0 type byte per cell (N; bits 0-2 kind, bit 3
+ * reference cell, bit 4 a source position is solid or outside, bit 5 boundary list);
+ * 1 boundary-list cells; 2 list position of each entry's reference cell (-1 none);
+ * 3 integer wall-normal sums v of each entry (3 per entry, sum of W_i c_i over solid neighbours,
+ * W_i = 36 w_i for D3Q19 and 216 w_i for D3Q27); 4 source population j and 5 source cell m of each
+ * (i, n) (q*N each, i-major; f_i(n, t+1) = f*_j(m, t); -1 for solid cells). */
+int lbm_debug_dump(lbm_ctx* ctx, int which, int64_t* out, size_t count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H_ */

@@ -1,0 +1,974 @@
+// Host side of the C ABI declared in include/lbm.h: context lifetime, argument validation, device
+// memory, geometry set-up, step orchestration, state access, checkpoints and the adjoint driver.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_adjoint.cuh"
+#include "lbm_device.cuh"
+#include "lbm_ops.h"
+
+using namespace lbm;
+
+namespace {
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define CK(call)                                                                               \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess) return fail(LBM_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));    \
+  } while (0)
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t n = 0;
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  // (re)allocate to at least `bytes`; contents undefined
+  cudaError_t ensure(size_t bytes) {
+    if (bytes <= n && p) return cudaSuccess;
+    release();
+    if (bytes == 0) return cudaSuccess;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e == cudaSuccess) n = bytes;
+    return e;
+  }
+};
+
+constexpr int RED_BLOCKS = 1024;
+constexpr uint32_t SAVE_MAGIC = 0x4C424D31u;  // "LBM1"
+
+struct SaveHeader {
+  uint32_t magic, q, storage, pad;
+  int64_t nx, ny, nz, n_list, t;
+  uint64_t fbytes, rbytes;
+};
+}  // namespace
+
+struct lbm_ctx {
+  int q = 19, nx = 0, ny = 0, nz = 0;
+  long long N = 0, stride = 0;
+  int storage = LBM_F32;
+  double tau0 = 0.6, cs = 0.0;
+  int face[6] = {0, 0, 0, 0, 0, 0};
+  double force[3] = {0, 0, 0};
+  double rho_out = 1.0;
+  bool wm = false;
+  double kappa = 0.41, E = 9.52;
+  int device = 0;
+  cudaStream_t stream = 0;
+  const Ops* ops = nullptr;
+  long long t = 0;
+  unsigned status_seen = 0;
+  // device buffers
+  DevBuf f, type, mask, wdist, gamma, uin, lcell, nsum, wref, wnrm, wyw, ref0, ref1, status, red, redout, stage;
+  bool has_gamma = false, has_wdist = false;
+  int n_list = 0;
+  long long counts[8] = {0};  // wall, ref, inflow, outflow, solid
+  std::vector<double> uin_host;
+  std::vector<uint8_t> type_host;
+  unsigned* status_h = nullptr;
+  double* red_h = nullptr;
+  // adjoint state
+  DevBuf lamA, lamB, dgam, duin;
+  std::vector<DevBuf> ckpts, ring;
+  int adj_T = 0, adj_W = 0, adj_xa = 0, adj_xb = 0, adj_ck = 0;
+  double adj_wa = 0, adj_wb = 0;
+  long long adj_t0 = -1;
+  double adj_ms[2] = {0, 0};
+
+  ~lbm_ctx() {
+    DevBuf* all[] = {&f, &type, &mask, &wdist, &gamma, &uin, &lcell, &nsum, &wref, &wnrm, &wyw, &ref0, &ref1, &status, &red,
+                     &redout, &stage, &lamA, &lamB, &dgam, &duin};
+    for (DevBuf* b : all) b->release();
+    for (auto& b : ckpts) b.release();
+    for (auto& b : ring) b.release();
+    if (status_h) cudaFreeHost(status_h);
+    if (red_h) cudaFreeHost(red_h);
+  }
+};
+
+namespace {
+
+const Ops* pick_ops(int q, int storage) {
+  switch (storage) {
+    case LBM_F64: return ops_f64(q);
+    case LBM_F32: return ops_f32(q);
+    case LBM_F16: return ops_f16(q);
+    case LBM_BF16: return ops_bf16(q);
+  }
+  return nullptr;
+}
+
+GeoArgs geo_args(const lbm_ctx* c) {
+  GeoArgs g{};
+  g.nx = c->nx; g.ny = c->ny; g.nz = c->nz;
+  g.nxy = (long long)c->nx * c->ny;
+  g.N = c->N;
+  for (int i = 0; i < 6; ++i) g.face[i] = c->face[i];
+  g.q = c->q;
+  return g;
+}
+
+Args make_args(const lbm_ctx* c) {
+  Args a{};
+  a.f = c->f.p;
+  a.stride = c->stride;
+  a.type = static_cast<const uint8_t*>(c->type.p);
+  a.gamma = c->has_gamma ? c->gamma.p : nullptr;
+  a.nx = c->nx; a.ny = c->ny; a.nz = c->nz;
+  a.nxy = (long long)c->nx * c->ny;
+  a.N = c->N;
+  for (int i = 0; i < 6; ++i) a.face[i] = c->face[i];
+  a.tau0 = c->tau0;
+  a.smag = 18.0 * std::sqrt(2.0) * c->cs * c->cs;
+  a.cs2smag = c->cs * c->cs;
+  a.fx = c->force[0]; a.fy = c->force[1]; a.fz = c->force[2];
+  a.status = static_cast<unsigned*>(c->status.p);
+  a.lcell = static_cast<const long long*>(c->lcell.p);
+  a.n_list = c->n_list;
+  a.wnrm = c->wnrm.p;
+  a.wyw = c->wyw.p;
+  a.wref = static_cast<const int*>(c->wref.p);
+  // step t reads the reference velocities written in step t-1 and writes its own
+  a.ref_rd = (c->t & 1) ? c->ref0.p : c->ref1.p;
+  a.ref_wr = (c->t & 1) ? c->ref1.p : c->ref0.p;
+  a.uin = c->uin.p;
+  a.rho_out = c->rho_out;
+  a.wm = c->wm ? 1 : 0;
+  a.kappa = c->kappa;
+  a.E = c->E;
+  return a;
+}
+
+bool is_device_ptr(const void* p, int device) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == device;
+}
+
+// Pointer check: host (any kind) is fine; device pointers must be on the context's device.
+int check_ptr(const lbm_ctx* c, const void* p, const char* what) {
+  if (!p) return fail(LBM_EINVAL, "%s: null pointer", what);
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return LBM_OK;
+  }
+  if ((at.type == cudaMemoryTypeDevice) && at.device != c->device)
+    return fail(LBM_EINVAL, "%s: device pointer on device %d, context on device %d", what, at.device, c->device);
+  return LBM_OK;
+}
+
+size_t dsize(int dtype) { return dtype == LBM_DTYPE_F64 ? 8 : 4; }
+
+int read_status(lbm_ctx* c) {
+  CK(cudaMemcpyAsync(c->status_h, c->status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->status_seen |= *c->status_h;
+  return LBM_OK;
+}
+
+int status_code(lbm_ctx* c) {
+  if (c->status_seen & ST_NAN) return fail(LBM_ENAN, "non-finite density or momentum seen by a step");
+  return LBM_OK;
+}
+
+// Copy `bytes` from a host or device pointer into device buffer dst (stream-ordered).
+int upload(lbm_ctx* c, void* dst, const void* src, size_t bytes) {
+  CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, c->stream));
+  if (!is_device_ptr(src, c->device)) CK(cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+
+int alloc_state(lbm_ctx* c) {
+  c->stride = (c->N + 127) / 128 * 128;
+  CK(c->f.ensure((size_t)c->q * c->stride * c->ops->elem));
+  CK(cudaMemsetAsync(c->f.p, 0, (size_t)c->q * c->stride * c->ops->elem, c->stream));
+  return LBM_OK;
+}
+
+// Compute-type inlet velocity buffer from the host copy.
+int upload_uin(lbm_ctx* c) {
+  const size_t n = 3 * (size_t)c->ny * c->nz;
+  CK(c->uin.ensure(n * c->ops->celem));
+  if (c->ops->celem == 8) {
+    CK(cudaMemcpyAsync(c->uin.p, c->uin_host.data(), n * 8, cudaMemcpyHostToDevice, c->stream));
+  } else {
+    std::vector<float> tmp(n);
+    for (size_t i = 0; i < n; ++i) tmp[i] = float(c->uin_host[i]);
+    CK(cudaMemcpyAsync(c->uin.p, tmp.data(), n * 4, cudaMemcpyHostToDevice, c->stream));
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+
+// Classification and boundary list from the device mask; list auxiliary data in compute type.
+int build_geometry(lbm_ctx* c) {
+  const GeoArgs g = geo_args(c);
+  cudaStream_t s = c->stream;
+  CK(cudaMemsetAsync(c->status.p, 0, sizeof(unsigned), s));
+  geo_classify(g, static_cast<const uint8_t*>(c->mask.p), static_cast<uint8_t*>(c->type.p), static_cast<unsigned*>(c->status.p), s);
+  geo_mark_ref(g, static_cast<uint8_t*>(c->type.p), s);
+  const int nb = geo_count_blocks(g);
+  DevBuf counts;
+  CK(counts.ensure((size_t)nb * sizeof(int)));
+  geo_list_count(g, static_cast<uint8_t*>(c->type.p), static_cast<int*>(counts.p), s);
+  std::vector<int> hc(nb);
+  CK(cudaMemcpyAsync(hc.data(), counts.p, nb * sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(c->status_h, c->status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (*c->status_h & ST_BADMASK) {
+    counts.release();
+    return fail(LBM_EINVAL, "mask holds codes other than 0 (fluid), 1 (solid), 3 (inflow), 4 (outflow)");
+  }
+  long long total = 0;
+  for (int b = 0; b < nb; ++b) {
+    int v = hc[b];
+    hc[b] = int(total);
+    total += v;
+  }
+  if (total > 0x7fffffffLL) {
+    counts.release();
+    return fail(LBM_EINVAL, "boundary list too long (%lld entries)", total);
+  }
+  c->n_list = int(total);
+  CK(cudaMemcpyAsync(counts.p, hc.data(), nb * sizeof(int), cudaMemcpyHostToDevice, s));
+  const size_t nl = std::max<size_t>(1, (size_t)c->n_list);
+  CK(c->lcell.ensure(nl * sizeof(long long)));
+  geo_list_write(g, static_cast<const uint8_t*>(c->type.p), static_cast<const int*>(counts.p), static_cast<long long*>(c->lcell.p), s);
+  CK(c->nsum.ensure(nl * 3 * sizeof(int)));
+  CK(c->wref.ensure(nl * sizeof(int)));
+  geo_list_meta(g, static_cast<const uint8_t*>(c->type.p), static_cast<const long long*>(c->lcell.p), c->n_list,
+                static_cast<int*>(c->nsum.p), static_cast<int*>(c->wref.p), s);
+  CK(c->wnrm.ensure(nl * 3 * c->ops->celem));
+  CK(c->wyw.ensure(nl * c->ops->celem));
+  CK(c->ref0.ensure(nl * 3 * c->ops->celem));
+  CK(c->ref1.ensure(nl * 3 * c->ops->celem));
+  CK(cudaMemsetAsync(c->ref0.p, 0, nl * 3 * c->ops->celem, s));
+  CK(cudaMemsetAsync(c->ref1.p, 0, nl * 3 * c->ops->celem, s));
+  Args a = make_args(c);
+  c->ops->list_aux(a, static_cast<const int*>(c->nsum.p), c->has_wdist ? static_cast<const float*>(c->wdist.p) : nullptr,
+                   c->wnrm.p, c->wyw.p, s);
+  CK(cudaGetLastError());
+  // host copy of the type bytes and counters
+  c->type_host.resize(c->N);
+  CK(cudaMemcpyAsync(c->type_host.data(), c->type.p, c->N, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  counts.release();
+  long long nw = 0, nr = 0, ni = 0, no = 0, ns = 0;
+  for (long long n = 0; n < c->N; ++n) {
+    const uint8_t t = c->type_host[n];
+    const int k = t & T_KIND;
+    nw += k == K_WALL; ni += k == K_INFLOW; no += k == K_OUTFLOW; ns += k == K_SOLID;
+    nr += (t & T_REF) != 0;
+  }
+  c->counts[0] = nw; c->counts[1] = nr; c->counts[2] = ni; c->counts[3] = no; c->counts[4] = ns;
+  return LBM_OK;
+}
+
+// State to rest (f = w), step counter 0, reference buffers from that state.
+int reset_state(lbm_ctx* c) {
+  CK(cudaMemsetAsync(c->f.p, 0, (size_t)c->q * c->stride * c->ops->elem, c->stream));
+  c->t = 0;
+  c->adj_t0 = -1;
+  const size_t nl = std::max<size_t>(1, (size_t)c->n_list);
+  CK(cudaMemsetAsync(c->ref0.p, 0, nl * 3 * c->ops->celem, c->stream));
+  CK(cudaMemsetAsync(c->ref1.p, 0, nl * 3 * c->ops->celem, c->stream));
+  return LBM_OK;
+}
+
+int fill_refs(lbm_ctx* c) {
+  Args a = make_args(c);
+  const int sw = int(c->t & 1);
+  c->ops->ref_fill(a, sw, c->ref0.p, c->stream);
+  c->ops->ref_fill(a, sw, c->ref1.p, c->stream);
+  CK(cudaGetLastError());
+  return LBM_OK;
+}
+
+// Convert a caller array (dtype, host or device) into a device buffer of the compute type.
+int upload_compute(lbm_ctx* c, DevBuf& dst, const void* src, int dtype, size_t count) {
+  const size_t bytes = count * dsize(dtype);
+  CK(dst.ensure(count * c->ops->celem));
+  CK(c->stage.ensure(bytes));
+  CK(cudaMemcpyAsync(c->stage.p, src, bytes, cudaMemcpyDefault, c->stream));
+  c->ops->convert(c->stage.p, dtype, dst.p, c->ops->celem == 8 ? LBM_DTYPE_F64 : LBM_DTYPE_F32, (long long)count, c->stream);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+
+int valid_dtype(int dtype) { return dtype == LBM_DTYPE_F32 || dtype == LBM_DTYPE_F64; }
+
+}  // namespace
+
+// =================================================================================================
+extern "C" {
+
+const char* lbm_last_error(void) { return g_err.c_str(); }
+
+lbm_ctx* lbm_create(int lattice, int nx, int ny, int nz, double tau, double c_smag) {
+  if (lattice != 19 && lattice != 27) { fail(LBM_EINVAL, "lattice must be 19 or 27"); return nullptr; }
+  if (nx < 1 || ny < 1 || nz < 1) { fail(LBM_EINVAL, "grid sizes must be >= 1"); return nullptr; }
+  if ((long long)nx * ny > 0x7fffffffLL || nz > 65535 || ny > 65535) {
+    fail(LBM_EINVAL, "grid too large for the launch shape (nx*ny < 2^31, ny <= 65535, nz <= 65535)");
+    return nullptr;
+  }
+  if (!(tau > 0.5) || !std::isfinite(tau)) { fail(LBM_EINVAL, "tau must be > 1/2"); return nullptr; }
+  if (!(c_smag >= 0.0) || !std::isfinite(c_smag)) { fail(LBM_EINVAL, "c_smag must be >= 0"); return nullptr; }
+  lbm_ctx* c = new lbm_ctx();
+  c->q = lattice; c->nx = nx; c->ny = ny; c->nz = nz;
+  c->N = (long long)nx * ny * nz;
+  c->tau0 = tau; c->cs = c_smag;
+  c->ops = pick_ops(lattice, LBM_F32);
+  c->uin_host.assign(3 * (size_t)ny * nz, 0.0);
+  auto bail = [&](const char* what, cudaError_t e) {
+    fail(e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+    delete c;
+    return nullptr;
+  };
+  cudaError_t e;
+  if ((e = cudaGetDevice(&c->device)) != cudaSuccess) return bail("cudaGetDevice", e);
+  if ((e = cudaMallocHost(&c->status_h, sizeof(unsigned))) != cudaSuccess) return bail("cudaMallocHost", e);
+  if ((e = cudaMallocHost(&c->red_h, 4 * sizeof(double))) != cudaSuccess) return bail("cudaMallocHost", e);
+  if ((e = c->status.ensure(sizeof(unsigned))) != cudaSuccess) return bail("status", e);
+  if ((e = c->red.ensure(RED_BLOCKS * 4 * sizeof(double))) != cudaSuccess) return bail("reduction", e);
+  if ((e = c->redout.ensure(4 * sizeof(double))) != cudaSuccess) return bail("reduction", e);
+  if ((e = c->type.ensure(((size_t)c->N + 3) / 4 * 4)) != cudaSuccess) return bail("type", e);
+  if ((e = c->mask.ensure((size_t)c->N)) != cudaSuccess) return bail("mask", e);
+  cudaMemset(c->mask.p, 0, c->N);
+  cudaMemset(c->type.p, 0, ((size_t)c->N + 3) / 4 * 4);
+  cudaMemset(c->status.p, 0, sizeof(unsigned));
+  if (alloc_state(c) != LBM_OK) { delete c; return nullptr; }
+  if (upload_uin(c) != LBM_OK || build_geometry(c) != LBM_OK || reset_state(c) != LBM_OK) { delete c; return nullptr; }
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) { fail(LBM_ECUDA, "create: %s", cudaGetErrorString(cudaGetLastError())); delete c; return nullptr; }
+  return c;
+}
+
+void lbm_destroy(lbm_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  delete c;
+}
+
+int lbm_set_stream(lbm_ctx* c, void* s) {
+  if (!c) return fail(LBM_EINVAL, "null context");
+  c->stream = static_cast<cudaStream_t>(s);
+  return LBM_OK;
+}
+
+int lbm_set_precision(lbm_ctx* c, int storage) {
+  if (!c) return fail(LBM_EINVAL, "null context");
+  const Ops* o = pick_ops(c->q, storage);
+  if (!o) return fail(LBM_EINVAL, "storage must be LBM_F64, LBM_F32, LBM_F16 or LBM_BF16");
+  CK(cudaStreamSynchronize(c->stream));
+  // compute-typed side buffers follow the new compute type
+  std::vector<double> g;
+  if (c->has_gamma) {
+    g.resize(c->N);
+    CK(c->stage.ensure((size_t)c->N * 8));
+    c->ops->convert(c->gamma.p, c->ops->celem == 8 ? LBM_DTYPE_F64 : LBM_DTYPE_F32, c->stage.p, LBM_DTYPE_F64, c->N, c->stream);
+    CK(cudaMemcpyAsync(g.data(), c->stage.p, (size_t)c->N * 8, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  c->storage = storage;
+  c->ops = o;
+  c->f.release();
+  c->gamma.release();
+  int rc;
+  if ((rc = alloc_state(c)) != LBM_OK) return rc;
+  if ((rc = upload_uin(c)) != LBM_OK) return rc;
+  if (c->has_gamma && (rc = upload_compute(c, c->gamma, g.data(), LBM_DTYPE_F64, c->N)) != LBM_OK) return rc;
+  c->wnrm.release(); c->wyw.release(); c->ref0.release(); c->ref1.release();
+  if ((rc = build_geometry(c)) != LBM_OK) return rc;
+  return reset_state(c);
+}
+
+int lbm_set_faces(lbm_ctx* c, const int kinds[6]) {
+  if (!c || !kinds) return fail(LBM_EINVAL, "null argument");
+  for (int f = 0; f < 6; ++f)
+    if (kinds[f] < 0 || kinds[f] > 3) return fail(LBM_EINVAL, "face kind %d out of range", kinds[f]);
+  for (int a = 0; a < 3; ++a)
+    if ((kinds[2 * a] == LBM_FACE_PERIODIC) != (kinds[2 * a + 1] == LBM_FACE_PERIODIC))
+      return fail(LBM_EINVAL, "periodic faces must come in pairs (axis %d)", a);
+  CK(cudaStreamSynchronize(c->stream));
+  for (int f = 0; f < 6; ++f) c->face[f] = kinds[f];
+  int rc = build_geometry(c);
+  if (rc != LBM_OK) return rc;
+  return reset_state(c);
+}
+
+int lbm_set_periodic(lbm_ctx* c, int px, int py, int pz) {
+  if (!c) return fail(LBM_EINVAL, "null context");
+  int k[6] = {px ? 0 : 1, px ? 0 : 1, py ? 0 : 1, py ? 0 : 1, pz ? 0 : 1, pz ? 0 : 1};
+  return lbm_set_faces(c, k);
+}
+
+int lbm_set_geometry(lbm_ctx* c, const uint8_t* mask, const float* wall_dist) {
+  if (!c) return fail(LBM_EINVAL, "null context");
+  int rc;
+  if ((rc = check_ptr(c, mask, "mask")) != LBM_OK) return rc;
+  if (wall_dist && (rc = check_ptr(c, wall_dist, "wall_dist")) != LBM_OK) return rc;
+  if (!is_device_ptr(mask, c->device)) {
+    for (long long n = 0; n < c->N; ++n) {
+      const uint8_t m = mask[n];
+      if (!(m == 0 || m == 1 || m == 3 || m == 4))
+        return fail(LBM_EINVAL, "mask[%lld] = %d: codes are 0 fluid, 1 solid, 3 inflow, 4 outflow", n, int(m));
+    }
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  if ((rc = upload(c, c->mask.p, mask, (size_t)c->N)) != LBM_OK) return rc;
+  if (wall_dist) {
+    CK(c->wdist.ensure((size_t)c->N * sizeof(float)));
+    if ((rc = upload(c, c->wdist.p, wall_dist, (size_t)c->N * sizeof(float))) != LBM_OK) return rc;
+    c->has_wdist = true;
+  } else {
+    c->has_wdist = false;
+  }
+  if ((rc = build_geometry(c)) != LBM_OK) {
+    cudaMemsetAsync(c->mask.p, 0, c->N, c->stream);
+    build_geometry(c);
+    reset_state(c);
+    return rc;
+  }
+  return reset_state(c);
+}
+
+int lbm_set_force(lbm_ctx* c, double fx, double fy, double fz) {
+  if (!c) return fail(LBM_EINVAL, "null context");
+  if (!std::isfinite(fx) || !std::isfinite(fy) || !std::isfinite(fz)) return fail(LBM_EINVAL, "force must be finite");
+  c->force[0] = fx; c->force[1] = fy; c->force[2] = fz;
+  return LBM_OK;
+}
+
+int lbm_set_inflow_ex(lbm_ctx* c, const void* u_in, int dtype) {
+  if (!c) return fail(LBM_EINVAL, "null context");
+  if (!valid_dtype(dtype)) return fail(LBM_EINVAL, "dtype must be LBM_DTYPE_F32 or LBM_DTYPE_F64");
+  int rc;
+  if ((rc = check_ptr(c, u_in, "u_in")) != LBM_OK) return rc;
+  const size_t n = 3 * (size_t)c->ny * c->nz;
+  CK(cudaStreamSynchronize(c->stream));
+  std::vector<unsigned char> tmp(n * dsize(dtype));
+  CK(cudaMemcpy(tmp.data(), u_in, tmp.size(), cudaMemcpyDefault));
+  for (size_t i = 0; i < n; ++i) {
+    const double v = dtype == LBM_DTYPE_F64 ? reinterpret_cast<const double*>(tmp.data())[i]
+                                            : double(reinterpret_cast<const float*>(tmp.data())[i]);
+    if (!std::isfinite(v) || (i < (size_t)c->ny * c->nz && v >= 1.0)) return fail(LBM_EINVAL, "u_in[%zu] = %g invalid", i, v);
+    c->uin_host[i] = v;
+  }
+  return upload_uin(c);
+}
+int lbm_set_inflow(lbm_ctx* c, const float* u_in) { return lbm_set_inflow_ex(c, u_in, LBM_DTYPE_F32); }
+
+int lbm_set_outflow(lbm_ctx* c, double rho_out) {
+  if (!c) return fail(LBM_EINVAL, "null context");
+  if (!(rho_out > 0.0) || !std::isfinite(rho_out)) return fail(LBM_EINVAL, "rho_out must be > 0");
+  c->rho_out = rho_out;
+  return LBM_OK;
+}
+
+int lbm_set_porosity_ex(lbm_ctx* c, const void* gamma, int dtype) {
+  if (!c) return fail(LBM_EINVAL, "null context");
+  if (!gamma) {
+    c->has_gamma = false;
+    return LBM_OK;
+  }
+  if (!valid_dtype(dtype)) return fail(LBM_EINVAL, "dtype must be LBM_DTYPE_F32 or LBM_DTYPE_F64");
+  int rc;
+  if ((rc = check_ptr(c, gamma, "gamma")) != LBM_OK) return rc;
+  CK(cudaStreamSynchronize(c->stream));
+  if ((rc = upload_compute(c, c->gamma, gamma, dtype, c->N)) != LBM_OK) return rc;
+  c->has_gamma = true;
+  return LBM_OK;
+}
+int lbm_set_porosity(lbm_ctx* c, const float* gamma) { return lbm_set_porosity_ex(c, gamma, LBM_DTYPE_F32); }
+
+int lbm_set_wall_model(lbm_ctx* c, double kappa, double E) {
+  if (!c) return fail(LBM_EINVAL, "null context");
+  if (!(kappa > 0.0)) {
+    c->wm = false;
+    return LBM_OK;
+  }
+  if (!(E > 0.0) || !std::isfinite(E) || !std::isfinite(kappa)) return fail(LBM_EINVAL, "E must be > 0");
+  c->wm = true;
+  c->kappa = kappa;
+  c->E = E;
+  return LBM_OK;
+}
+
+int lbm_init_equilibrium_ex(lbm_ctx* c, const void* rho, const void* u, int dtype) {
+  if (!c) return fail(LBM_EINVAL, "null context");
+  if (!valid_dtype(dtype)) return fail(LBM_EINVAL, "dtype must be LBM_DTYPE_F32 or LBM_DTYPE_F64");
+  int rc;
+  if ((rc = check_ptr(c, rho, "rho")) != LBM_OK) return rc;
+  if ((rc = check_ptr(c, u, "u")) != LBM_OK) return rc;
+  const size_t es = dsize(dtype);
+  const size_t bytes = (size_t)c->N * es;
+  CK(c->stage.ensure(4 * bytes));
+  CK(cudaMemcpyAsync(c->stage.p, rho, bytes, cudaMemcpyDefault, c->stream));
+  CK(cudaMemcpyAsync(static_cast<char*>(c->stage.p) + bytes, u, 3 * bytes, cudaMemcpyDefault, c->stream));
+  c->t = 0;
+  c->adj_t0 = -1;
+  Args a = make_args(c);
+  c->ops->init_eq(a, c->stage.p, static_cast<char*>(c->stage.p) + bytes, dtype, c->stream);
+  CK(cudaGetLastError());
+  CK(cudaMemsetAsync(c->status.p, 0, sizeof(unsigned), c->stream));
+  c->status_seen = 0;
+  if ((rc = fill_refs(c)) != LBM_OK) return rc;
+  CK(cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+int lbm_init_equilibrium(lbm_ctx* c, const float* rho, const float* u) {
+  return lbm_init_equilibrium_ex(c, rho, u, LBM_DTYPE_F32);
+}
+
+int lbm_step(lbm_ctx* c, int n) {
+  if (!c) return fail(LBM_EINVAL, "null context");
+  if (n < 0) return fail(LBM_EINVAL, "n must be >= 0");
+  for (int s = 0; s < n; ++s) {
+    const Args a = make_args(c);
+    const int odd = int(c->t & 1);
+    c->ops->step_bulk(a, odd, c->stream);
+    c->ops->step_list(a, odd, c->stream);
+    ++c->t;
+  }
+  CK(cudaGetLastError());
+  return status_code(c);
+}
+
+int lbm_step_timed(lbm_ctx* c, int n, double ms[3]) {
+  if (!c || !ms) return fail(LBM_EINVAL, "null argument");
+  if (n < 1) return fail(LBM_EINVAL, "n must be >= 1");
+  std::vector<cudaEvent_t> ev(3 * (size_t)n);
+  for (auto& e : ev) CK(cudaEventCreate(&e));
+  for (int s = 0; s < n; ++s) {
+    const Args a = make_args(c);
+    const int odd = int(c->t & 1);
+    CK(cudaEventRecord(ev[3 * s], c->stream));
+    c->ops->step_bulk(a, odd, c->stream);
+    CK(cudaEventRecord(ev[3 * s + 1], c->stream));
+    c->ops->step_list(a, odd, c->stream);
+    CK(cudaEventRecord(ev[3 * s + 2], c->stream));
+    ++c->t;
+  }
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(c->stream));
+  for (int s = 0; s < n; ++s) {
+    float t0 = 0, t1 = 0;
+    CK(cudaEventElapsedTime(&t0, ev[3 * s], ev[3 * s + 1]));
+    CK(cudaEventElapsedTime(&t1, ev[3 * s + 1], ev[3 * s + 2]));
+    ms[0] += t0;
+    ms[1] += t1;
+  }
+  float tot = 0;
+  CK(cudaEventElapsedTime(&tot, ev[0], ev[3 * (size_t)n - 1]));
+  ms[2] += tot;
+  for (auto& e : ev) cudaEventDestroy(e);
+  int rc = read_status(c);
+  if (rc != LBM_OK) return rc;
+  return status_code(c);
+}
+
+int lbm_sync(lbm_ctx* c) {
+  if (!c) return fail(LBM_EINVAL, "null context");
+  int rc = read_status(c);
+  if (rc != LBM_OK) return rc;
+  return status_code(c);
+}
+
+int lbm_moments_ex(lbm_ctx* c, void* rho, void* u, int dtype) {
+  if (!c) return fail(LBM_EINVAL, "null context");
+  if (!valid_dtype(dtype)) return fail(LBM_EINVAL, "dtype must be LBM_DTYPE_F32 or LBM_DTYPE_F64");
+  int rc;
+  if ((rc = check_ptr(c, rho, "rho")) != LBM_OK) return rc;
+  if ((rc = check_ptr(c, u, "u")) != LBM_OK) return rc;
+  const size_t bytes = (size_t)c->N * dsize(dtype);
+  Args a = make_args(c);
+  const int sw = int(c->t & 1);
+  const bool dev = is_device_ptr(rho, c->device) && is_device_ptr(u, c->device);
+  if (dev) {
+    c->ops->moments(a, sw, rho, u, dtype, c->stream);
+    CK(cudaGetLastError());
+  } else {
+    CK(c->stage.ensure(4 * bytes));
+    c->ops->moments(a, sw, c->stage.p, static_cast<char*>(c->stage.p) + bytes, dtype, c->stream);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(rho, c->stage.p, bytes, cudaMemcpyDefault, c->stream));
+    CK(cudaMemcpyAsync(u, static_cast<char*>(c->stage.p) + bytes, 3 * bytes, cudaMemcpyDefault, c->stream));
+  }
+  if ((rc = read_status(c)) != LBM_OK) return rc;
+  return status_code(c);
+}
+int lbm_moments(lbm_ctx* c, float* rho, float* u) { return lbm_moments_ex(c, rho, u, LBM_DTYPE_F32); }
+
+int lbm_reduce(lbm_ctx* c, double* mass, double mom[3]) {
+  if (!c || !mass || !mom) return fail(LBM_EINVAL, "null argument");
+  Args a = make_args(c);
+  c->ops->reduce(a, int(c->t & 1), static_cast<double*>(c->red.p), RED_BLOCKS, c->stream);
+  reduce_final(static_cast<const double*>(c->red.p), RED_BLOCKS, static_cast<double*>(c->redout.p), c->stream);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(c->red_h, c->redout.p, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  int rc = read_status(c);
+  if (rc != LBM_OK) return rc;
+  *mass = c->red_h[0];
+  mom[0] = c->red_h[1]; mom[1] = c->red_h[2]; mom[2] = c->red_h[3];
+  return status_code(c);
+}
+
+int lbm_get_populations(lbm_ctx* c, void* f, int dtype) {
+  if (!c) return fail(LBM_EINVAL, "null context");
+  if (!valid_dtype(dtype)) return fail(LBM_EINVAL, "dtype must be LBM_DTYPE_F32 or LBM_DTYPE_F64");
+  int rc;
+  if ((rc = check_ptr(c, f, "f")) != LBM_OK) return rc;
+  const size_t bytes = (size_t)c->q * c->N * dsize(dtype);
+  Args a = make_args(c);
+  if (is_device_ptr(f, c->device)) {
+    c->ops->get_pops(a, int(c->t & 1), f, dtype, c->stream);
+    CK(cudaGetLastError());
+  } else {
+    CK(c->stage.ensure(bytes));
+    c->ops->get_pops(a, int(c->t & 1), c->stage.p, dtype, c->stream);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(f, c->stage.p, bytes, cudaMemcpyDefault, c->stream));
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+
+int lbm_set_populations(lbm_ctx* c, const void* f, int dtype) {
+  if (!c) return fail(LBM_EINVAL, "null context");
+  if (!valid_dtype(dtype)) return fail(LBM_EINVAL, "dtype must be LBM_DTYPE_F32 or LBM_DTYPE_F64");
+  int rc;
+  if ((rc = check_ptr(c, f, "f")) != LBM_OK) return rc;
+  const size_t bytes = (size_t)c->q * c->N * dsize(dtype);
+  CK(c->stage.ensure(bytes));
+  CK(cudaMemcpyAsync(c->stage.p, f, bytes, cudaMemcpyDefault, c->stream));
+  Args a = make_args(c);
+  c->ops->set_pops(a, int(c->t & 1), c->stage.p, dtype, c->stream);
+  CK(cudaGetLastError());
+  c->adj_t0 = -1;
+  if ((rc = fill_refs(c)) != LBM_OK) return rc;
+  CK(cudaStreamSynchronize(c->stream));
+  return LBM_OK;
+}
+
+int lbm_info(lbm_ctx* c, int64_t out[10]) {
+  if (!c || !out) return fail(LBM_EINVAL, "null argument");
+  out[0] = c->N; out[1] = c->n_list; out[2] = c->counts[0]; out[3] = c->counts[1]; out[4] = c->counts[2];
+  out[5] = c->counts[3]; out[6] = c->counts[4]; out[7] = c->t; out[8] = c->storage; out[9] = c->q;
+  return LBM_OK;
+}
+
+int lbm_debug_dump(lbm_ctx* c, int which, int64_t* out, size_t count) {
+  if (!c || !out) return fail(LBM_EINVAL, "null argument");
+  CK(cudaStreamSynchronize(c->stream));
+  size_t need = 0;
+  switch (which) {
+    case 0: need = c->N; break;
+    case 1: case 2: need = c->n_list; break;
+    case 3: need = 3 * (size_t)c->n_list; break;
+    case 4: case 5: need = (size_t)c->q * c->N; break;
+    default: return fail(LBM_EINVAL, "which must be 0..5");
+  }
+  if (count < need) return fail(LBM_EINVAL, "output holds %zu values, %zu needed", count, need);
+  if (which == 0) {
+    for (long long n = 0; n < c->N; ++n) out[n] = c->type_host[n];
+    return LBM_OK;
+  }
+  if (which == 1) {
+    std::vector<long long> v(need);
+    if (need) CK(cudaMemcpy(v.data(), c->lcell.p, need * sizeof(long long), cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < need; ++i) out[i] = v[i];
+    return LBM_OK;
+  }
+  if (which == 2 || which == 3) {
+    std::vector<int> v(need);
+    if (need) CK(cudaMemcpy(v.data(), which == 2 ? c->wref.p : c->nsum.p, need * sizeof(int), cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < need; ++i) out[i] = v[i];
+    return LBM_OK;
+  }
+  DevBuf tmp;
+  CK(tmp.ensure(2 * need * sizeof(int64_t)));
+  geo_source_map(geo_args(c), static_cast<const uint8_t*>(c->type.p), static_cast<int64_t*>(tmp.p),
+                 static_cast<int64_t*>(tmp.p) + need, c->stream);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(out, static_cast<int64_t*>(tmp.p) + (which == 4 ? 0 : need), need * sizeof(int64_t),
+                     cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  tmp.release();
+  return LBM_OK;
+}
+
+int lbm_save(lbm_ctx* c, void* buf, size_t* len) {
+  if (!c || !len) return fail(LBM_EINVAL, "null argument");
+  const size_t fb = (size_t)c->q * c->stride * c->ops->elem;
+  const size_t rb = std::max<size_t>(1, (size_t)c->n_list) * 3 * c->ops->celem;
+  const size_t total = sizeof(SaveHeader) + fb + 2 * rb;
+  if (!buf) {
+    *len = total;
+    return LBM_OK;
+  }
+  if (*len < total) return fail(LBM_EINVAL, "buffer holds %zu bytes, %zu needed", *len, total);
+  SaveHeader h{};
+  h.magic = SAVE_MAGIC; h.q = c->q; h.storage = c->storage;
+  h.nx = c->nx; h.ny = c->ny; h.nz = c->nz; h.n_list = c->n_list; h.t = c->t;
+  h.fbytes = fb; h.rbytes = rb;
+  char* p = static_cast<char*>(buf);
+  std::memcpy(p, &h, sizeof(h));
+  CK(cudaMemcpyAsync(p + sizeof(h), c->f.p, fb, cudaMemcpyDefault, c->stream));
+  CK(cudaMemcpyAsync(p + sizeof(h) + fb, c->ref0.p, rb, cudaMemcpyDefault, c->stream));
+  CK(cudaMemcpyAsync(p + sizeof(h) + fb + rb, c->ref1.p, rb, cudaMemcpyDefault, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  *len = total;
+  return LBM_OK;
+}
+
+int lbm_load(lbm_ctx* c, const void* buf, size_t len) {
+  if (!c || !buf) return fail(LBM_EINVAL, "null argument");
+  if (len < sizeof(SaveHeader)) return fail(LBM_EINVAL, "buffer too short");
+  SaveHeader h;
+  std::memcpy(&h, buf, sizeof(h));
+  const size_t fb = (size_t)c->q * c->stride * c->ops->elem;
+  const size_t rb = std::max<size_t>(1, (size_t)c->n_list) * 3 * c->ops->celem;
+  if (h.magic != SAVE_MAGIC || int(h.q) != c->q || int(h.storage) != c->storage || h.nx != c->nx || h.ny != c->ny ||
+      h.nz != c->nz || h.n_list != c->n_list || h.fbytes != fb || h.rbytes != rb || len < sizeof(h) + fb + 2 * rb)
+    return fail(LBM_EINVAL, "checkpoint does not match this context (lattice, size, storage or geometry)");
+  const char* p = static_cast<const char*>(buf);
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaMemcpyAsync(c->f.p, p + sizeof(h), fb, cudaMemcpyDefault, c->stream));
+  CK(cudaMemcpyAsync(c->ref0.p, p + sizeof(h) + fb, rb, cudaMemcpyDefault, c->stream));
+  CK(cudaMemcpyAsync(c->ref1.p, p + sizeof(h) + fb + rb, rb, cudaMemcpyDefault, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->t = h.t;
+  c->adj_t0 = -1;
+  return LBM_OK;
+}
+
+// ---- adjoint ---------------------------------------------------------------------------------------------
+static int adj_check(lbm_ctx* c, int xa, int xb, double* wa, double* wb, int W) {
+  if (c->wm) return fail(LBM_ESTATE, "the wall model is not differentiated; switch it off (kappa <= 0)");
+  if (xa < 0 || xa >= c->nx || xb < 0 || xb >= c->nx || xa == xb) return fail(LBM_EINVAL, "objective planes out of range");
+  long long na = 0, nb = 0;
+  for (long long n = 0; n < c->N; ++n) {
+    const int x = int(n % c->nx);
+    if (x != xa && x != xb) continue;
+    const int k = c->type_host[n] & T_KIND;
+    if (k == K_SOLID) continue;
+    if (k == K_INFLOW || k == K_OUTFLOW) return fail(LBM_EINVAL, "objective plane x=%d holds boundary cells", x);
+    (x == xa ? na : nb)++;
+  }
+  if (na == 0 || nb == 0) return fail(LBM_EINVAL, "objective plane without fluid cells");
+  *wa = (1.0 / 3.0) / (double(W) * na);
+  *wb = -(1.0 / 3.0) / (double(W) * nb);
+  return LBM_OK;
+}
+
+int lbm_objective_forward(lbm_ctx* c, int T, int W, int xa, int xb, int ckpt, double* J) {
+  if (!c || !J) return fail(LBM_EINVAL, "null argument");
+  if (T < 1 || W < 1 || W > T) return fail(LBM_EINVAL, "need 1 <= W <= T");
+  if (ckpt < 2 || (ckpt & 1)) return fail(LBM_EINVAL, "checkpoint interval must be even and >= 2");
+  if (c->t & 1) return fail(LBM_ESTATE, "the forward run must start after an even number of steps");
+  double wa, wb;
+  int rc = adj_check(c, xa, xb, &wa, &wb, W);
+  if (rc != LBM_OK) return rc;
+  const int nck = (T + ckpt - 1) / ckpt;
+  const size_t sb = (size_t)c->q * c->stride * c->ops->elem;
+  if ((int)c->ckpts.size() < nck) c->ckpts.resize(nck);
+  for (int k = 0; k < nck; ++k) {
+    cudaError_t e = c->ckpts[k].ensure(sb);
+    if (e != cudaSuccess) return fail(e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, "checkpoints: %s", cudaGetErrorString(e));
+  }
+  CK(cudaMemsetAsync(c->redout.p, 0, sizeof(double), c->stream));
+  for (int s = 0; s < T; ++s) {
+    if (s % ckpt == 0) CK(cudaMemcpyAsync(c->ckpts[s / ckpt].p, c->f.p, sb, cudaMemcpyDeviceToDevice, c->stream));
+    const Args a = make_args(c);
+    const int odd = int(c->t & 1);
+    c->ops->step_bulk(a, odd, c->stream);
+    c->ops->step_list(a, odd, c->stream);
+    ++c->t;
+    if (s + 1 > T - W) {
+      const Args b = make_args(c);
+      c->ops->plane_rho(b, c->f.p, int(c->t & 1), xa, xb, static_cast<double*>(c->redout.p), wa, wb, c->stream);
+    }
+  }
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(c->red_h, c->redout.p, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  if ((rc = read_status(c)) != LBM_OK) return rc;
+  *J = c->red_h[0];
+  c->adj_T = T; c->adj_W = W; c->adj_xa = xa; c->adj_xb = xb; c->adj_ck = ckpt;
+  c->adj_wa = wa; c->adj_wb = wb;
+  c->adj_t0 = c->t;
+  return status_code(c);
+}
+
+int lbm_objective_backward(lbm_ctx* c, double* dJ_dgamma, double* dJ_duin) {
+  if (!c) return fail(LBM_EINVAL, "null context");
+  if (c->adj_t0 != c->t) return fail(LBM_ESTATE, "no forward run to differentiate (run lbm_objective_forward first)");
+  if (c->wm) return fail(LBM_ESTATE, "the wall model is not differentiated");
+  const int T = c->adj_T, W = c->adj_W, ck = c->adj_ck;
+  const int nck = (T + ck - 1) / ck;
+  const size_t sb = (size_t)c->q * c->stride * c->ops->elem;
+  const size_t lb = (size_t)c->q * c->stride * c->ops->celem;
+  const size_t pl = 3 * (size_t)c->ny * c->nz;
+  if ((int)c->ring.size() < ck) c->ring.resize(ck);
+  for (int k = 1; k < ck; ++k) {
+    cudaError_t e = c->ring[k].ensure(sb);
+    if (e != cudaSuccess) return fail(e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, "ring: %s", cudaGetErrorString(e));
+  }
+  CK(c->lamA.ensure(lb));
+  CK(c->lamB.ensure(lb));
+  CK(c->dgam.ensure((size_t)c->N * c->ops->celem));
+  CK(c->duin.ensure(pl * c->ops->celem));
+  cudaStream_t s = c->stream;
+  CK(cudaMemsetAsync(c->dgam.p, 0, (size_t)c->N * c->ops->celem, s));
+  CK(cudaMemsetAsync(c->duin.p, 0, pl * c->ops->celem, s));
+  Args a = make_args(c);
+  c->ops->seed(a, c->lamA.p, c->adj_xa, c->adj_xb, c->adj_wa, c->adj_wb, s);
+  void* lin = c->lamA.p;
+  void* lout = c->lamB.p;
+  cudaEvent_t e0, e1, e2;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaEventCreate(&e2));
+  float rec_ms = 0, rev_ms = 0;
+  for (int seg = nck - 1; seg >= 0; --seg) {
+    const int t0 = seg * ck;
+    const int L = std::min(T, t0 + ck) - t0;
+    std::vector<const void*> st(L);
+    st[0] = c->ckpts[seg].p;
+    CK(cudaEventRecord(e0, s));
+    for (int j = 1; j < L; ++j) {
+      c->ops->step_oop(a, st[j - 1], c->ring[j].p, s);
+      st[j] = c->ring[j].p;
+    }
+    CK(cudaEventRecord(e1, s));
+    for (int j = L - 1; j >= 0; --j) {
+      const int t = t0 + j;
+      AdjArgs d{};
+      d.fst = st[j];
+      d.lam_in = lin;
+      d.lam_out = lout;
+      d.dgam = c->dgam.p;
+      d.duin = c->duin.p;
+      d.add_dj = (t > T - W) ? 1 : 0;
+      d.xa = c->adj_xa; d.xb = c->adj_xb; d.wa = c->adj_wa; d.wb = c->adj_wb;
+      c->ops->reverse(a, d, s);
+      std::swap(lin, lout);
+    }
+    CK(cudaEventRecord(e2, s));
+    CK(cudaEventSynchronize(e2));
+    float m0 = 0, m1 = 0;
+    CK(cudaEventElapsedTime(&m0, e0, e1));
+    CK(cudaEventElapsedTime(&m1, e1, e2));
+    rec_ms += m0;
+    rev_ms += m1;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaEventDestroy(e2);
+  CK(cudaGetLastError());
+  c->adj_ms[0] = rec_ms;
+  c->adj_ms[1] = rev_ms;
+  const int cd = c->ops->celem == 8 ? LBM_DTYPE_F64 : LBM_DTYPE_F32;
+  if (dJ_dgamma) {
+    CK(c->stage.ensure((size_t)c->N * 8));
+    c->ops->convert(c->dgam.p, cd, c->stage.p, LBM_DTYPE_F64, c->N, s);
+    CK(cudaMemcpyAsync(dJ_dgamma, c->stage.p, (size_t)c->N * 8, cudaMemcpyDefault, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  if (dJ_duin) {
+    CK(c->stage.ensure(pl * 8));
+    c->ops->convert(c->duin.p, cd, c->stage.p, LBM_DTYPE_F64, (long long)pl, s);
+    CK(cudaMemcpyAsync(dJ_duin, c->stage.p, pl * 8, cudaMemcpyDefault, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  int rc = read_status(c);
+  if (rc != LBM_OK) return rc;
+  return status_code(c);
+}
+
+int lbm_adjoint_step(lbm_ctx* c, const void* lam_in, void* lam_out, int dtype, double* dgamma, double* duin) {
+  if (!c) return fail(LBM_EINVAL, "null context");
+  if (!valid_dtype(dtype)) return fail(LBM_EINVAL, "dtype must be LBM_DTYPE_F32 or LBM_DTYPE_F64");
+  if (c->wm) return fail(LBM_ESTATE, "the wall model is not differentiated");
+  if (c->t & 1) return fail(LBM_ESTATE, "the reverse step needs the state after an even number of steps");
+  int rc;
+  if ((rc = check_ptr(c, lam_in, "lam_in")) != LBM_OK) return rc;
+  if ((rc = check_ptr(c, lam_out, "lam_out")) != LBM_OK) return rc;
+  const size_t cnt = (size_t)c->q * c->N;
+  const size_t lb = (size_t)c->q * c->stride * c->ops->celem;
+  const size_t pl = 3 * (size_t)c->ny * c->nz;
+  const int cd = c->ops->celem == 8 ? LBM_DTYPE_F64 : LBM_DTYPE_F32;
+  cudaStream_t s = c->stream;
+  CK(c->lamA.ensure(lb));
+  CK(c->lamB.ensure(lb));
+  CK(c->dgam.ensure((size_t)c->N * c->ops->celem));
+  CK(c->duin.ensure(pl * c->ops->celem));
+  CK(cudaMemsetAsync(c->dgam.p, 0, (size_t)c->N * c->ops->celem, s));
+  CK(cudaMemsetAsync(c->duin.p, 0, pl * c->ops->celem, s));
+  // caller layout q*N -> padded q*stride
+  CK(c->stage.ensure(cnt * 8));
+  CK(cudaMemcpyAsync(c->stage.p, lam_in, cnt * dsize(dtype), cudaMemcpyDefault, s));
+  for (int i = 0; i < c->q; ++i)
+    c->ops->convert(static_cast<const char*>(c->stage.p) + (size_t)i * c->N * dsize(dtype), dtype,
+                    static_cast<char*>(c->lamA.p) + (size_t)i * c->stride * c->ops->celem, cd, c->N, s);
+  Args a = make_args(c);
+  AdjArgs d{};
+  d.fst = c->f.p;
+  d.lam_in = c->lamA.p;
+  d.lam_out = c->lamB.p;
+  d.dgam = c->dgam.p;
+  d.duin = c->duin.p;
+  c->ops->reverse(a, d, s);
+  for (int i = 0; i < c->q; ++i)
+    c->ops->convert(static_cast<const char*>(c->lamB.p) + (size_t)i * c->stride * c->ops->celem, cd,
+                    static_cast<char*>(c->stage.p) + (size_t)i * c->N * dsize(dtype), dtype, c->N, s);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(lam_out, c->stage.p, cnt * dsize(dtype), cudaMemcpyDefault, s));
+  CK(cudaStreamSynchronize(s));
+  if (dgamma) {
+    c->ops->convert(c->dgam.p, cd, c->stage.p, LBM_DTYPE_F64, c->N, s);
+    CK(cudaMemcpyAsync(dgamma, c->stage.p, (size_t)c->N * 8, cudaMemcpyDefault, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  if (duin) {
+    c->ops->convert(c->duin.p, cd, c->stage.p, LBM_DTYPE_F64, (long long)pl, s);
+    CK(cudaMemcpyAsync(duin, c->stage.p, pl * 8, cudaMemcpyDefault, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  return LBM_OK;
+}
+
+int lbm_adjoint_timing(lbm_ctx* c, double ms[2]) {
+  if (!c || !ms) return fail(LBM_EINVAL, "null argument");
+  ms[0] = c->adj_ms[0];
+  ms[1] = c->adj_ms[1];
+  return LBM_OK;
+}
+
+}  // extern "C"

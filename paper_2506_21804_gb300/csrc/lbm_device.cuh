@@ -1,0 +1,426 @@
+// Device-side building blocks of the fused collide-and-stream update: velocity sets, storage
+// codecs, the AA-pattern slot map, and the per-cell physics (moments, equilibrium, Smagorinsky
+// relaxation, regularised boundaries, Spalding wall model).
+//
+// Populations are stored as deviations h_i = f_i - w_i from the rest state in structure-of-arrays
+// form, one array per population index. Propagation is the in-place AA pattern: an even step
+// reads and writes only the cell's own slots (writing f*_i into slot opp(i)), an odd step reads
+// each incoming population from the slot where the previous even step left it and writes each
+// outgoing population into the same slot, where the next even step finds it. Boundary
+// substitutions (bounce-back, specular slip, open-face unknowns) only change which slot a
+// direction uses, so every slot is still read and written by exactly one cell per step.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <type_traits>
+#include <utility>
+
+namespace lbm {
+
+// ---- type byte -----------------------------------------------------------------------------------
+constexpr uint8_t T_KIND = 7;    // bits 0-2: kind
+constexpr uint8_t T_REF = 8;     // wall-model reference cell (writes its velocity)
+constexpr uint8_t T_NEAR = 16;   // some source position is solid or outside the domain
+constexpr uint8_t T_LIST = 32;   // handled by the boundary-list kernel
+enum { K_FLUID = 0, K_SOLID = 1, K_WALL = 2, K_INFLOW = 3, K_OUTFLOW = 4 };
+enum { F_PERIODIC = 0, F_WALL = 1, F_SLIP = 2, F_OPEN = 3 };
+constexpr unsigned ST_NAN = 1u, ST_BADMASK = 2u;
+
+// ---- velocity sets (Sec. 2.2, Fig. "lattice"), ordering of include/lbm.h -------------------------
+template <int Q> struct Lat;
+template <> struct Lat<19> {
+  static constexpr int Q = 19, H = 9, Wden = 36;
+  __host__ __device__ static constexpr int cx(int i) {
+    constexpr int t[19] = {0, 1, 0, 0, 1, 1, 1, 1, 0, 0, -1, 0, 0, -1, -1, -1, -1, 0, 0};
+    return t[i];
+  }
+  __host__ __device__ static constexpr int cy(int i) {
+    constexpr int t[19] = {0, 0, 1, 0, 1, -1, 0, 0, 1, 1, 0, -1, 0, -1, 1, 0, 0, -1, -1};
+    return t[i];
+  }
+  __host__ __device__ static constexpr int cz(int i) {
+    constexpr int t[19] = {0, 0, 0, 1, 0, 0, 1, -1, 1, -1, 0, 0, -1, 0, 0, -1, 1, -1, 1};
+    return t[i];
+  }
+  __host__ __device__ static constexpr int W(int i) {  // 36 w_i
+    constexpr int t[19] = {12, 2, 2, 2, 1, 1, 1, 1, 1, 1, 2, 2, 2, 1, 1, 1, 1, 1, 1};
+    return t[i];
+  }
+};
+template <> struct Lat<27> {
+  static constexpr int Q = 27, H = 13, Wden = 216;
+  __host__ __device__ static constexpr int cx(int i) {
+    constexpr int t[27] = {0, 1, 0, 0, 1, 1, 1, 1, 0, 0, 1, 1, 1, 1, -1, 0, 0, -1, -1, -1, -1, 0, 0, -1, -1, -1, -1};
+    return t[i];
+  }
+  __host__ __device__ static constexpr int cy(int i) {
+    constexpr int t[27] = {0, 0, 1, 0, 1, -1, 0, 0, 1, 1, 1, 1, -1, -1, 0, -1, 0, -1, 1, 0, 0, -1, -1, -1, -1, 1, 1};
+    return t[i];
+  }
+  __host__ __device__ static constexpr int cz(int i) {
+    constexpr int t[27] = {0, 0, 0, 1, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, -1, 0, 0, -1, 1, -1, 1, -1, 1, -1, 1};
+    return t[i];
+  }
+  __host__ __device__ static constexpr int W(int i) {  // 216 w_i
+    constexpr int t[27] = {64, 16, 16, 16, 4, 4, 4, 4, 4, 4, 1, 1, 1, 1, 16, 16, 16, 4, 4, 4, 4, 4, 4, 1, 1, 1, 1};
+    return t[i];
+  }
+};
+template <int Q> __host__ __device__ constexpr int opp(int i) {
+  return i == 0 ? 0 : (i <= Lat<Q>::H ? i + Lat<Q>::H : i - Lat<Q>::H);
+}
+template <int Q, class C> __device__ __forceinline__ constexpr C wgt(int i) {
+  return C(Lat<Q>::W(i)) / C(Lat<Q>::Wden);
+}
+// Direction index of a velocity (components in {-1,0,1}); -1 if absent from the set.
+template <int Q> __device__ __forceinline__ int dir_of(int x, int y, int z) {
+  int r = -1;
+#pragma unroll
+  for (int i = 0; i < Q; ++i)
+    if (Lat<Q>::cx(i) == x && Lat<Q>::cy(i) == y && Lat<Q>::cz(i) == z) r = i;
+  return r;
+}
+
+// Compile-time integer usable as an index in device code.
+template <int V> struct IC {
+  static constexpr int value = V;
+  __host__ __device__ constexpr operator int() const { return V; }
+};
+// Compile-time loop: f(IC<I>) for I = B..E-1.
+template <int B, int E, class F> __device__ __forceinline__ void sfor(F&& f) {
+  if constexpr (B < E) {
+    f(IC<B>{});
+    sfor<B + 1, E>(f);
+  }
+}
+
+// ---- storage codecs --------------------------------------------------------------------------------
+template <class S> struct Codec;
+template <> struct Codec<double> {
+  using C = double;
+  static __device__ __forceinline__ C ld(const double* p) { return *p; }
+  static __device__ __forceinline__ void st(double* p, C v) { *p = v; }
+};
+template <> struct Codec<float> {
+  using C = float;
+  static __device__ __forceinline__ C ld(const float* p) { return *p; }
+  static __device__ __forceinline__ void st(float* p, C v) { *p = v; }
+};
+template <> struct Codec<__half> {
+  using C = float;
+  static __device__ __forceinline__ C ld(const __half* p) { return __half2float(*p); }
+  static __device__ __forceinline__ void st(__half* p, C v) { *p = __float2half_rn(v); }
+};
+template <> struct Codec<__nv_bfloat16> {
+  using C = float;
+  static __device__ __forceinline__ C ld(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+  static __device__ __forceinline__ void st(__nv_bfloat16* p, C v) { *p = __float2bfloat16_rn(v); }
+};
+
+// ---- kernel arguments (plain data, copied by value into the launch) ---------------------------------
+struct Args {
+  void* f;                 // population deviations, population p of cell m at f + p*stride + m
+  long long stride;        // elements between population arrays
+  const uint8_t* type;     // classified type byte per cell
+  const void* gamma;       // porosity per cell (compute type) or null
+  int nx, ny, nz;
+  long long nxy, N;
+  int face[6];
+  double tau0;             // molecular relaxation time
+  double smag;             // 18 sqrt(2) C_S^2
+  double cs2smag;          // C_S^2
+  double fx, fy, fz;       // body force
+  unsigned* status;        // sticky device status bits
+  // boundary list
+  const long long* lcell;  // cell index per entry
+  int n_list;
+  const void* wnrm;        // C[3] unit normal per entry (WALL entries)
+  const void* wyw;         // C wall distance per entry
+  const int* wref;         // list position of the reference cell, -1 none
+  const void* ref_rd;      // C[3] per entry, reference velocities of the previous step
+  void* ref_wr;            // C[3] per entry, written by reference cells this step
+  const void* uin;         // C[3][ny*nz] inlet velocity
+  double rho_out;
+  int wm;                  // wall model on
+  double kappa, E;
+};
+
+// ---- AA-pattern slot map ------------------------------------------------------------------------------
+// Slot of direction i of cell (x,y,z): population index p and cell m. Before an odd step slot
+// (p, m) holds f_i(x); during the odd step it receives f*_opp(i)(x). Rules:
+//   source x - c_i inside (after periodic wrap), not solid -> (opp(i), x - c_i)   [streaming]
+//   source solid                                          -> (i, x)             [bounce-back]
+//   source beyond any open or bounce-back face            -> (i, x)             [unknown / BB]
+//   source beyond full-slip faces only                    -> (opp(j), x') with x' the source
+//     with the crossed coordinates set back to x's, j = c_i with crossed components reversed;
+//     (i, x) if x' is solid.
+template <int Q>
+__device__ __forceinline__ void slot_of(const Args& a, int x, int y, int z, long long n, int i, int& p, long long& m) {
+  int sx = x - Lat<Q>::cx(i), sy = y - Lat<Q>::cy(i), sz = z - Lat<Q>::cz(i);
+  int crossed = 0;
+  if (sx < 0) { if (a.face[0] == F_PERIODIC) sx += a.nx; else crossed |= 1; }
+  else if (sx >= a.nx) { if (a.face[1] == F_PERIODIC) sx -= a.nx; else crossed |= 2; }
+  if (sy < 0) { if (a.face[2] == F_PERIODIC) sy += a.ny; else crossed |= 4; }
+  else if (sy >= a.ny) { if (a.face[3] == F_PERIODIC) sy -= a.ny; else crossed |= 8; }
+  if (sz < 0) { if (a.face[4] == F_PERIODIC) sz += a.nz; else crossed |= 16; }
+  else if (sz >= a.nz) { if (a.face[5] == F_PERIODIC) sz -= a.nz; else crossed |= 32; }
+  if (crossed == 0) {
+    long long s = sx + (long long)a.nx * sy + a.nxy * sz;
+    if ((a.type[s] & T_KIND) == K_SOLID) { p = i; m = n; }
+    else { p = opp<Q>(i); m = s; }
+    return;
+  }
+  bool allslip = true;
+#pragma unroll
+  for (int f = 0; f < 6; ++f)
+    if ((crossed >> f & 1) && a.face[f] != F_SLIP) allslip = false;
+  if (!allslip) { p = i; m = n; return; }
+  int jx = Lat<Q>::cx(i), jy = Lat<Q>::cy(i), jz = Lat<Q>::cz(i);
+  if (crossed & 3) { sx = x; jx = -jx; }
+  if (crossed & 12) { sy = y; jy = -jy; }
+  if (crossed & 48) { sz = z; jz = -jz; }
+  long long s = sx + (long long)a.nx * sy + a.nxy * sz;
+  if ((a.type[s] & T_KIND) == K_SOLID) { p = i; m = n; return; }
+  p = opp<Q>(dir_of<Q>(jx, jy, jz));
+  m = s;
+}
+
+// ---- per-cell physics ------------------------------------------------------------------------------------
+// Equilibrium deviation f_i^eq(rho, v) - w_i = w_i (drho + rho (3 c.v + 4.5 (c.v)^2 - 1.5 v.v)).
+template <int Q, class C, int I>
+__device__ __forceinline__ C heq(C drho, C rho, C vx, C vy, C vz, C vsq) {
+  constexpr int cx = Lat<Q>::cx(I), cy = Lat<Q>::cy(I), cz = Lat<Q>::cz(I);
+  C cv = C(cx) * vx + C(cy) * vy + C(cz) * vz;
+  return wgt<Q, C>(I) * (drho + rho * (C(3) * cv + C(4.5) * cv * cv - C(1.5) * vsq));
+}
+
+template <int Q, class C>
+__device__ __forceinline__ void sums(const C* h, C& drho, C& jx, C& jy, C& jz) {
+  drho = jx = jy = jz = C(0);
+  sfor<0, Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    drho += h[i];
+    if (Lat<Q>::cx(i)) jx += C(Lat<Q>::cx(i)) * h[i];
+    if (Lat<Q>::cy(i)) jy += C(Lat<Q>::cy(i)) * h[i];
+    if (Lat<Q>::cz(i)) jz += C(Lat<Q>::cz(i)) * h[i];
+  });
+}
+
+// Q_i : A (A symmetric, given by its six components) with Q_i = c_i c_i - I/3.
+template <int Q, class C, int I>
+__device__ __forceinline__ C qcontract(C axx, C ayy, C azz, C axy, C axz, C ayz) {
+  constexpr int cx = Lat<Q>::cx(I), cy = Lat<Q>::cy(I), cz = Lat<Q>::cz(I);
+  C tr = (axx + ayy + azz) * C(1.0 / 3.0);
+  return C(cx * cx) * axx + C(cy * cy) * ayy + C(cz * cz) * azz + C(2 * cx * cy) * axy + C(2 * cx * cz) * axz +
+         C(2 * cy * cz) * ayz - tr;
+}
+
+// BGK + Smagorinsky + porosity + exact-difference force on the deviations h (in place).
+// Returns the density and the reported velocity u + F/(2 rho).
+template <int Q, class C>
+__device__ __forceinline__ void collide_fluid(C* h, C gamma, const Args& a, C& rho_o, C& urx, C& ury, C& urz) {
+  C drho, jx, jy, jz;
+  sums<Q, C>(h, drho, jx, jy, jz);
+  const C rho = C(1) + drho, ir = C(1) / rho;
+  const C ux = jx * ir, uy = jy * ir, uz = jz * ir;
+  const C usq = ux * ux + uy * uy + uz * uz;
+  C tau = C(a.tau0);
+  if (a.smag > 0.0) {
+    // Pi^neq = sum c c h - drho/3 I - rho u u (second moment of the 2nd-order equilibrium).
+    C sxx = 0, syy = 0, szz = 0, sxy = 0, sxz = 0, syz = 0;
+    sfor<0, Q>([&](auto I) {
+      constexpr int i = decltype(I)::value, cx = Lat<Q>::cx(i), cy = Lat<Q>::cy(i), cz = Lat<Q>::cz(i);
+      if (cx) sxx += h[i];
+      if (cy) syy += h[i];
+      if (cz) szz += h[i];
+      if (cx * cy) sxy += C(cx * cy) * h[i];
+      if (cx * cz) sxz += C(cx * cz) * h[i];
+      if (cy * cz) syz += C(cy * cz) * h[i];
+    });
+    const C d3 = drho * C(1.0 / 3.0);
+    const C pxx = sxx - d3 - rho * ux * ux, pyy = syy - d3 - rho * uy * uy, pzz = szz - d3 - rho * uz * uz;
+    const C pxy = sxy - rho * ux * uy, pxz = sxz - rho * ux * uz, pyz = syz - rho * uy * uz;
+    const C pn = sqrt(pxx * pxx + pyy * pyy + pzz * pzz + C(2) * (pxy * pxy + pxz * pxz + pyz * pyz));
+    const C t0 = C(a.tau0);
+    tau = C(0.5) * (t0 + sqrt(t0 * t0 + C(a.smag) * pn * ir));
+  }
+  const C k = C(1) - C(1) / tau;
+  const C vx = gamma * ux + C(a.fx) * ir, vy = gamma * uy + C(a.fy) * ir, vz = gamma * uz + C(a.fz) * ir;
+  const C vsq = vx * vx + vy * vy + vz * vz;
+  sfor<0, Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    const C eu = heq<Q, C, i>(drho, rho, ux, uy, uz, usq);
+    const C ev = heq<Q, C, i>(drho, rho, vx, vy, vz, vsq);
+    h[i] = ev + k * (h[i] - eu);
+  });
+  rho_o = rho;
+  const C hf = C(0.5) * ir;
+  urx = ux + C(a.fx) * hf;
+  ury = uy + C(a.fy) * hf;
+  urz = uz + C(a.fz) * hf;
+}
+
+// Regularised reconstruction: unknown populations (known(i) false) take the non-equilibrium part
+// of their opposite; all populations become f^eq + w_i/(2 cs^4) Q_i : Pi^neq.
+template <int Q, class C, class Known>
+__device__ __forceinline__ void regularise(C* h, C drho, C rho, C ux, C uy, C uz) {
+  const C usq = ux * ux + uy * uy + uz * uz;
+  C ne[Q];
+  sfor<0, Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    ne[i] = h[i] - heq<Q, C, i>(drho, rho, ux, uy, uz, usq);
+  });
+  sfor<0, Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    if constexpr (!Known{}(i)) ne[i] = ne[opp<Q>(i)];
+  });
+  C pxx = 0, pyy = 0, pzz = 0, pxy = 0, pxz = 0, pyz = 0;
+  sfor<0, Q>([&](auto I) {
+    constexpr int i = decltype(I)::value, cx = Lat<Q>::cx(i), cy = Lat<Q>::cy(i), cz = Lat<Q>::cz(i);
+    if (cx) pxx += ne[i];
+    if (cy) pyy += ne[i];
+    if (cz) pzz += ne[i];
+    if (cx * cy) pxy += C(cx * cy) * ne[i];
+    if (cx * cz) pxz += C(cx * cz) * ne[i];
+    if (cy * cz) pyz += C(cy * cz) * ne[i];
+  });
+  sfor<0, Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    h[i] = heq<Q, C, i>(drho, rho, ux, uy, uz, usq) +
+           wgt<Q, C>(i) * C(4.5) * qcontract<Q, C, i>(pxx, pyy, pzz, pxy, pxz, pyz);
+  });
+}
+
+template <int Q> struct KnownInlet { __host__ __device__ constexpr bool operator()(int i) const { return Lat<Q>::cx(i) <= 0; } };
+template <int Q> struct KnownOutlet { __host__ __device__ constexpr bool operator()(int i) const { return Lat<Q>::cx(i) >= 0; } };
+
+// Velocity inlet (inward normal +x): rho (1 - u_x) = sum_{c_x=0} f + 2 sum_{c_x<0} f.
+// With f = h + w and sum_{c_x=0} w + 2 sum_{c_x<0} w = 1 this is 1 + the same sums over h.
+template <int Q, class C>
+__device__ __forceinline__ void bc_inlet(C* h, C ubx, C uby, C ubz) {
+  C s = C(1);
+  sfor<0, Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    if (Lat<Q>::cx(i) == 0) s += h[i];
+    if (Lat<Q>::cx(i) < 0) s += C(2) * h[i];
+  });
+  const C rho = s / (C(1) - ubx);
+  regularise<Q, C, KnownInlet<Q>>(h, rho - C(1), rho, ubx, uby, ubz);
+}
+
+// Pressure outlet (inward normal -x): rho = rho_out, rho_out (1 + u_x) = sum_{c_x=0} f + 2 sum_{c_x>0} f,
+// tangential velocity 0.
+template <int Q, class C>
+__device__ __forceinline__ void bc_outlet(C* h, C rho_out) {
+  C s = C(1);
+  sfor<0, Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    if (Lat<Q>::cx(i) == 0) s += h[i];
+    if (Lat<Q>::cx(i) > 0) s += C(2) * h[i];
+  });
+  const C ux = s / rho_out - C(1);
+  regularise<Q, C, KnownOutlet<Q>>(h, rho_out - C(1), rho_out, ux, C(0), C(0));
+}
+
+// ---- Spalding wall function, Eq. (spaldingfunct) -----------------------------------------------------
+template <class C> __device__ __forceinline__ C cexp(C x) { return exp(x); }
+template <> __device__ __forceinline__ float cexp<float>(float x) { return expf(x); }
+template <class C> __device__ __forceinline__ C clog(C x) { return log(x); }
+template <> __device__ __forceinline__ float clog<float>(float x) { return logf(x); }
+
+template <class C> __device__ __forceinline__ C sp_y(C u, C k, C E) {
+  const C x = k * u;
+  return u + (cexp(x) - C(1) - x - x * x * C(0.5) - x * x * x * C(1.0 / 6.0)) / E;
+}
+template <class C> __device__ __forceinline__ C sp_dy(C u, C k, C E) {
+  const C x = k * u;
+  return C(1) + k * (cexp(x) - C(1) - x - x * x * C(0.5)) / E;
+}
+template <class C> __device__ __forceinline__ C newton_tol() { return std::is_same<C, double>::value ? C(1e-14) : C(1e-6); }
+
+// u+ with u+ * y+(u+) = Re; Newton from the right of the root (monotone for this convex function).
+template <class C> __device__ C sp_solve_re(C Re, C k, C E) {
+  if (!(Re > C(0))) return C(0);
+  C u = sqrt(Re);
+  if (k * u > C(10)) {
+    const C u1 = clog(C(2) * E * Re) / k;
+    if (u1 < u && u1 * sp_y(u1, k, E) - Re >= C(0)) u = u1;
+  }
+  for (int it = 0; it < 30; ++it) {
+    const C y = sp_y(u, k, E);
+    const C du = (u * y - Re) / (y + u * sp_dy(u, k, E));
+    u -= du;
+    if (fabs(du) <= newton_tol<C>() * fabs(u)) break;
+  }
+  return u;
+}
+// u+ with y+(u+) = yp.
+template <class C> __device__ C sp_solve_y(C yp, C k, C E) {
+  if (!(yp > C(0))) return C(0);
+  C u = yp;
+  if (k * u > C(10)) {
+    const C u1 = clog(C(2) * E * yp) / k;
+    if (u1 < u && sp_y(u1, k, E) - yp >= C(0)) u = u1;
+  }
+  for (int it = 0; it < 30; ++it) {
+    const C du = (sp_y(u, k, E) - yp) / sp_dy(u, k, E);
+    u -= du;
+    if (fabs(du) <= newton_tol<C>() * fabs(u)) break;
+  }
+  return u;
+}
+
+// Wall-model update of a WALL cell (sigma = 0, Sec. 2.2.1): from the reference velocity ur at
+// distance yw + 1 along the unit normal n, the solid velocity u^B and modelled shear du/dn; then
+// f* = f^eq(rho, u^B + F/rho) + (1 - 1/tau) f^(1,FD), f^(1,FD)_i = -(w_i rho tau / cs^2) Q_i : S,
+// S = (du/dn)/2 (t n^T + n t^T), tau = tau0 + 3 C_S^2 |du/dn|.
+template <int Q, class C>
+__device__ __forceinline__ void collide_wall(C* h, const Args& a, const C* nrm, C yw, const C* ur, bool has_ref, C& rho_o,
+                                             C& urx, C& ury, C& urz) {
+  C drho, jx, jy, jz;
+  sums<Q, C>(h, drho, jx, jy, jz);
+  const C rho = C(1) + drho, ir = C(1) / rho;
+  rho_o = rho;
+  const C hf = C(0.5) * ir;
+  urx = jx * ir + C(a.fx) * hf;
+  ury = jy * ir + C(a.fy) * hf;
+  urz = jz * ir + C(a.fz) * hf;
+  C ubx = 0, uby = 0, ubz = 0, dudn = 0, tx = 0, ty = 0, tz = 0;
+  const C nx = nrm[0], ny = nrm[1], nz = nrm[2];
+  if (has_ref && (nx != C(0) || ny != C(0) || nz != C(0))) {
+    const C un = ur[0] * nx + ur[1] * ny + ur[2] * nz;
+    const C utx = ur[0] - un * nx, uty = ur[1] - un * ny, utz = ur[2] - un * nz;
+    const C U = sqrt(utx * utx + uty * uty + utz * utz);
+    if (U >= C(1e-12)) {
+      tx = utx / U; ty = uty / U; tz = utz / U;
+      const C k = C(a.kappa), E = C(a.E);
+      const C nu = (C(a.tau0) - C(0.5)) * C(1.0 / 3.0);
+      const C upr = sp_solve_re<C>(U * (yw + C(1)) / nu, k, E);
+      const C utau = U / upr;
+      const C upw = sp_solve_y<C>(yw * utau / nu, k, E);
+      const C ub = utau * upw;
+      ubx = ub * tx; uby = ub * ty; ubz = ub * tz;
+      dudn = (utau * utau / nu) / sp_dy<C>(upw, k, E);
+    }
+  }
+  const C tau = C(a.tau0) + C(3) * C(a.cs2smag) * fabs(dudn);
+  const C hd = C(0.5) * dudn;
+  const C sxx = hd * C(2) * tx * nx, syy = hd * C(2) * ty * ny, szz = hd * C(2) * tz * nz;
+  const C sxy = hd * (tx * ny + nx * ty), sxz = hd * (tx * nz + nx * tz), syz = hd * (ty * nz + ny * tz);
+  const C vx = ubx + C(a.fx) * ir, vy = uby + C(a.fy) * ir, vz = ubz + C(a.fz) * ir;
+  const C vsq = vx * vx + vy * vy + vz * vz;
+  const C g = -C(3) * rho * (tau - C(1));  // (1 - 1/tau) * (-rho tau / cs^2)
+  sfor<0, Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    h[i] = heq<Q, C, i>(drho, rho, vx, vy, vz, vsq) + g * wgt<Q, C>(i) * qcontract<Q, C, i>(sxx, syy, szz, sxy, sxz, syz);
+  });
+}
+
+template <class C> __device__ __forceinline__ bool finite_all(C a, C b, C c, C d) {
+  return fabs(a) + fabs(b) + fabs(c) + fabs(d) < C(1e30);
+}
+
+}  // namespace lbm

@@ -1,0 +1,255 @@
+// One-time integer work on the geometry: cell classification, wall-model reference cells, the
+// ascending boundary-cell list (warp ballots and per-block offsets), the list's integer wall-normal
+// sums and reference positions, and the debug source map. All results are exact integers.
+#include "lbm_device.cuh"
+#include "lbm_ops.h"
+
+namespace lbm {
+namespace {
+
+constexpr int CELLS_PER_BLOCK = 256;
+
+struct Pos {
+  int x, y, z;
+  int crossed;  // non-periodic faces beyond which the position lies (bit f for face f)
+};
+
+__device__ __forceinline__ Pos wrap(const GeoArgs& g, int x, int y, int z) {
+  Pos p{x, y, z, 0};
+  if (p.x < 0) { if (g.face[0] == F_PERIODIC) p.x += g.nx; else p.crossed |= 1; }
+  else if (p.x >= g.nx) { if (g.face[1] == F_PERIODIC) p.x -= g.nx; else p.crossed |= 2; }
+  if (p.y < 0) { if (g.face[2] == F_PERIODIC) p.y += g.ny; else p.crossed |= 4; }
+  else if (p.y >= g.ny) { if (g.face[3] == F_PERIODIC) p.y -= g.ny; else p.crossed |= 8; }
+  if (p.z < 0) { if (g.face[4] == F_PERIODIC) p.z += g.nz; else p.crossed |= 16; }
+  else if (p.z >= g.nz) { if (g.face[5] == F_PERIODIC) p.z -= g.nz; else p.crossed |= 32; }
+  return p;
+}
+
+__device__ __forceinline__ long long lin(const GeoArgs& g, const Pos& p) {
+  return p.x + (long long)g.nx * p.y + g.nxy * p.z;
+}
+
+__device__ __forceinline__ bool beyond_wall_face(const GeoArgs& g, int crossed) {
+  bool w = false;
+#pragma unroll
+  for (int f = 0; f < 6; ++f)
+    if ((crossed >> f & 1) && g.face[f] == F_WALL) w = true;
+  return w;
+}
+
+__device__ __forceinline__ void coords(const GeoArgs& g, long long n, int& x, int& y, int& z) {
+  const long long r = n / g.nx;
+  x = int(n - r * g.nx);
+  z = int(r / g.ny);
+  y = int(r - (long long)z * g.ny);
+}
+
+// Integer wall-normal sum v = sum over solid-like neighbours x + c_i of W_i c_i, from the type bytes.
+template <int Q>
+__device__ __forceinline__ void normal_sum(const GeoArgs& g, const uint8_t* type, int x, int y, int z, int v[3]) {
+  v[0] = v[1] = v[2] = 0;
+  sfor<1, Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    const Pos p = wrap(g, x + Lat<Q>::cx(i), y + Lat<Q>::cy(i), z + Lat<Q>::cz(i));
+    const bool solid = p.crossed ? beyond_wall_face(g, p.crossed) : ((type[lin(g, p)] & T_KIND) == K_SOLID);
+    if (solid) {
+      v[0] += Lat<Q>::W(i) * Lat<Q>::cx(i);
+      v[1] += Lat<Q>::W(i) * Lat<Q>::cy(i);
+      v[2] += Lat<Q>::W(i) * Lat<Q>::cz(i);
+    }
+  });
+}
+
+// Reference cell of a WALL cell: one step along the dominant axis of n = -v (ties: lowest axis);
+// -1 when v = 0, or the cell lies outside the domain or is solid.
+__device__ __forceinline__ long long ref_cell(const GeoArgs& g, const uint8_t* type, int x, int y, int z, const int v[3]) {
+  if (v[0] == 0 && v[1] == 0 && v[2] == 0) return -1;
+  int a = 0;
+  if (abs(v[1]) > abs(v[a])) a = 1;
+  if (abs(v[2]) > abs(v[a])) a = 2;
+  int d[3] = {0, 0, 0};
+  d[a] = v[a] > 0 ? -1 : 1;
+  const Pos p = wrap(g, x + d[0], y + d[1], z + d[2]);
+  if (p.crossed) return -1;
+  const long long r = lin(g, p);
+  if ((type[r] & T_KIND) == K_SOLID) return -1;
+  return r;
+}
+
+template <int Q>
+__global__ void k_classify(const GeoArgs g, const uint8_t* mask, uint8_t* type, unsigned* status) {
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= g.N) return;
+  int x, y, z;
+  coords(g, n, x, y, z);
+  uint8_t m = mask[n];
+  if (!(m == 0 || m == 1 || m == 3 || m == 4)) {
+    atomicOr(status, ST_BADMASK);
+    m = 0;
+  }
+  if (m == 1) { type[n] = K_SOLID; return; }
+  bool wall = false, near = false;
+  sfor<1, Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    // neighbour x + c_i (solid neighbour => WALL)
+    const Pos p = wrap(g, x + Lat<Q>::cx(i), y + Lat<Q>::cy(i), z + Lat<Q>::cz(i));
+    if (p.crossed) {
+      near = true;
+      if (beyond_wall_face(g, p.crossed)) wall = true;
+    } else if (mask[lin(g, p)] == 1) {
+      wall = true;
+      near = true;
+    }
+  });
+  uint8_t kind = m == 3 ? K_INFLOW : m == 4 ? K_OUTFLOW : (wall ? K_WALL : K_FLUID);
+  type[n] = kind | (near ? T_NEAR : 0);
+}
+
+template <int Q>
+__global__ void k_mark_ref(const GeoArgs g, uint8_t* type) {
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= g.N) return;
+  if ((type[n] & T_KIND) != K_WALL) return;
+  int x, y, z;
+  coords(g, n, x, y, z);
+  int v[3];
+  normal_sum<Q>(g, type, x, y, z, v);
+  const long long r = ref_cell(g, type, x, y, z, v);
+  if (r < 0) return;
+  unsigned* word = reinterpret_cast<unsigned*>(type + (r & ~3LL));
+  atomicOr(word, unsigned(T_REF) << (8 * (r & 3)));
+}
+
+__device__ __forceinline__ bool on_list(uint8_t t) {
+  const int k = t & T_KIND;
+  return k == K_WALL || k == K_INFLOW || k == K_OUTFLOW || (t & T_REF);
+}
+
+__global__ void k_list_count(const GeoArgs g, uint8_t* type, int* counts) {
+  const long long n = blockIdx.x * (long long)CELLS_PER_BLOCK + threadIdx.x;
+  bool f = false;
+  if (n < g.N) {
+    const uint8_t t = type[n];
+    f = on_list(t);
+    if (f) type[n] = t | T_LIST;
+  }
+  const int c = __syncthreads_count(f);
+  if (threadIdx.x == 0) counts[blockIdx.x] = c;
+}
+
+__global__ void k_list_write(const GeoArgs g, const uint8_t* type, const int* offsets, long long* lcell) {
+  __shared__ int wcount[CELLS_PER_BLOCK / 32];
+  const long long n = blockIdx.x * (long long)CELLS_PER_BLOCK + threadIdx.x;
+  const bool f = n < g.N && (type[n] & T_LIST);
+  const unsigned b = __ballot_sync(0xffffffffu, f);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) wcount[w] = __popc(b);
+  __syncthreads();
+  int base = offsets[blockIdx.x];
+  for (int i = 0; i < w; ++i) base += wcount[i];
+  if (f) lcell[base + __popc(b & ((1u << lane) - 1u))] = n;
+}
+
+template <int Q>
+__global__ void k_list_meta(const GeoArgs g, const uint8_t* type, const long long* lcell, int n_list, int* nsum, int* wref) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_list) return;
+  const long long n = lcell[k];
+  nsum[3 * k] = nsum[3 * k + 1] = nsum[3 * k + 2] = 0;
+  wref[k] = -1;
+  if ((type[n] & T_KIND) != K_WALL) return;
+  int x, y, z;
+  coords(g, n, x, y, z);
+  int v[3];
+  normal_sum<Q>(g, type, x, y, z, v);
+  nsum[3 * k] = v[0];
+  nsum[3 * k + 1] = v[1];
+  nsum[3 * k + 2] = v[2];
+  const long long r = ref_cell(g, type, x, y, z, v);
+  if (r < 0) return;
+  int lo = 0, hi = n_list - 1;  // the reference cell is on the (ascending) list
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (lcell[mid] < r) lo = mid + 1;
+    else hi = mid;
+  }
+  wref[k] = (lcell[lo] == r) ? lo : -1;
+}
+
+template <int Q>
+__global__ void k_source_map(const Args a, int64_t* sdir, int64_t* scell) {
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= a.N) return;
+  const bool solid = (a.type[n] & T_KIND) == K_SOLID;
+  const long long r = n / a.nx;
+  const int x = int(n - r * a.nx), z = int(r / a.ny), y = int(r - (long long)z * a.ny);
+  sfor<0, Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    if (solid) {
+      sdir[(long long)i * a.N + n] = -1;
+      scell[(long long)i * a.N + n] = -1;
+      return;
+    }
+    int p;
+    long long m;
+    slot_of<Q>(a, x, y, z, n, i, p, m);
+    // after an even step slot (p, m) holds f*_opp(p)(m)
+    sdir[(long long)i * a.N + n] = opp<Q>(p);
+    scell[(long long)i * a.N + n] = m;
+  });
+}
+
+__global__ void k_reduce_final(const double* partial, int nblk, double* out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double s[4] = {0, 0, 0, 0};
+  for (int b = 0; b < nblk; ++b)
+    for (int c = 0; c < 4; ++c) s[c] += partial[4 * b + c];
+  for (int c = 0; c < 4; ++c) out[c] = s[c];
+}
+
+inline unsigned nblocks(long long n, int t) { return unsigned((n + t - 1) / t); }
+
+}  // namespace
+
+void geo_classify(const GeoArgs& g, const uint8_t* mask, uint8_t* type, unsigned* status, cudaStream_t s) {
+  if (g.q == 19) k_classify<19><<<nblocks(g.N, 256), 256, 0, s>>>(g, mask, type, status);
+  else k_classify<27><<<nblocks(g.N, 256), 256, 0, s>>>(g, mask, type, status);
+}
+
+void geo_mark_ref(const GeoArgs& g, uint8_t* type, cudaStream_t s) {
+  if (g.q == 19) k_mark_ref<19><<<nblocks(g.N, 256), 256, 0, s>>>(g, type);
+  else k_mark_ref<27><<<nblocks(g.N, 256), 256, 0, s>>>(g, type);
+}
+
+int geo_count_blocks(const GeoArgs& g) { return int(nblocks(g.N, CELLS_PER_BLOCK)); }
+
+void geo_list_count(const GeoArgs& g, uint8_t* type, int* counts, cudaStream_t s) {
+  k_list_count<<<nblocks(g.N, CELLS_PER_BLOCK), CELLS_PER_BLOCK, 0, s>>>(g, type, counts);
+}
+
+void geo_list_write(const GeoArgs& g, const uint8_t* type, const int* offsets, long long* lcell, cudaStream_t s) {
+  k_list_write<<<nblocks(g.N, CELLS_PER_BLOCK), CELLS_PER_BLOCK, 0, s>>>(g, type, offsets, lcell);
+}
+
+void geo_list_meta(const GeoArgs& g, const uint8_t* type, const long long* lcell, int n_list, int* nsum, int* wref,
+                   cudaStream_t s) {
+  if (n_list <= 0) return;
+  if (g.q == 19) k_list_meta<19><<<nblocks(n_list, 128), 128, 0, s>>>(g, type, lcell, n_list, nsum, wref);
+  else k_list_meta<27><<<nblocks(n_list, 128), 128, 0, s>>>(g, type, lcell, n_list, nsum, wref);
+}
+
+void geo_source_map(const GeoArgs& g, const uint8_t* type, int64_t* sdir, int64_t* scell, cudaStream_t s) {
+  Args a{};
+  a.type = type;
+  a.nx = g.nx; a.ny = g.ny; a.nz = g.nz;
+  a.nxy = g.nxy; a.N = g.N;
+  for (int f = 0; f < 6; ++f) a.face[f] = g.face[f];
+  if (g.q == 19) k_source_map<19><<<nblocks(g.N, 128), 128, 0, s>>>(a, sdir, scell);
+  else k_source_map<27><<<nblocks(g.N, 128), 128, 0, s>>>(a, sdir, scell);
+}
+
+void reduce_final(const double* partial, int nblk, double* out, cudaStream_t s) {
+  k_reduce_final<<<1, 32, 0, s>>>(partial, nblk, out);
+}
+
+}  // namespace lbm

@@ -1,0 +1,568 @@
+// Kernel templates of the fused collide-and-stream step and of the state access, reduction and
+// adjoint passes. Instantiated per storage type in lbm_ops_<storage>.cu.
+#pragma once
+
+#include "lbm_device.cuh"
+#include "lbm_adjoint.cuh"
+#include "lbm_ops.h"
+
+namespace lbm {
+
+constexpr int BULK_THREADS = 128;
+constexpr int LIST_THREADS = 128;
+
+enum { LOAD_LOCAL = 0, LOAD_SLOTS = 1 };
+enum { STORE_MIRROR = 0, STORE_SLOTS = 1 };
+
+__device__ __forceinline__ void cell_coords(const Args& a, long long n, int& x, int& y, int& z) {
+  const long long r = n / a.nx;
+  x = int(n - r * a.nx);
+  z = int(r / a.ny);
+  y = int(r - (long long)z * a.ny);
+}
+
+template <class C> __device__ __forceinline__ C gamma_at(const Args& a, long long n) {
+  return a.gamma ? static_cast<const C*>(a.gamma)[n] : C(1);
+}
+
+// Gather the Q deviations of cell n. LOAD_LOCAL: h_i from slot (i, n) of src (natural layout);
+// LOAD_SLOTS: h_i from the AA slot of direction i (state after an even step).
+template <int Q, class S, int LOAD>
+__device__ __forceinline__ void gather(const Args& a, const S* src, int x, int y, int z, long long n, bool near,
+                                       typename Codec<S>::C* h) {
+  using C = typename Codec<S>::C;
+  if constexpr (LOAD == LOAD_LOCAL) {
+    sfor<0, Q>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      h[i] = Codec<S>::ld(src + (long long)i * a.stride + n);
+    });
+  } else {
+    if (!near) {
+      const int xm = x == 0 ? a.nx - 1 : x - 1, xp = x == a.nx - 1 ? 0 : x + 1;
+      const long long y0 = (long long)y * a.nx;
+      const long long ym = (long long)(y == 0 ? a.ny - 1 : y - 1) * a.nx, yp = (long long)(y == a.ny - 1 ? 0 : y + 1) * a.nx;
+      const long long z0 = (long long)z * a.nxy;
+      const long long zm = (long long)(z == 0 ? a.nz - 1 : z - 1) * a.nxy, zp = (long long)(z == a.nz - 1 ? 0 : z + 1) * a.nxy;
+      sfor<0, Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        constexpr int dx = -Lat<Q>::cx(i), dy = -Lat<Q>::cy(i), dz = -Lat<Q>::cz(i);
+        const long long s = (dx < 0 ? xm : dx > 0 ? xp : x) + (dy < 0 ? ym : dy > 0 ? yp : y0) + (dz < 0 ? zm : dz > 0 ? zp : z0);
+        h[i] = Codec<S>::ld(src + (long long)opp<Q>(i) * a.stride + s);
+      });
+    } else {
+      sfor<0, Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        int p;
+        long long m;
+        slot_of<Q>(a, x, y, z, n, i, p, m);
+        h[i] = Codec<S>::ld(src + (long long)p * a.stride + m);
+      });
+    }
+  }
+}
+
+// Write the post-collision deviations h*. STORE_MIRROR: h*_i into slot (opp(i), n) of dst (even
+// step); STORE_SLOTS: h*_opp(i) into the AA slot of direction i (odd step, or out-of-place push
+// into a natural-layout array).
+template <int Q, class S, int STORE>
+__device__ __forceinline__ void scatter(const Args& a, S* dst, int x, int y, int z, long long n, bool near,
+                                        const typename Codec<S>::C* h) {
+  if constexpr (STORE == STORE_MIRROR) {
+    sfor<0, Q>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      Codec<S>::st(dst + (long long)opp<Q>(i) * a.stride + n, h[i]);
+    });
+  } else {
+    if (!near) {
+      const int xm = x == 0 ? a.nx - 1 : x - 1, xp = x == a.nx - 1 ? 0 : x + 1;
+      const long long y0 = (long long)y * a.nx;
+      const long long ym = (long long)(y == 0 ? a.ny - 1 : y - 1) * a.nx, yp = (long long)(y == a.ny - 1 ? 0 : y + 1) * a.nx;
+      const long long z0 = (long long)z * a.nxy;
+      const long long zm = (long long)(z == 0 ? a.nz - 1 : z - 1) * a.nxy, zp = (long long)(z == a.nz - 1 ? 0 : z + 1) * a.nxy;
+      sfor<0, Q>([&](auto I) {
+        constexpr int k = decltype(I)::value;  // outgoing direction: f*_k goes to slot (k, x + c_k)
+        constexpr int dx = Lat<Q>::cx(k), dy = Lat<Q>::cy(k), dz = Lat<Q>::cz(k);
+        const long long s = (dx < 0 ? xm : dx > 0 ? xp : x) + (dy < 0 ? ym : dy > 0 ? yp : y0) + (dz < 0 ? zm : dz > 0 ? zp : z0);
+        Codec<S>::st(dst + (long long)k * a.stride + s, h[k]);
+      });
+    } else {
+      sfor<0, Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        int p;
+        long long m;
+        slot_of<Q>(a, x, y, z, n, i, p, m);
+        Codec<S>::st(dst + (long long)p * a.stride + m, h[opp<Q>(i)]);
+      });
+    }
+  }
+}
+
+template <class C> __device__ __forceinline__ const C* cptr(const void* p) { return static_cast<const C*>(p); }
+template <class C> __device__ __forceinline__ C* cptr(void* p) { return static_cast<C*>(p); }
+
+// Boundary reconstruction of INFLOW/OUTFLOW cells (in place on h).
+template <int Q, class C>
+__device__ __forceinline__ void apply_bc(const Args& a, int kind, int y, int z, C* h) {
+  if (kind == K_INFLOW) {
+    const C* ub = cptr<C>(a.uin);
+    const long long pl = (long long)a.ny * a.nz, p = y + (long long)a.ny * z;
+    bc_inlet<Q, C>(h, ub[p], ub[pl + p], ub[2 * pl + p]);
+  } else if (kind == K_OUTFLOW) {
+    bc_outlet<Q, C>(h, C(a.rho_out));
+  }
+}
+
+// Collision of a cell of any non-solid kind (boundary reconstruction first, then fluid or wall
+// model). k = list entry for reference-velocity bookkeeping (-1: not a list cell).
+template <int Q, class C>
+__device__ __forceinline__ void collide_any(const Args& a, int kind, uint8_t t, int y, int z, long long n, int k, C* h) {
+  apply_bc<Q, C>(a, kind, y, z, h);
+  C rho, urx, ury, urz;
+  if (kind == K_WALL && a.wm) {
+    const C* nr = cptr<C>(a.wnrm) + 3 * (long long)k;
+    const int r = a.wref[k];
+    const C* ur = r >= 0 ? cptr<C>(a.ref_rd) + 3 * (long long)r : nullptr;
+    C z3[3] = {C(0), C(0), C(0)};
+    collide_wall<Q, C>(h, a, nr, cptr<C>(a.wyw)[k], r >= 0 ? ur : z3, r >= 0, rho, urx, ury, urz);
+  } else {
+    collide_fluid<Q, C>(h, gamma_at<C>(a, n), a, rho, urx, ury, urz);
+  }
+  if ((t & T_REF) && k >= 0) {
+    C* w = cptr<C>(a.ref_wr) + 3 * (long long)k;
+    w[0] = urx; w[1] = ury; w[2] = urz;
+  }
+  if (!finite_all<C>(rho, urx, ury, urz)) atomicOr(a.status, ST_NAN);
+}
+
+// ---- the step kernels ----------------------------------------------------------------------------------
+// Interior kernel: every FLUID cell that is not on the boundary list. Threads map to (x, y, z).
+template <int Q, class S, bool ODD>
+__global__ void __launch_bounds__(BULK_THREADS) k_bulk(const Args a) {
+  using C = typename Codec<S>::C;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= a.nx || y >= a.ny) return;
+  const long long n = x + (long long)y * a.nx + (long long)z * a.nxy;
+  const uint8_t t = a.type[n];
+  if (t & (T_LIST | T_KIND)) return;
+  S* f = static_cast<S*>(a.f);
+  const bool near = (t & T_NEAR) != 0;
+  C h[Q];
+  gather<Q, S, ODD ? LOAD_SLOTS : LOAD_LOCAL>(a, f, x, y, z, n, near, h);
+  C rho, urx, ury, urz;
+  collide_fluid<Q, C>(h, gamma_at<C>(a, n), a, rho, urx, ury, urz);
+  if (!finite_all<C>(rho, urx, ury, urz)) atomicOr(a.status, ST_NAN);
+  scatter<Q, S, ODD ? STORE_SLOTS : STORE_MIRROR>(a, f, x, y, z, n, near, h);
+}
+
+// Boundary-list kernel: WALL, INFLOW, OUTFLOW and reference cells, one thread per list entry.
+template <int Q, class S, bool ODD>
+__global__ void __launch_bounds__(LIST_THREADS) k_list(const Args a) {
+  using C = typename Codec<S>::C;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= a.n_list) return;
+  const long long n = a.lcell[k];
+  int x, y, z;
+  cell_coords(a, n, x, y, z);
+  const uint8_t t = a.type[n];
+  const int kind = t & T_KIND;
+  S* f = static_cast<S*>(a.f);
+  const bool near = (t & T_NEAR) != 0;
+  C h[Q];
+  gather<Q, S, ODD ? LOAD_SLOTS : LOAD_LOCAL>(a, f, x, y, z, n, near, h);
+  collide_any<Q, C>(a, kind, t, y, z, n, k, h);
+  scatter<Q, S, ODD ? STORE_SLOTS : STORE_MIRROR>(a, f, x, y, z, n, near, h);
+}
+
+// Out-of-place step for the adjoint's recomputation: natural-layout state fin -> natural-layout fout.
+// Handles every cell kind (the wall model is excluded by the host).
+template <int Q, class S>
+__global__ void __launch_bounds__(BULK_THREADS) k_step_oop(const Args a, const S* __restrict__ fin, S* __restrict__ fout) {
+  using C = typename Codec<S>::C;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= a.nx || y >= a.ny) return;
+  const long long n = x + (long long)y * a.nx + (long long)z * a.nxy;
+  const uint8_t t = a.type[n];
+  const int kind = t & T_KIND;
+  if (kind == K_SOLID) return;
+  const bool near = (t & T_NEAR) != 0;
+  C h[Q];
+  gather<Q, S, LOAD_LOCAL>(a, fin, x, y, z, n, near, h);
+  apply_bc<Q, C>(a, kind, y, z, h);
+  C rho, urx, ury, urz;
+  collide_fluid<Q, C>(h, gamma_at<C>(a, n), a, rho, urx, ury, urz);
+  if (!finite_all<C>(rho, urx, ury, urz)) atomicOr(a.status, ST_NAN);
+  scatter<Q, S, STORE_SLOTS>(a, fout, x, y, z, n, near, h);
+}
+
+// ---- state access ------------------------------------------------------------------------------------
+template <class C> __device__ __forceinline__ C load_in(const void* p, int dtype, long long i) {
+  return dtype == 0 ? C(static_cast<const double*>(p)[i]) : C(static_cast<const float*>(p)[i]);
+}
+__device__ __forceinline__ void store_out(void* p, int dtype, long long i, double v) {
+  if (dtype == 0) static_cast<double*>(p)[i] = v;
+  else static_cast<float*>(p)[i] = float(v);
+}
+
+template <int Q, class S>
+__global__ void k_init_eq(const Args a, const void* rho, const void* u, int dtype) {
+  using C = typename Codec<S>::C;
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= a.N) return;
+  S* f = static_cast<S*>(a.f);
+  const bool solid = (a.type[n] & T_KIND) == K_SOLID;
+  const C r = load_in<C>(rho, dtype, n);
+  const C ux = load_in<C>(u, dtype, n), uy = load_in<C>(u, dtype, a.N + n), uz = load_in<C>(u, dtype, 2 * a.N + n);
+  const C usq = ux * ux + uy * uy + uz * uz;
+  sfor<0, Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    const C v = solid ? C(0) : heq<Q, C, i>(r - C(1), r, ux, uy, uz, usq);
+    Codec<S>::st(f + (long long)i * a.stride + n, v);
+  });
+}
+
+// Reported macroscopic state of cell n: boundary reconstruction, rho, u = j/rho + F/(2 rho).
+template <int Q, class S>
+__device__ __forceinline__ void cell_macro(const Args& a, long long n, bool swapped, typename Codec<S>::C& rho,
+                                           typename Codec<S>::C* u) {
+  using C = typename Codec<S>::C;
+  int x, y, z;
+  cell_coords(a, n, x, y, z);
+  const uint8_t t = a.type[n];
+  const S* f = static_cast<const S*>(a.f);
+  C h[Q];
+  if (swapped) gather<Q, S, LOAD_SLOTS>(a, f, x, y, z, n, true, h);
+  else gather<Q, S, LOAD_LOCAL>(a, f, x, y, z, n, false, h);
+  apply_bc<Q, C>(a, t & T_KIND, y, z, h);
+  C drho, jx, jy, jz;
+  sums<Q, C>(h, drho, jx, jy, jz);
+  rho = C(1) + drho;
+  const C ir = C(1) / rho, hf = C(0.5) * ir;
+  u[0] = jx * ir + C(a.fx) * hf;
+  u[1] = jy * ir + C(a.fy) * hf;
+  u[2] = jz * ir + C(a.fz) * hf;
+}
+
+template <int Q, class S>
+__global__ void k_moments(const Args a, int swapped, void* rho, void* u, int dtype) {
+  using C = typename Codec<S>::C;
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= a.N) return;
+  if ((a.type[n] & T_KIND) == K_SOLID) {
+    store_out(rho, dtype, n, 0.0);
+    for (int c = 0; c < 3; ++c) store_out(u, dtype, c * a.N + n, 0.0);
+    return;
+  }
+  C r, uu[3];
+  cell_macro<Q, S>(a, n, swapped != 0, r, uu);
+  store_out(rho, dtype, n, double(r));
+  for (int c = 0; c < 3; ++c) store_out(u, dtype, c * a.N + n, double(uu[c]));
+}
+
+template <int Q, class S>
+__global__ void k_get_pops(const Args a, int swapped, void* out, int dtype) {
+  using C = typename Codec<S>::C;
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= a.N) return;
+  if ((a.type[n] & T_KIND) == K_SOLID) {
+    sfor<0, Q>([&](auto I) { store_out(out, dtype, (long long)I * a.N + n, 0.0); });
+    return;
+  }
+  int x, y, z;
+  cell_coords(a, n, x, y, z);
+  const S* f = static_cast<const S*>(a.f);
+  C h[Q];
+  if (swapped) gather<Q, S, LOAD_SLOTS>(a, f, x, y, z, n, true, h);
+  else gather<Q, S, LOAD_LOCAL>(a, f, x, y, z, n, false, h);
+  sfor<0, Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    store_out(out, dtype, (long long)i * a.N + n, double(h[i]) + double(Lat<Q>::W(i)) / double(Lat<Q>::Wden));
+  });
+}
+
+template <int Q, class S>
+__global__ void k_set_pops(const Args a, int swapped, const void* in, int dtype) {
+  using C = typename Codec<S>::C;
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= a.N) return;
+  if ((a.type[n] & T_KIND) == K_SOLID) return;
+  int x, y, z;
+  cell_coords(a, n, x, y, z);
+  S* f = static_cast<S*>(a.f);
+  sfor<0, Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    const double v = dtype == 0 ? static_cast<const double*>(in)[(long long)i * a.N + n]
+                                : double(static_cast<const float*>(in)[(long long)i * a.N + n]);
+    const C hv = C(v - double(Lat<Q>::W(i)) / double(Lat<Q>::Wden));
+    if (swapped) {
+      int p;
+      long long m;
+      slot_of<Q>(a, x, y, z, n, i, p, m);
+      Codec<S>::st(f + (long long)p * a.stride + m, hv);
+    } else {
+      Codec<S>::st(f + (long long)i * a.stride + n, hv);
+    }
+  });
+}
+
+// Reference buffer from the current state: entry k of a reference cell gets its reported velocity.
+template <int Q, class S>
+__global__ void k_ref_fill(const Args a, int swapped, void* ref) {
+  using C = typename Codec<S>::C;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= a.n_list) return;
+  const long long n = a.lcell[k];
+  C* r = cptr<C>(ref) + 3 * (long long)k;
+  if (!(a.type[n] & T_REF)) { r[0] = r[1] = r[2] = C(0); return; }
+  C rho, u[3];
+  cell_macro<Q, S>(a, n, swapped != 0, rho, u);
+  r[0] = u[0]; r[1] = u[1]; r[2] = u[2];
+}
+
+// FP64 mass and momentum: grid-stride accumulation per thread, warp shuffles, one partial per block.
+template <int Q, class S>
+__global__ void __launch_bounds__(256) k_reduce(const Args a, int swapped, double* partial) {
+  using C = typename Codec<S>::C;
+  double s[4] = {0, 0, 0, 0};
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < a.N; n += (long long)gridDim.x * blockDim.x) {
+    if ((a.type[n] & T_KIND) == K_SOLID) continue;
+    C r, u[3];
+    cell_macro<Q, S>(a, n, swapped != 0, r, u);
+    const double rd = double(r);
+    s[0] += rd;
+    s[1] += rd * double(u[0]);
+    s[2] += rd * double(u[1]);
+    s[3] += rd * double(u[2]);
+  }
+  __shared__ double sm[8][4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+    for (int o = 16; o > 0; o >>= 1) s[c] += __shfl_down_sync(0xffffffffu, s[c], o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0)
+    for (int c = 0; c < 4; ++c) sm[w][c] = s[c];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int c = 0; c < 4; ++c) {
+      double t = 0;
+      for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += sm[i][c];
+      partial[4 * (long long)blockIdx.x + c] = t;
+    }
+  }
+}
+
+// Wall normals and distances of the list entries from the integer normal sums.
+template <class C>
+__global__ void k_list_aux(const Args a, const int* nsum, const float* wall_dist, C* wnrm, C* wyw) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= a.n_list) return;
+  const long long n = a.lcell[k];
+  const int v0 = nsum[3 * k], v1 = nsum[3 * k + 1], v2 = nsum[3 * k + 2];
+  const C vn = sqrt(C(v0) * C(v0) + C(v1) * C(v1) + C(v2) * C(v2));
+  if (vn > C(0)) {
+    wnrm[3 * k] = -C(v0) / vn;
+    wnrm[3 * k + 1] = -C(v1) / vn;
+    wnrm[3 * k + 2] = -C(v2) / vn;
+  } else {
+    wnrm[3 * k] = wnrm[3 * k + 1] = wnrm[3 * k + 2] = C(0);
+  }
+  wyw[k] = wall_dist ? C(wall_dist[n]) : C(0.5);
+}
+
+// Objective plane sums: acc += wa * sum_{x=xa} rho + wb * sum_{x=xb} rho over non-solid cells
+// (one block, fixed summation order).
+template <int Q, class S>
+__global__ void __launch_bounds__(1024) k_plane_rho(const Args a, const S* state, int swapped, int xa, int xb, double* acc,
+                                                    double wa, double wb) {
+  using C = typename Codec<S>::C;
+  Args b = a;
+  b.f = const_cast<S*>(state);
+  const long long pl = (long long)a.ny * a.nz;
+  double s = 0.0;
+  for (long long q = threadIdx.x; q < 2 * pl; q += blockDim.x) {
+    const int which = q >= pl;
+    const long long p = which ? q - pl : q;
+    const int y = int(p % a.ny), z = int(p / a.ny);
+    const long long n = (which ? xb : xa) + (long long)y * a.nx + (long long)z * a.nxy;
+    if ((a.type[n] & T_KIND) == K_SOLID) continue;
+    C h[Q];
+    if (swapped) gather<Q, S, LOAD_SLOTS>(b, state, which ? xb : xa, y, z, n, true, h);
+    else gather<Q, S, LOAD_LOCAL>(b, state, which ? xb : xa, y, z, n, false, h);
+    C drho = C(0);
+    sfor<0, Q>([&](auto I) { drho += h[I]; });
+    s += (which ? wb : wa) * (1.0 + double(drho));
+  }
+  __shared__ double sm[32];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += sm[i];
+    *acc += t;
+  }
+}
+
+// ---- adjoint reverse step ---------------------------------------------------------------------------------
+// lam_out(n) = (d f*(n) / d f(n))^T mu(n) (+ objective weights), mu_k(n) = lam_in at the slot that
+// f*_k(n) streams into; gamma and inlet-velocity sensitivities accumulate in C precision.
+template <int Q, class S>
+__global__ void __launch_bounds__(BULK_THREADS) k_reverse(const Args a, const AdjArgs d) {
+  using C = typename Codec<S>::C;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= a.nx || y >= a.ny) return;
+  const long long n = x + (long long)y * a.nx + (long long)z * a.nxy;
+  const uint8_t t = a.type[n];
+  const int kind = t & T_KIND;
+  C* lo = cptr<C>(d.lam_out);
+  if (kind == K_SOLID) {
+    sfor<0, Q>([&](auto I) { lo[(long long)I * a.stride + n] = C(0); });
+    return;
+  }
+  const bool near = (t & T_NEAR) != 0;
+  // mu_opp(i) from slot of direction i (where f*_opp(i) went), read from the natural-layout lam_in
+  const C* li = cptr<C>(d.lam_in);
+  C mu[Q];
+  {
+    C tmp[Q];
+    gather<Q, C, LOAD_SLOTS>(a, li, x, y, z, n, near, tmp);
+    sfor<0, Q>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      mu[opp<Q>(i)] = tmp[i];
+    });
+  }
+  C h[Q];
+  gather<Q, S, LOAD_LOCAL>(a, static_cast<const S*>(d.fst), x, y, z, n, false, h);
+  C lam[Q], ggam = C(0), gub[3] = {C(0), C(0), C(0)};
+  const C gam = gamma_at<C>(a, n);
+  if (kind == K_INFLOW || kind == K_OUTFLOW) {
+    C hb[Q];
+    sfor<0, Q>([&](auto I) { hb[I] = h[I]; });
+    apply_bc<Q, C>(a, kind, y, z, hb);
+    C gh[Q];
+    collide_fluid_vjp<Q, C>(hb, gam, a, mu, gh, ggam);
+    if (kind == K_INFLOW) {
+      const C* ub = cptr<C>(a.uin);
+      const long long pl = (long long)a.ny * a.nz, p = y + (long long)a.ny * z;
+      bc_inlet_vjp<Q, C>(h, ub[p], ub[pl + p], ub[2 * pl + p], gh, lam, gub);
+    } else {
+      bc_outlet_vjp<Q, C>(h, C(a.rho_out), gh, lam);
+    }
+  } else {
+    collide_fluid_vjp<Q, C>(h, gam, a, mu, lam, ggam);
+  }
+  if (d.add_dj) {
+    const C w = C(x == d.xa ? d.wa : 0.0) + C(x == d.xb ? d.wb : 0.0);
+    sfor<0, Q>([&](auto I) { lam[I] += w; });
+  }
+  sfor<0, Q>([&](auto I) { lo[(long long)I * a.stride + n] = lam[I]; });
+  if (d.dgam) cptr<C>(d.dgam)[n] += ggam;
+  if (kind == K_INFLOW && d.duin) {
+    const long long pl = (long long)a.ny * a.nz, p = y + (long long)a.ny * z;
+    C* du = cptr<C>(d.duin);
+    atomicAdd(du + p, gub[0]);
+    atomicAdd(du + pl + p, gub[1]);
+    atomicAdd(du + 2 * pl + p, gub[2]);
+  }
+}
+
+// Adjoint seed lambda_T = dJ/dS_T: weight wa on every population of the non-solid cells of plane
+// x = xa, wb on plane x = xb, zero elsewhere.
+template <class C>
+__global__ void k_seed(const Args a, C* lam, int xa, int xb, double wa, double wb, int q) {
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= a.N) return;
+  const int x = int(n % a.nx);
+  C w = C(0);
+  if ((a.type[n] & T_KIND) != K_SOLID) w = C(x == xa ? wa : 0.0) + C(x == xb ? wb : 0.0);
+  for (int i = 0; i < q; ++i) lam[(long long)i * a.stride + n] = w;
+}
+
+template <class A, class B>
+__global__ void k_convert(const A* in, B* out, long long n) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = B(in[i]);
+}
+
+// ---- host launchers ------------------------------------------------------------------------------------
+inline dim3 bulk_block(const Args& a) {
+  int bx = a.nx >= 128 ? 128 : ((a.nx + 31) / 32) * 32;
+  int by = BULK_THREADS / bx;
+  if (by < 1) by = 1;
+  return dim3(bx, by, 1);
+}
+inline dim3 bulk_grid(const Args& a) {
+  dim3 b = bulk_block(a);
+  return dim3((a.nx + b.x - 1) / b.x, (a.ny + b.y - 1) / b.y, a.nz);
+}
+inline unsigned blocks_for(long long n, int t) { return unsigned((n + t - 1) / t); }
+
+template <int Q, class S>
+struct Impl {
+  using C = typename Codec<S>::C;
+  static void step_bulk(const Args& a, int odd, cudaStream_t s) {
+    if (odd) k_bulk<Q, S, true><<<bulk_grid(a), bulk_block(a), 0, s>>>(a);
+    else k_bulk<Q, S, false><<<bulk_grid(a), bulk_block(a), 0, s>>>(a);
+  }
+  static void step_list(const Args& a, int odd, cudaStream_t s) {
+    if (a.n_list <= 0) return;
+    if (odd) k_list<Q, S, true><<<blocks_for(a.n_list, LIST_THREADS), LIST_THREADS, 0, s>>>(a);
+    else k_list<Q, S, false><<<blocks_for(a.n_list, LIST_THREADS), LIST_THREADS, 0, s>>>(a);
+  }
+  static void init_eq(const Args& a, const void* rho, const void* u, int dtype, cudaStream_t s) {
+    k_init_eq<Q, S><<<blocks_for(a.N, 256), 256, 0, s>>>(a, rho, u, dtype);
+  }
+  static void moments(const Args& a, int swapped, void* rho, void* u, int dtype, cudaStream_t s) {
+    k_moments<Q, S><<<blocks_for(a.N, 128), 128, 0, s>>>(a, swapped, rho, u, dtype);
+  }
+  static void get_pops(const Args& a, int swapped, void* out, int dtype, cudaStream_t s) {
+    k_get_pops<Q, S><<<blocks_for(a.N, 128), 128, 0, s>>>(a, swapped, out, dtype);
+  }
+  static void set_pops(const Args& a, int swapped, const void* in, int dtype, cudaStream_t s) {
+    k_set_pops<Q, S><<<blocks_for(a.N, 128), 128, 0, s>>>(a, swapped, in, dtype);
+  }
+  static void ref_fill(const Args& a, int swapped, void* ref, cudaStream_t s) {
+    if (a.n_list <= 0) return;
+    k_ref_fill<Q, S><<<blocks_for(a.n_list, 128), 128, 0, s>>>(a, swapped, ref);
+  }
+  static void reduce(const Args& a, int swapped, double* partial, int nblk, cudaStream_t s) {
+    k_reduce<Q, S><<<nblk, 256, 0, s>>>(a, swapped, partial);
+  }
+  static void list_aux(const Args& a, const int* nsum, const float* wd, void* wnrm, void* wyw, cudaStream_t s) {
+    if (a.n_list <= 0) return;
+    k_list_aux<C><<<blocks_for(a.n_list, 128), 128, 0, s>>>(a, nsum, wd, static_cast<C*>(wnrm), static_cast<C*>(wyw));
+  }
+  static void step_oop(const Args& a, const void* fin, void* fout, cudaStream_t s) {
+    k_step_oop<Q, S><<<bulk_grid(a), bulk_block(a), 0, s>>>(a, static_cast<const S*>(fin), static_cast<S*>(fout));
+  }
+  static void reverse(const Args& a, const AdjArgs& d, cudaStream_t s) {
+    k_reverse<Q, S><<<bulk_grid(a), bulk_block(a), 0, s>>>(a, d);
+  }
+  static void plane_rho(const Args& a, const void* state, int swapped, int xa, int xb, double* acc, double wa, double wb,
+                        cudaStream_t s) {
+    k_plane_rho<Q, S><<<1, 1024, 0, s>>>(a, static_cast<const S*>(state), swapped, xa, xb, acc, wa, wb);
+  }
+  static void seed(const Args& a, void* lam, int xa, int xb, double wa, double wb, cudaStream_t s) {
+    k_seed<C><<<blocks_for(a.N, 256), 256, 0, s>>>(a, static_cast<C*>(lam), xa, xb, wa, wb, Q);
+  }
+  static void convert(const void* in, int idt, void* out, int odt, long long n, cudaStream_t s) {
+    const unsigned g = blocks_for(n, 256);
+    if (idt == 0 && odt == 0) k_convert<double, double><<<g, 256, 0, s>>>((const double*)in, (double*)out, n);
+    else if (idt == 0) k_convert<double, float><<<g, 256, 0, s>>>((const double*)in, (float*)out, n);
+    else if (odt == 0) k_convert<float, double><<<g, 256, 0, s>>>((const float*)in, (double*)out, n);
+    else k_convert<float, float><<<g, 256, 0, s>>>((const float*)in, (float*)out, n);
+  }
+  static const Ops* table() {
+    static const Ops ops = {Q,        int(sizeof(S)), int(sizeof(C)), step_bulk, step_list, init_eq,   moments,
+                            get_pops, set_pops,       ref_fill,       reduce,    list_aux,  step_oop,  reverse,
+                            plane_rho, seed,           convert};
+    return &ops;
+  }
+};
+
+}  // namespace lbm

@@ -1,0 +1,62 @@
+// Host-side table of the kernel launchers of one (lattice, storage) instantiation.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbm {
+struct Args;
+
+struct AdjArgs;
+
+struct Ops {
+  int q;
+  int elem;      // bytes per stored population value
+  int celem;     // bytes per compute value (float or double)
+  // one step: interior kernel then boundary-list kernel; parity odd = step counter & 1
+  void (*step_bulk)(const Args&, int odd, cudaStream_t);
+  void (*step_list)(const Args&, int odd, cudaStream_t);
+  // state access; swapped = state stored in the after-even-step form
+  void (*init_eq)(const Args&, const void* rho, const void* u, int dtype, cudaStream_t);
+  void (*moments)(const Args&, int swapped, void* rho, void* u, int dtype, cudaStream_t);
+  void (*get_pops)(const Args&, int swapped, void* out, int dtype, cudaStream_t);
+  void (*set_pops)(const Args&, int swapped, const void* in, int dtype, cudaStream_t);
+  void (*ref_fill)(const Args&, int swapped, void* ref, cudaStream_t);
+  // FP64 reduction: writes nblk partials of (mass, mom x, y, z)
+  void (*reduce)(const Args&, int swapped, double* partial, int nblk, cudaStream_t);
+  // list auxiliary data (normals, wall distances) from integer normal sums
+  void (*list_aux)(const Args&, const int* nsum, const float* wall_dist, void* wnrm, void* wyw, cudaStream_t);
+  // adjoint: out-of-place forward from a natural-layout state, reverse step, objective plane sums
+  void (*step_oop)(const Args&, const void* fin, void* fout, cudaStream_t);
+  void (*reverse)(const Args&, const AdjArgs&, cudaStream_t);
+  void (*plane_rho)(const Args&, const void* state, int swapped, int xa, int xb, double* acc, double wa, double wb,
+                    cudaStream_t);
+  void (*seed)(const Args&, void* lam, int xa, int xb, double wa, double wb, cudaStream_t);
+  void (*convert)(const void* in, int in_dtype, void* out, int out_dtype, long long n, cudaStream_t);
+};
+
+const Ops* ops_f64(int q);
+const Ops* ops_f32(int q);
+const Ops* ops_f16(int q);
+const Ops* ops_bf16(int q);
+
+// Geometry kernels (storage independent)
+struct GeoArgs {
+  int nx, ny, nz;
+  long long nxy, N;
+  int face[6];
+  int q;
+};
+void geo_classify(const GeoArgs&, const uint8_t* mask, uint8_t* type, unsigned* status, cudaStream_t);
+void geo_mark_ref(const GeoArgs&, uint8_t* type, cudaStream_t);
+// list compaction: per-block counts (blocks of 256 cells), then scatter with block offsets
+int geo_count_blocks(const GeoArgs&);
+void geo_list_count(const GeoArgs&, uint8_t* type, int* counts, cudaStream_t);
+void geo_list_write(const GeoArgs&, const uint8_t* type, const int* offsets, long long* lcell, cudaStream_t);
+void geo_list_meta(const GeoArgs&, const uint8_t* type, const long long* lcell, int n_list, int* nsum, int* wref,
+                   cudaStream_t);
+// source map (debug): for each (i, n): source population and cell, -1 for solid cells
+void geo_source_map(const GeoArgs&, const uint8_t* type, int64_t* src_dir, int64_t* src_cell, cudaStream_t);
+// FP64 final reduction of nblk partials (4 doubles each) into out[4], fixed order
+void reduce_final(const double* partial, int nblk, double* out, cudaStream_t);
+}  // namespace lbm

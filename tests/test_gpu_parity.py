@@ -1,0 +1,438 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Integer work (classification, boundary list, wall normals, reference cells, propagation map) is
+compared bit-exactly; FP64 storage within 1e-12 on populations; FP32 storage within 1e-5 relative on
+rho and u after 100 steps; 16-bit storage against the FP64 oracle with its stated error; the adjoint
+against the oracle's transpose; full-size workloads on sampled cells recomputed by the oracle on
+crops around them.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2506_21804_gb300 import inputs as I
+from tests.helpers import oracle_from, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+lbm = pytest.importorskip("paper_2506_21804_gb300.lbm")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    lbm.lib()
+
+
+def gpu_from(w, storage):
+    return lbm.Lattice.from_workload(w, storage=storage)
+
+
+def small_cases(q=19):
+    return [
+        I.random_box(9, 7, 6, seed=1, q=q, solid_frac=0.15, tau=0.62, cs=0.12, faces=(0, 0, 0, 0, 0, 0)),
+        I.random_box(10, 7, 5, seed=2, q=q, solid_frac=0.1, tau=0.55, cs=0.1, faces=(3, 3, 2, 2, 1, 2),
+                     inflow=True, outflow=True),
+        I.random_box(8, 6, 7, seed=3, q=q, solid_frac=0.2, tau=0.8, cs=0.0, faces=(2, 2, 2, 2, 2, 2)),
+        I.random_box(33, 5, 4, seed=4, q=q, solid_frac=0.05, tau=0.7, cs=0.15, faces=(1, 1, 2, 2, 0, 0)),
+        I.canopy(nx=40, ny=24, nz=20, q=q, n_buildings=6, seed=2506, domain=(200, 24, 60), crop=(64, 0, 0),
+                 dtype=np.float64),
+        I.channel(nx=16, ny=14, nz=6, q=q, noise=0.05, seed=5, dtype=np.float64),
+        I.duct(n=10, q=q, u_in=0.03, tau=0.7, sigma=2.0, cs=0.1, dtype=np.float64),
+    ]
+
+
+def with_features(w):
+    """Switch on force, porosity and the wall model where the case has room for them."""
+    rng = np.random.default_rng(w.nx * 7 + w.ny)
+    if w.gamma is None and w.name.startswith("random"):
+        w.gamma = 0.7 + 0.3 * rng.random(w.N)
+    if w.name.startswith("random") and w.faces[0] != 3:
+        w.force = (2e-6, -1e-6, 5e-7)
+    w.wall_model = True
+    return w
+
+
+# ---- integer work: bit-exact ------------------------------------------------------------------------------
+@pytest.mark.parametrize("q", [19, 27])
+def test_classification_lists_and_source_map_bit_exact(q):
+    for w in small_cases(q):
+        o = oracle_from(w)
+        g = gpu_from(w, lbm.F32)
+        kind, isref, nsum, ref = o.classification()
+        t = g.debug_dump(0)
+        assert np.array_equal(t & 7, kind), w.name
+        assert np.array_equal((t & 8) != 0, isref == 1), w.name
+        on = (kind == 2) | (kind == 3) | (kind == 4) | (isref == 1)
+        assert np.array_equal((t & 32) != 0, on), w.name
+        cells, refpos = o.boundary_list()
+        assert np.array_equal(g.debug_dump(1), cells), w.name
+        assert np.array_equal(g.debug_dump(2), refpos), w.name
+        assert np.array_equal(g.debug_dump(3).reshape(-1, 3), nsum[cells]), w.name
+        sd, sc = o.source_map()
+        assert np.array_equal(g.debug_dump(4).reshape(q, -1), sd), w.name
+        assert np.array_equal(g.debug_dump(5).reshape(q, -1), sc), w.name
+        info = g.info()
+        assert info["n_list"] == len(cells) and info["n_wall"] == int((kind == 2).sum())
+
+
+# ---- FP64 storage: parity to roundoff ------------------------------------------------------------------------
+@pytest.mark.parametrize("q", [19, 27])
+@pytest.mark.parametrize("steps", [1, 2, 7])
+def test_fp64_step_parity(q, steps):
+    for w in small_cases(q):
+        w = with_features(w)
+        o = oracle_from(w)
+        g = gpu_from(w, lbm.F64)
+        o.step(steps)
+        g.step(steps)
+        fo = o.populations()
+        fg = g.get_populations()
+        fl = w.mask != 1
+        assert np.abs(fg[:, fl] - fo[:, fl]).max() < 1e-12, w.name
+        ro, uo = o.moments()
+        rg, ug = g.moments()
+        assert np.abs(rg - ro).max() < 1e-12, w.name
+        assert np.abs(ug - uo).max() < 1e-12, w.name
+        mo, po = o.reduce()
+        mg, pg = g.reduce()
+        assert abs(mg - mo) < 1e-10 and np.abs(pg - po).max() < 1e-10
+
+
+def test_fp64_taylor_green_32cube_200_steps():
+    """Config: D3Q19 BGK FP64, 32^3 periodic TGV (u0 = 0.05, tau = 0.6), 200 steps: parity with the
+    oracle, the analytic amplitude decay exp(-2 nu k^2 t) within 1 %, and exact mass conservation."""
+    w = I.taylor_green(n=32, u0=0.05, tau=0.6)
+    g = gpu_from(w, lbm.F64)
+    o = oracle_from(w)
+    m0, _ = g.reduce()
+    g.step(200)
+    o.step(200)
+    rg, ug = g.moments()
+    ro, uo = o.moments()
+    assert np.abs(rg - ro).max() < 1e-12
+    assert np.abs(ug - uo).max() < 1e-12
+    shape = w.u0 / 0.05
+    A = (ug * shape).sum() / (shape * shape).sum()
+    exact = 0.05 * np.exp(-2 * w.meta["nu"] * w.meta["k"] ** 2 * 200)
+    assert abs(A / exact - 1) < 0.01
+    m1, _ = g.reduce()
+    assert abs(m1 - m0) / m0 < 1e-13
+
+
+# ---- FP32 storage -------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("q", [19, 27])
+def test_fp32_parity_100_steps(q):
+    for w in small_cases(q):
+        w = with_features(w)
+        o = oracle_from(w, cast32=True)
+        g = gpu_from(w, lbm.F32)
+        o.step(100)
+        g.step(100)
+        ro, uo = o.moments()
+        rg, ug = g.moments()
+        fl = w.mask != 1
+        assert np.abs(rg[fl] - ro[fl]).max() / np.abs(ro[fl]).max() < 1e-5, w.name
+        assert rel_l2(ug[:, fl], uo[:, fl]) < 1e-5, w.name
+
+
+def test_fp32_channel_and_canopy_crops_100_steps():
+    """Channel (wall function, force, Smagorinsky) and an urban-canopy crop 128x64x64 of the seeded
+    1024x512x256 geometry, 100 steps, FP32 vs the FP64 oracle."""
+    cases = [I.channel(nx=32, ny=34, nz=16, seed=550, dtype=np.float64),
+             I.canopy(nx=128, ny=64, nz=64, seed=2506, crop=(64, 0, 0), domain=(1024, 512, 256), dtype=np.float64)]
+    for w in cases:
+        o = oracle_from(w, cast32=True)
+        g = gpu_from(w, lbm.F32)
+        o.step(100)
+        g.step(100)
+        ro, uo = o.moments()
+        rg, ug = g.moments()
+        fl = w.mask != 1
+        assert np.abs(rg[fl] - ro[fl]).max() < 1e-5, w.name
+        assert rel_l2(ug[:, fl], uo[:, fl]) < 1e-5, w.name
+        assert g.info()["n_wall"] > 0
+
+
+# ---- 16-bit storage ---------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("storage,bound", [(lbm.F16, 1e-3), (lbm.BF16, 2e-2)])
+def test_16bit_taylor_green_error(storage, bound):
+    w = I.taylor_green(n=32, u0=0.05, tau=0.6)
+    g = gpu_from(w, storage)
+    o = oracle_from(w)
+    g.step(200)
+    o.step(200)
+    _, ug = g.moments()
+    _, uo = o.moments()
+    assert rel_l2(ug, uo) < bound
+
+
+def test_16bit_matches_oracle_storage_emulation_one_step():
+    """One step of FP16 storage equals the oracle's FP16-rounded storage up to one rounding of the
+    stored deviation (FP32 vs FP64 arithmetic decides ties differently only at the last bit)."""
+    w = I.random_box(12, 8, 6, seed=9, q=19, solid_frac=0.1, tau=0.7, cs=0.1)
+    g = gpu_from(w, lbm.F16)
+    o = oracle_from(w, storage=2)
+    g.step(1)
+    o.step(1)
+    fg = g.get_populations()
+    fo = o.populations()
+    fl = w.mask != 1
+    c, wts, *_ = O.lattice(19)
+    dev = np.abs(fo[:, fl] - wts[:, None])
+    assert (np.abs(fg[:, fl] - fo[:, fl]) <= np.maximum(dev, 6.1e-5) * 2.0 ** -10 + 1e-12).all()
+
+
+# ---- adjoint -------------------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("storage,tol", [(lbm.F64, 1e-11), (lbm.F32, 2e-4)])
+def test_reverse_step_matches_oracle_transpose(storage, tol):
+    for w in [I.duct(n=8, u_in=0.03, tau=0.7, sigma=1.5, cs=0.12, dtype=np.float64),
+              I.random_box(9, 7, 6, seed=1, q=19, solid_frac=0.15, tau=0.62, cs=0.12),
+              I.random_box(10, 7, 5, seed=2, q=19, solid_frac=0.1, tau=0.55, cs=0.1, faces=(3, 3, 2, 2, 1, 2),
+                           inflow=True, outflow=True),
+              I.duct(n=6, q=27, u_in=0.02, tau=0.8, sigma=1.5, cs=0.0, dtype=np.float64)]:
+        if w.gamma is None:
+            w.gamma = 0.6 + 0.4 * np.random.default_rng(3).random(w.N)
+        o = oracle_from(w, cast32=storage == lbm.F32)
+        g = gpu_from(w, storage)
+        o.step(2)
+        g.step(2)
+        lam = np.random.default_rng(5).standard_normal((w.q, w.N))
+        lam[:, w.mask == 1] = 0
+        gl, gg, gu = g.adjoint_step(lam)
+        ol, og, ou = o.vjp_step(lam)
+        s = np.abs(ol).max()
+        assert np.abs(gl - ol).max() < tol * s, w.name
+        assert np.abs(gg - og).max() < tol * max(np.abs(og).max(), 1e-30), w.name
+        assert np.abs(gu.reshape(-1) - ou).max() <= tol * max(np.abs(ou).max(), 1e-30), w.name
+
+
+def test_objective_gradient_fp64_matches_oracle():
+    w = I.duct(n=12, u_in=0.03, tau=0.7, sigma=2.0, cs=0.1, dtype=np.float64)
+    T, W = 26, 6
+    o = oracle_from(w)
+    Jo = o.objective_run(T, W, 1, w.nx - 2)
+    go, uo = o.adjoint()
+    g = gpu_from(w, lbm.F64)
+    Jg = g.objective_forward(T, W, 1, w.nx - 2, ckpt=4)
+    gg, ug = g.objective_backward()
+    assert abs(Jg - Jo) < 1e-12 * max(1.0, abs(Jo))
+    assert rel_l2(gg, go) < 1e-10
+    assert rel_l2(ug, uo) < 1e-10
+    # the state after backward is the one after the forward run
+    assert g.info()["t"] == T
+
+
+def test_objective_gradient_fp32_32cube_vs_fp64_oracle():
+    """Differentiation config at 32^3 (sigma = 2 cells, 250 steps, objective over the last 25,
+    checkpoint interval 32): GPU FP32 adjoint vs FP64 oracle adjoint within 1e-4 (L2 over gamma)."""
+    w = I.duct(n=32, u_in=0.04, tau=0.6, sigma=2.0, dtype=np.float64)
+    T, W = 250, 25
+    o = oracle_from(w, cast32=True)
+    Jo = o.objective_run(T, W, 1, w.nx - 2)
+    go, uo = o.adjoint()
+    g = gpu_from(w, lbm.F32)
+    Jg = g.objective_forward(T, W, 1, w.nx - 2, ckpt=32)
+    gg, ug = g.objective_backward()
+    assert abs(Jg - Jo) < 1e-4 * abs(Jo)
+    assert rel_l2(gg, go) < 1e-4
+    prof = w.uin[0] / 0.04
+    assert abs((ug[0] * prof).sum() - (uo[0] * prof).sum()) < 1e-4 * abs((uo[0] * prof).sum())
+
+
+def test_objective_gradient_fp64_central_differences():
+    w = I.duct(n=10, u_in=0.03, tau=0.7, sigma=1.5, cs=0.1, dtype=np.float64)
+    T, W = 20, 5
+    g = gpu_from(w, lbm.F64)
+    g.objective_forward(T, W, 1, w.nx - 2, ckpt=6)
+    dg, _ = g.objective_backward()
+    rng = np.random.default_rng(8)
+    cells = rng.choice(np.nonzero(w.mask != 1)[0], 16, replace=False)
+    h = 1e-5
+    for n in cells:
+        vals = []
+        for s in (1, -1):
+            gam = w.gamma.copy()
+            gam[n] += s * h
+            g2 = gpu_from(w, lbm.F64)
+            g2.set_porosity(gam)
+            vals.append(g2.objective_forward(T, W, 1, w.nx - 2, ckpt=6))
+        fd = (vals[0] - vals[1]) / (2 * h)
+        assert abs(fd - dg[n]) <= 1e-3 * max(abs(fd), 1e-3 * np.abs(dg).max())
+
+
+# ---- state handling, checkpoints, failure paths --------------------------------------------------------------
+def test_save_load_resume_is_bit_identical():
+    w = with_features(small_cases()[4])
+    g = gpu_from(w, lbm.F32)
+    g.step(5)
+    buf = g.save()
+    g.step(8)
+    a = g.get_populations(np.float32)
+    g.load(buf)
+    assert g.info()["t"] == 5
+    g.step(8)
+    b = g.get_populations(np.float32)
+    assert np.array_equal(a, b)
+
+
+def test_populations_round_trip_both_layouts():
+    w = small_cases()[1]
+    g = gpu_from(w, lbm.F64)
+    for steps in (0, 1):
+        g.step(steps)
+        f = g.get_populations()
+        f2 = f * (1 + 1e-3 * np.random.default_rng(1).standard_normal(f.shape))
+        f2[:, w.mask == 1] = 0
+        g.set_populations(f2)
+        assert np.abs(g.get_populations() - f2).max() < 1e-15
+
+
+def test_nan_is_reported_and_context_recovers():
+    w = small_cases()[0]
+    g = gpu_from(w, lbm.F32)
+    f = g.get_populations()
+    n = int(np.nonzero(w.mask != 1)[0][3])
+    f[5, n] = np.nan
+    g.set_populations(f)
+    g.step(2)
+    with pytest.raises(lbm.LBMError) as e:
+        g.sync()
+    assert e.value.code == lbm.ENAN
+    g.init_equilibrium(np.asarray(w.rho0, np.float32), np.asarray(w.u0, np.float32))
+    g.step(2)
+    g.sync()
+
+
+def test_invalid_arguments_are_rejected():
+    g = lbm.Lattice(19, 8, 6, 4, 0.6)
+    bad = np.zeros(8 * 6 * 4, np.uint8)
+    bad[7] = 9
+    with pytest.raises(lbm.LBMError) as e:
+        g.set_geometry(bad)
+    assert e.value.code == lbm.EINVAL
+    with pytest.raises(lbm.LBMError):
+        g.set_faces([0, 1, 0, 0, 0, 0])
+    with pytest.raises(lbm.LBMError):
+        lbm.Lattice(19, 8, 8, 8, 0.5)
+    with pytest.raises(lbm.LBMError):
+        lbm.Lattice(21, 8, 8, 8, 0.6)
+    g.set_wall_model(0.41, 9.52)
+    with pytest.raises(lbm.LBMError) as e:
+        g.objective_forward(4, 2, 1, 6)
+    assert e.value.code == lbm.ESTATE
+
+
+def test_device_buffers_through_torch():
+    import torch
+    w = small_cases()[0]
+    g = gpu_from(w, lbm.F32)
+    s = torch.cuda.Stream()
+    g.set_stream(s)
+    with torch.cuda.stream(s):
+        g.step(3)
+        rho = torch.empty(w.N, dtype=torch.float32, device="cuda")
+        u = torch.empty(3, w.N, dtype=torch.float32, device="cuda")
+        g.moments(np.float32, rho, u)
+    s.synchronize()
+    rh, uh = g.moments(np.float32)
+    assert np.array_equal(rho.cpu().numpy(), rh)
+    assert np.array_equal(u.cpu().numpy(), uh)
+    g.set_stream(0)
+
+
+# ---- full-size workloads in the benchmark's launch configuration, sampled --------------------------------------
+def _crop_oracle(w, centre, R):
+    """Oracle on the (2R+1)^3 neighbourhood of `centre` of workload w: coordinates wrap on periodic
+    axes; positions beyond a bounce-back face become solid cells; a crop face on the domain's own
+    face keeps its kind; other crop faces are bounce-back (their effect stays > R - 2*steps away)."""
+    dims = (w.nx, w.ny, w.nz)
+    rng_ax, faces, solid_pad = [], [], []
+    for a in range(3):
+        per = w.faces[2 * a] == 0
+        lo, hi = centre[a] - R, centre[a] + R
+        if per:
+            if dims[a] <= 2 * R + 1:
+                idx = np.arange(dims[a]); f = (0, 0)
+            else:
+                idx = np.arange(lo, hi + 1) % dims[a]; f = (1, 1)
+            pad = np.zeros(len(idx), bool)
+        else:
+            l2, h2 = max(lo, 0), min(hi, dims[a] - 1)
+            fl = w.faces[2 * a] if lo <= 0 else 1
+            fh = w.faces[2 * a + 1] if hi >= dims[a] - 1 else 1
+            idx = np.arange(l2, h2 + 1)
+            pad = np.zeros(len(idx), bool)
+            f = (fl, fh)
+        rng_ax.append(idx)
+        faces += list(f)
+        solid_pad.append(pad)
+    xs, ys, zs = rng_ax
+    Z, Y, X = np.meshgrid(zs, ys, xs, indexing="ij")
+    gidx = (X + w.nx * (Y + w.ny * Z)).reshape(-1)
+    nx, ny, nz = len(xs), len(ys), len(zs)
+    sub = I.Workload(name="crop", q=w.q, nx=nx, ny=ny, nz=nz, tau=w.tau, cs=w.cs, faces=tuple(faces),
+                     mask=w.mask[gidx].copy(), force=w.force, rho_out=w.rho_out, wall_model=w.wall_model,
+                     kappa=w.kappa, E=w.E, rho0=np.asarray(w.rho0)[gidx], u0=np.asarray(w.u0)[:, gidx])
+    if w.ywall is not None:
+        sub.ywall = np.asarray(w.ywall)[gidx]
+    if w.gamma is not None:
+        sub.gamma = np.asarray(w.gamma)[gidx]
+    if w.uin is not None:
+        YY, ZZ = np.meshgrid(ys, zs, indexing="xy")
+        pidx = (YY + w.ny * ZZ).reshape(-1)
+        sub.uin = np.asarray(w.uin)[:, pidx]
+    # open faces keep their inlet/outlet cells only where the crop touches the domain face
+    m = sub.mask.reshape(nz, ny, nx)
+    if faces[0] != 3:
+        m[:, :, 0][m[:, :, 0] == 3] = 0
+    if faces[1] != 3:
+        m[:, :, -1][m[:, :, -1] == 4] = 0
+    sub.mask = m.reshape(-1)
+    local = [int(np.nonzero(rng_ax[a] == centre[a])[0][0]) for a in range(3)]
+    return sub, local[0] + nx * (local[1] + ny * local[2])
+
+
+def _sampled_full_size(w, storage, steps, samples, R, seed):
+    g = gpu_from(w, storage)
+    g.step(steps)
+    rg, ug = g.moments(np.float32)
+    rng = np.random.default_rng(seed)
+    kind = (g.debug_dump(0) & 7)
+    cand_wall = np.nonzero(kind == 2)[0]
+    cand_bc = np.nonzero((kind == 3) | (kind == 4))[0]
+    cand_f = np.nonzero(kind == 0)[0]
+    picks = list(rng.choice(cand_f, samples // 2, replace=False))
+    if len(cand_wall):
+        picks += list(rng.choice(cand_wall, samples // 4, replace=False))
+    if len(cand_bc):
+        picks += list(rng.choice(cand_bc, samples // 4, replace=False))
+    worst_r = worst_u = 0.0
+    for n in picks:
+        c = (n % w.nx, (n // w.nx) % w.ny, n // (w.nx * w.ny))
+        sub, ln = _crop_oracle(w, c, R)
+        o = oracle_from(sub, cast32=True)
+        o.step(steps)
+        ro, uo = o.moments()
+        worst_r = max(worst_r, abs(float(rg[n]) - ro[ln]))
+        worst_u = max(worst_u, float(np.abs(ug[:, n] - uo[:, ln]).max()) / 0.05)
+    return worst_r, worst_u
+
+
+def test_full_size_channel_256_sampled():
+    """256^3 turbulent channel (D3Q19, Smagorinsky C_S = 0.1, wall function, body force), FP32, in the
+    benchmark's launch shape: 4 steps (both parities twice), 48 sampled cells recomputed by the oracle
+    on 15^3 crops (dependency radius 2 per step including the lagged reference velocity)."""
+    w = I.channel(nx=256, ny=256, nz=256, seed=550, dtype=np.float32)
+    er, eu = _sampled_full_size(w, lbm.F32, steps=4, samples=48, R=7, seed=1)
+    assert er < 1e-6 and eu < 1e-5, (er, eu)
+
+
+@pytest.mark.parametrize("q", [19, 27])
+def test_full_size_canopy_512_sampled(q):
+    w = I.canopy(nx=512, ny=512, nz=256, q=q, seed=2506, dtype=np.float32)
+    er, eu = _sampled_full_size(w, lbm.F32, steps=2, samples=32, R=5, seed=2)
+    assert er < 1e-6 and eu < 1e-5, (er, eu)
