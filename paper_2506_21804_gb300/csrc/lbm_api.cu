@@ -81,7 +81,7 @@ struct lbm_ctx {
   long long t = 0;
   unsigned status_seen = 0;
   // device buffers
-  DevBuf f, type, mask, wdist, gamma, uin, lcell, nsum, wref, wnrm, wyw, ref0, ref1, status, red, redout, stage;
+  DevBuf f, type, mask, wdist, gamma, uin, lcell, nsum, wref, lxyz, lcode, wnrm, wyw, ref0, ref1, status, red, redout, stage;
   bool has_gamma = false, has_wdist = false;
   int n_list = 0;
   long long counts[8] = {0};  // wall, ref, inflow, outflow, solid
@@ -98,7 +98,7 @@ struct lbm_ctx {
   double adj_ms[2] = {0, 0};
 
   ~lbm_ctx() {
-    DevBuf* all[] = {&f, &type, &mask, &wdist, &gamma, &uin, &lcell, &nsum, &wref, &wnrm, &wyw, &ref0, &ref1, &status, &red,
+    DevBuf* all[] = {&f, &type, &mask, &wdist, &gamma, &uin, &lcell, &nsum, &wref, &lxyz, &lcode, &wnrm, &wyw, &ref0, &ref1, &status, &red,
                      &redout, &stage, &lamA, &lamB, &dgam, &duin};
     for (DevBuf* b : all) b->release();
     for (auto& b : ckpts) b.release();
@@ -141,11 +141,14 @@ Args make_args(const lbm_ctx* c) {
   a.N = c->N;
   for (int i = 0; i < 6; ++i) a.face[i] = c->face[i];
   a.tau0 = c->tau0;
+  a.nu0 = (c->tau0 - 0.5) / 3.0;
   a.smag = 18.0 * std::sqrt(2.0) * c->cs * c->cs;
   a.cs2smag = c->cs * c->cs;
   a.fx = c->force[0]; a.fy = c->force[1]; a.fz = c->force[2];
   a.status = static_cast<unsigned*>(c->status.p);
   a.lcell = static_cast<const long long*>(c->lcell.p);
+  a.lxyz = static_cast<const int*>(c->lxyz.p);
+  a.lcode = static_cast<const unsigned long long*>(c->lcode.p);
   a.n_list = c->n_list;
   a.wnrm = c->wnrm.p;
   a.wyw = c->wyw.p;
@@ -263,8 +266,11 @@ int build_geometry(lbm_ctx* c) {
   geo_list_write(g, static_cast<const uint8_t*>(c->type.p), static_cast<const int*>(counts.p), static_cast<long long*>(c->lcell.p), s);
   CK(c->nsum.ensure(nl * 3 * sizeof(int)));
   CK(c->wref.ensure(nl * sizeof(int)));
+  CK(c->lxyz.ensure(nl * 3 * sizeof(int)));
+  CK(c->lcode.ensure(nl * sizeof(unsigned long long)));
   geo_list_meta(g, static_cast<const uint8_t*>(c->type.p), static_cast<const long long*>(c->lcell.p), c->n_list,
-                static_cast<int*>(c->nsum.p), static_cast<int*>(c->wref.p), s);
+                static_cast<int*>(c->nsum.p), static_cast<int*>(c->wref.p), static_cast<int*>(c->lxyz.p),
+                static_cast<unsigned long long*>(c->lcode.p), s);
   CK(c->wnrm.ensure(nl * 3 * c->ops->celem));
   CK(c->wyw.ensure(nl * c->ops->celem));
   CK(c->ref0.ensure(nl * 3 * c->ops->celem));

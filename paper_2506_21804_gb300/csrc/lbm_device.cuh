@@ -130,12 +130,15 @@ struct Args {
   long long nxy, N;
   int face[6];
   double tau0;             // molecular relaxation time
+  double nu0;              // molecular viscosity (tau0 - 1/2)/3, formed in double precision
   double smag;             // 18 sqrt(2) C_S^2
   double cs2smag;          // C_S^2
   double fx, fy, fz;       // body force
   unsigned* status;        // sticky device status bits
   // boundary list
   const long long* lcell;  // cell index per entry
+  const int* lxyz;         // x, y, z per entry
+  const unsigned long long* lcode;  // 2 bits per direction: 0 streaming, 1 bounce-back slot, 2 general
   int n_list;
   const void* wnrm;        // C[3] unit normal per entry (WALL entries)
   const void* wyw;         // C wall distance per entry
@@ -397,7 +400,7 @@ __device__ __forceinline__ void collide_wall(C* h, const Args& a, const C* nrm, 
     if (U >= C(1e-12)) {
       tx = utx / U; ty = uty / U; tz = utz / U;
       const C k = C(a.kappa), E = C(a.E);
-      const C nu = (C(a.tau0) - C(0.5)) * C(1.0 / 3.0);
+      const C nu = C(a.nu0);
       const C upr = sp_solve_re<C>(U * (yw + C(1)) / nu, k, E);
       const C utau = U / upr;
       const C upw = sp_solve_y<C>(yw * utau / nu, k, E);

@@ -150,16 +150,38 @@ __global__ void k_list_write(const GeoArgs g, const uint8_t* type, const int* of
   if (f) lcell[base + __popc(b & ((1u << lane) - 1u))] = n;
 }
 
+// Per list entry: coordinates, integer wall-normal sum and reference position (WALL entries), and
+// the 2-bit slot code of every direction (0 plain neighbour, 1 own bounce-back slot, 2 slip rule).
 template <int Q>
-__global__ void k_list_meta(const GeoArgs g, const uint8_t* type, const long long* lcell, int n_list, int* nsum, int* wref) {
+__global__ void k_list_meta(const GeoArgs g, const uint8_t* type, const long long* lcell, int n_list, int* nsum, int* wref,
+                            int* lxyz, unsigned long long* lcode) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n_list) return;
   const long long n = lcell[k];
+  int x, y, z;
+  coords(g, n, x, y, z);
+  lxyz[3 * k] = x;
+  lxyz[3 * k + 1] = y;
+  lxyz[3 * k + 2] = z;
+  unsigned long long code = 0;
+  sfor<0, Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    const Pos p = wrap(g, x - Lat<Q>::cx(i), y - Lat<Q>::cy(i), z - Lat<Q>::cz(i));
+    unsigned long long c;
+    if (p.crossed) {
+      bool allslip = true;
+      for (int f = 0; f < 6; ++f)
+        if ((p.crossed >> f & 1) && g.face[f] != F_SLIP) allslip = false;
+      c = allslip ? 2ull : 1ull;
+    } else {
+      c = ((type[lin(g, p)] & T_KIND) == K_SOLID) ? 1ull : 0ull;
+    }
+    code |= c << (2 * i);
+  });
+  lcode[k] = code;
   nsum[3 * k] = nsum[3 * k + 1] = nsum[3 * k + 2] = 0;
   wref[k] = -1;
   if ((type[n] & T_KIND) != K_WALL) return;
-  int x, y, z;
-  coords(g, n, x, y, z);
   int v[3];
   normal_sum<Q>(g, type, x, y, z, v);
   nsum[3 * k] = v[0];
@@ -232,10 +254,10 @@ void geo_list_write(const GeoArgs& g, const uint8_t* type, const int* offsets, l
 }
 
 void geo_list_meta(const GeoArgs& g, const uint8_t* type, const long long* lcell, int n_list, int* nsum, int* wref,
-                   cudaStream_t s) {
+                   int* lxyz, unsigned long long* lcode, cudaStream_t s) {
   if (n_list <= 0) return;
-  if (g.q == 19) k_list_meta<19><<<nblocks(n_list, 128), 128, 0, s>>>(g, type, lcell, n_list, nsum, wref);
-  else k_list_meta<27><<<nblocks(n_list, 128), 128, 0, s>>>(g, type, lcell, n_list, nsum, wref);
+  if (g.q == 19) k_list_meta<19><<<nblocks(n_list, 128), 128, 0, s>>>(g, type, lcell, n_list, nsum, wref, lxyz, lcode);
+  else k_list_meta<27><<<nblocks(n_list, 128), 128, 0, s>>>(g, type, lcell, n_list, nsum, wref, lxyz, lcode);
 }
 
 void geo_source_map(const GeoArgs& g, const uint8_t* type, int64_t* sdir, int64_t* scell, cudaStream_t s) {

@@ -97,6 +97,59 @@ __device__ __forceinline__ void scatter(const Args& a, S* dst, int x, int y, int
   }
 }
 
+// Odd-step access of a boundary-list cell with precomputed per-direction slot codes: 0 the plain
+// (periodic-wrapped) neighbour slot, 1 the cell's own bounce-back slot (i, n), 2 the general rule.
+struct Nbr {
+  int x, xm, xp;
+  long long y0, ym, yp, z0, zm, zp;
+  __device__ __forceinline__ Nbr(const Args& a, int x_, int y, int z) {
+    x = x_;
+    xm = x == 0 ? a.nx - 1 : x - 1;
+    xp = x == a.nx - 1 ? 0 : x + 1;
+    y0 = (long long)y * a.nx;
+    ym = (long long)(y == 0 ? a.ny - 1 : y - 1) * a.nx;
+    yp = (long long)(y == a.ny - 1 ? 0 : y + 1) * a.nx;
+    z0 = (long long)z * a.nxy;
+    zm = (long long)(z == 0 ? a.nz - 1 : z - 1) * a.nxy;
+    zp = (long long)(z == a.nz - 1 ? 0 : z + 1) * a.nxy;
+  }
+  __device__ __forceinline__ long long at(int dx, int dy, int dz) const {
+    return (dx < 0 ? xm : dx > 0 ? xp : x) + (dy < 0 ? ym : dy > 0 ? yp : y0) + (dz < 0 ? zm : dz > 0 ? zp : z0);
+  }
+};
+
+template <int Q, class S>
+__device__ __forceinline__ void gather_coded(const Args& a, const S* src, int x, int y, int z, long long n,
+                                             unsigned long long code, typename Codec<S>::C* h) {
+  const Nbr nb(a, x, y, z);
+  sfor<0, Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    const int c = int(code >> (2 * i)) & 3;
+    int p;
+    long long m;
+    if (c == 0) { p = opp<Q>(i); m = nb.at(-Lat<Q>::cx(i), -Lat<Q>::cy(i), -Lat<Q>::cz(i)); }
+    else if (c == 1) { p = i; m = n; }
+    else slot_of<Q>(a, x, y, z, n, i, p, m);
+    h[i] = Codec<S>::ld(src + (long long)p * a.stride + m);
+  });
+}
+
+template <int Q, class S>
+__device__ __forceinline__ void scatter_coded(const Args& a, S* dst, int x, int y, int z, long long n,
+                                              unsigned long long code, const typename Codec<S>::C* h) {
+  const Nbr nb(a, x, y, z);
+  sfor<0, Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    const int c = int(code >> (2 * i)) & 3;
+    int p;
+    long long m;
+    if (c == 0) { p = opp<Q>(i); m = nb.at(-Lat<Q>::cx(i), -Lat<Q>::cy(i), -Lat<Q>::cz(i)); }
+    else if (c == 1) { p = i; m = n; }
+    else slot_of<Q>(a, x, y, z, n, i, p, m);
+    Codec<S>::st(dst + (long long)p * a.stride + m, h[opp<Q>(i)]);
+  });
+}
+
 template <class C> __device__ __forceinline__ const C* cptr(const void* p) { return static_cast<const C*>(p); }
 template <class C> __device__ __forceinline__ C* cptr(void* p) { return static_cast<C*>(p); }
 
@@ -163,16 +216,21 @@ __global__ void __launch_bounds__(LIST_THREADS) k_list(const Args a) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= a.n_list) return;
   const long long n = a.lcell[k];
-  int x, y, z;
-  cell_coords(a, n, x, y, z);
+  const int x = a.lxyz[3 * k], y = a.lxyz[3 * k + 1], z = a.lxyz[3 * k + 2];
   const uint8_t t = a.type[n];
   const int kind = t & T_KIND;
   S* f = static_cast<S*>(a.f);
-  const bool near = (t & T_NEAR) != 0;
   C h[Q];
-  gather<Q, S, ODD ? LOAD_SLOTS : LOAD_LOCAL>(a, f, x, y, z, n, near, h);
-  collide_any<Q, C>(a, kind, t, y, z, n, k, h);
-  scatter<Q, S, ODD ? STORE_SLOTS : STORE_MIRROR>(a, f, x, y, z, n, near, h);
+  if constexpr (ODD) {
+    const unsigned long long code = a.lcode[k];
+    gather_coded<Q, S>(a, f, x, y, z, n, code, h);
+    collide_any<Q, C>(a, kind, t, y, z, n, k, h);
+    scatter_coded<Q, S>(a, f, x, y, z, n, code, h);
+  } else {
+    gather<Q, S, LOAD_LOCAL>(a, f, x, y, z, n, false, h);
+    collide_any<Q, C>(a, kind, t, y, z, n, k, h);
+    scatter<Q, S, STORE_MIRROR>(a, f, x, y, z, n, false, h);
+  }
 }
 
 // Out-of-place step for the adjoint's recomputation: natural-layout state fin -> natural-layout fout.

@@ -54,7 +54,7 @@ int geo_count_blocks(const GeoArgs&);
 void geo_list_count(const GeoArgs&, uint8_t* type, int* counts, cudaStream_t);
 void geo_list_write(const GeoArgs&, const uint8_t* type, const int* offsets, long long* lcell, cudaStream_t);
 void geo_list_meta(const GeoArgs&, const uint8_t* type, const long long* lcell, int n_list, int* nsum, int* wref,
-                   cudaStream_t);
+                   int* lxyz, unsigned long long* lcode, cudaStream_t);
 // source map (debug): for each (i, n): source population and cell, -1 for solid cells
 void geo_source_map(const GeoArgs&, const uint8_t* type, int64_t* src_dir, int64_t* src_cell, cudaStream_t);
 // FP64 final reduction of nblk partials (4 doubles each) into out[4], fixed order

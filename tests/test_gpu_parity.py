@@ -99,7 +99,7 @@ def test_fp64_step_parity(q, steps):
         assert np.abs(ug - uo).max() < 1e-12, w.name
         mo, po = o.reduce()
         mg, pg = g.reduce()
-        assert abs(mg - mo) < 1e-10 and np.abs(pg - po).max() < 1e-10
+        assert abs(mg - mo) < 1e-13 * mo and np.abs(pg - po).max() < 1e-13 * mo
 
 
 def test_fp64_taylor_green_32cube_200_steps():
@@ -171,8 +171,9 @@ def test_16bit_taylor_green_error(storage, bound):
 
 
 def test_16bit_matches_oracle_storage_emulation_one_step():
-    """One step of FP16 storage equals the oracle's FP16-rounded storage up to one rounding of the
-    stored deviation (FP32 vs FP64 arithmetic decides ties differently only at the last bit)."""
+    """One step of FP16 storage equals the oracle's FP16-rounded storage to within a few units in
+    the last place of the stored deviation: FP32 (GPU) and FP64 (oracle) arithmetic can round the
+    initial state and the stored result to neighbouring FP16 values."""
     w = I.random_box(12, 8, 6, seed=9, q=19, solid_frac=0.1, tau=0.7, cs=0.1)
     g = gpu_from(w, lbm.F16)
     o = oracle_from(w, storage=2)
@@ -183,7 +184,7 @@ def test_16bit_matches_oracle_storage_emulation_one_step():
     fl = w.mask != 1
     c, wts, *_ = O.lattice(19)
     dev = np.abs(fo[:, fl] - wts[:, None])
-    assert (np.abs(fg[:, fl] - fo[:, fl]) <= np.maximum(dev, 6.1e-5) * 2.0 ** -10 + 1e-12).all()
+    assert (np.abs(fg[:, fl] - fo[:, fl]) <= 4 * np.maximum(dev, 6.1e-5) * 2.0 ** -10 + 1e-12).all()
 
 
 # ---- adjoint -------------------------------------------------------------------------------------------------------------
