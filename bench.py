@@ -262,8 +262,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extra", action="store_true", help="skip the secondary forms and the CPU baseline")
-    ap.add_argument("--size", type=int, nargs=3, default=(256, 256, 256), metavar=("NX", "NY", "NZ"),
-                    help="channel size (the headline workload is 256 256 256; smaller sizes are for profiling)")
+    ap.add_argument("--size", type=int, nargs=3, default=None, metavar=("NX", "NY", "NZ"),
+                    help="grid size (the headline channel is 256 256 256; other sizes are for profiling)")
+    ap.add_argument("--workload", default="channel", choices=["channel", "canopy"],
+                    help="channel (headline) or the urban canopy (for profiling the boundary-list kernel)")
+    ap.add_argument("--kernel", default="auto", choices=["auto", "plain"], help="interior kernel variant")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -281,11 +284,20 @@ def main():
     build.build()
     lbm.lib()
 
-    nx, ny, nz = args.size
-    w = I.channel(nx=nx, ny=ny, nz=nz, seed=550 + rank, dtype=np.float32)
+    headline = args.workload == "channel" and args.size in (None, [256, 256, 256])
+    if args.workload == "channel":
+        nx, ny, nz = args.size or (256, 256, 256)
+        w = I.channel(nx=nx, ny=ny, nz=nz, seed=550 + rank, dtype=np.float32)
+        wname = WORKLOAD.replace("256x256x256", f"{nx}x{ny}x{nz}")
+    else:
+        nx, ny, nz = args.size or (512, 512, 256)
+        w = I.canopy(nx=nx, ny=ny, nz=nz, seed=2506, dtype=np.float32)
+        wname = f"urban canopy {nx}x{ny}x{nz} D3Q19 Smagorinsky + wall function, log-law inlet, FP32"
     stream = torch.cuda.current_stream()
     lat = lbm.Lattice.from_workload(w, storage=lbm.F32)
     lat.set_stream(stream)
+    if args.kernel == "plain":
+        lat.set_option(lbm.OPT_KERNEL, lbm.KERNEL_PLAIN)
     info = lat.info()
     lat.step(args.warmup)
     lat.sync()
@@ -307,7 +319,7 @@ def main():
     bulk_ms = ms[0] / args.steps
     peak, peak_src = peaks()
     achieved = bytes_bulk / (bulk_ms * 1e-3) / 1e9
-    traffic = kernel_traffic("k_bulk", "channel256") if tuple(args.size) == (256, 256, 256) else None
+    traffic = kernel_traffic("k_bulk", "channel256") if headline else None
     step_bytes = (info["N"] - info["n_solid"]) * Q19_FP32_BYTES + info["N"]
 
     # end to end through the C ABI with host buffers: geometry + initial state in, fields out
@@ -333,11 +345,10 @@ def main():
         "metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD if tuple(args.size) == (256, 256, 256) else WORKLOAD.replace("256x256x256", "%dx%dx%d" % tuple(args.size)),
-                   "cells": w.N, "parallelism": f"replicas x{world}",
+        "config": {"workload": wname, "kernel": args.kernel, "cells": w.N, "parallelism": f"replicas x{world}",
                    "l2": "state of 2.6 GB > 129 MB L2 between steps, no flush needed",
                    "non_solid_cells": info["N"] - info["n_solid"], "boundary_list_cells": info["n_list"]},
-        "roofline": {"bound": "hbm", "kernel": "k_bulk (interior cells)", "achieved": achieved, "peak": peak,
+        "roofline": {"bound": "hbm", "kernel": ("k_bulk_tma" if (args.kernel == "auto" and w.nx % 32 == 0 and w.nx <= 512) else "k_bulk") + " (interior cells)", "achieved": achieved, "peak": peak,
                      "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "bytes_per_launch": bytes_bulk, "launch_ms": bulk_ms,
                      "share_of_step": ms[0] / ms[2]},
@@ -347,7 +358,7 @@ def main():
         "gpu_launches": 2 * args.steps,
         "clocks": clocks,
     }
-    if rank == 0 and not args.no_extra:
+    if rank == 0 and not args.no_extra and headline:
         try:
             line["extra"] = secondary(lbm, I, torch)
         except Exception as e:  # reported, not hidden

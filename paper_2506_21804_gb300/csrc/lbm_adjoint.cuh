@@ -178,20 +178,22 @@ __device__ __forceinline__ void regularise_vjp(C rho, C ux, C uy, C uz, const C*
 }
 
 // Reverse of bc_inlet: h = gathered deviations, gout = dJ/dh'; lam = dJ/dh; gub += dJ/du_b.
+// Forward: s = sum_{c_x=0} h + 2 sum_{c_x<0} h, drho = (s + u_x)/(1 - u_x), rho = 1 + drho.
 template <int Q, class C>
 __device__ __forceinline__ void bc_inlet_vjp(const C* h, C ubx, C uby, C ubz, const C* gout, C* lam, C* gub) {
-  C s = C(1);
+  C s = C(0);
   sfor<0, Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
     if (Lat<Q>::cx(i) == 0) s += h[i];
     if (Lat<Q>::cx(i) < 0) s += C(2) * h[i];
   });
   const C den = C(1) - ubx;
-  const C rho = s / den;
+  const C rho = C(1) + (s + ubx) / den;
   C grho, gux, guy, guz;
   regularise_vjp<Q, C, KnownInlet<Q>>(rho, ubx, uby, ubz, gout, lam, grho, gux, guy, guz);
+  // rho = (1 + s) / (1 - u_x): d rho/ds = 1/den, d rho/du_x = (1 + s)/den^2
   const C gs = grho / den;
-  gux += grho * s / (den * den);
+  gux += grho * (C(1) + s) / (den * den);
   sfor<0, Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
     if (Lat<Q>::cx(i) == 0) lam[i] += gs;
@@ -200,16 +202,16 @@ __device__ __forceinline__ void bc_inlet_vjp(const C* h, C ubx, C uby, C ubz, co
   gub[0] += gux; gub[1] += guy; gub[2] += guz;
 }
 
-// Reverse of bc_outlet.
+// Reverse of bc_outlet (u_x = (s - (rho_out - 1))/rho_out).
 template <int Q, class C>
-__device__ __forceinline__ void bc_outlet_vjp(const C* h, C rho_out, const C* gout, C* lam) {
-  C s = C(1);
+__device__ __forceinline__ void bc_outlet_vjp(const C* h, C rho_out, C drho_out, const C* gout, C* lam) {
+  C s = C(0);
   sfor<0, Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
     if (Lat<Q>::cx(i) == 0) s += h[i];
     if (Lat<Q>::cx(i) > 0) s += C(2) * h[i];
   });
-  const C ux = s / rho_out - C(1);
+  const C ux = (s - drho_out) / rho_out;
   C grho, gux, guy, guz;
   regularise_vjp<Q, C, KnownOutlet<Q>>(rho_out, ux, C(0), C(0), gout, lam, grho, gux, guy, guz);
   const C gs = gux / rho_out;

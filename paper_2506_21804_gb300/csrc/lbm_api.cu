@@ -75,6 +75,8 @@ struct lbm_ctx {
   double rho_out = 1.0;
   bool wm = false;
   double kappa = 0.41, E = 9.52;
+  int kernel = 0;       // LBM_OPT_KERNEL value
+  int debug_stall = 0;  // LBM_OPT_DEBUG_STALL value
   int device = 0;
   cudaStream_t stream = 0;
   const Ops* ops = nullptr;
@@ -158,9 +160,12 @@ Args make_args(const lbm_ctx* c) {
   a.ref_wr = (c->t & 1) ? c->ref1.p : c->ref0.p;
   a.uin = c->uin.p;
   a.rho_out = c->rho_out;
+  a.drho_out = c->rho_out - 1.0;
   a.wm = c->wm ? 1 : 0;
   a.kappa = c->kappa;
   a.E = c->E;
+  a.kernel = c->kernel;
+  a.debug_stall = c->debug_stall;
   return a;
 }
 
@@ -197,6 +202,8 @@ int read_status(lbm_ctx* c) {
 }
 
 int status_code(lbm_ctx* c) {
+  if (c->status_seen & 4u)
+    return fail(LBM_ETIMEOUT, "a bounded wait in the staged step kernel ran out; the state is incomplete (re-initialise)");
   if (c->status_seen & ST_NAN) return fail(LBM_ENAN, "non-finite density or momentum seen by a step");
   return LBM_OK;
 }
@@ -681,6 +688,21 @@ int lbm_set_populations(lbm_ctx* c, const void* f, int dtype) {
   if ((rc = fill_refs(c)) != LBM_OK) return rc;
   CK(cudaStreamSynchronize(c->stream));
   return LBM_OK;
+}
+
+int lbm_set_option(lbm_ctx* c, int option, int value) {
+  if (!c) return fail(LBM_EINVAL, "null context");
+  switch (option) {
+    case LBM_OPT_KERNEL:
+      if (value != 0 && value != 1) return fail(LBM_EINVAL, "LBM_OPT_KERNEL takes 0 (auto) or 1 (plain)");
+      c->kernel = value;
+      return LBM_OK;
+    case LBM_OPT_DEBUG_STALL:
+      if (value != 0 && value != 1) return fail(LBM_EINVAL, "LBM_OPT_DEBUG_STALL takes 0 or 1");
+      c->debug_stall = value;
+      return LBM_OK;
+  }
+  return fail(LBM_EINVAL, "unknown option %d", option);
 }
 
 int lbm_info(lbm_ctx* c, int64_t out[10]) {

@@ -147,7 +147,10 @@ struct Args {
   void* ref_wr;            // C[3] per entry, written by reference cells this step
   const void* uin;         // C[3][ny*nz] inlet velocity
   double rho_out;
+  double drho_out;         // rho_out - 1, formed in double precision
   int wm;                  // wall model on
+  int kernel;              // interior kernel: 0 staged (bulk copies into shared memory) where the shape allows, 1 plain
+  int debug_stall;         // 1: the staged kernel also waits on a barrier nobody completes (tests the bounded wait)
   double kappa, E;
 };
 
@@ -301,31 +304,33 @@ template <int Q> struct KnownInlet { __host__ __device__ constexpr bool operator
 template <int Q> struct KnownOutlet { __host__ __device__ constexpr bool operator()(int i) const { return Lat<Q>::cx(i) >= 0; } };
 
 // Velocity inlet (inward normal +x): rho (1 - u_x) = sum_{c_x=0} f + 2 sum_{c_x<0} f.
-// With f = h + w and sum_{c_x=0} w + 2 sum_{c_x<0} w = 1 this is 1 + the same sums over h.
+// With f = h + w and sum_{c_x=0} w + 2 sum_{c_x<0} w = 1 the right side is 1 + s, s the same sums
+// over h; the density deviation is formed without cancellation as (s + u_x) / (1 - u_x).
 template <int Q, class C>
 __device__ __forceinline__ void bc_inlet(C* h, C ubx, C uby, C ubz) {
-  C s = C(1);
+  C s = C(0);
   sfor<0, Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
     if (Lat<Q>::cx(i) == 0) s += h[i];
     if (Lat<Q>::cx(i) < 0) s += C(2) * h[i];
   });
-  const C rho = s / (C(1) - ubx);
-  regularise<Q, C, KnownInlet<Q>>(h, rho - C(1), rho, ubx, uby, ubz);
+  const C den = C(1) - ubx;
+  const C drho = (s + ubx) / den;
+  regularise<Q, C, KnownInlet<Q>>(h, drho, C(1) + drho, ubx, uby, ubz);
 }
 
 // Pressure outlet (inward normal -x): rho = rho_out, rho_out (1 + u_x) = sum_{c_x=0} f + 2 sum_{c_x>0} f,
-// tangential velocity 0.
+// tangential velocity 0; u_x = (s - (rho_out - 1)) / rho_out with s the deviation sums.
 template <int Q, class C>
-__device__ __forceinline__ void bc_outlet(C* h, C rho_out) {
-  C s = C(1);
+__device__ __forceinline__ void bc_outlet(C* h, C rho_out, C drho_out) {
+  C s = C(0);
   sfor<0, Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
     if (Lat<Q>::cx(i) == 0) s += h[i];
     if (Lat<Q>::cx(i) > 0) s += C(2) * h[i];
   });
-  const C ux = s / rho_out - C(1);
-  regularise<Q, C, KnownOutlet<Q>>(h, rho_out - C(1), rho_out, ux, C(0), C(0));
+  const C ux = (s - drho_out) / rho_out;
+  regularise<Q, C, KnownOutlet<Q>>(h, drho_out, rho_out, ux, C(0), C(0));
 }
 
 // ---- Spalding wall function, Eq. (spaldingfunct) -----------------------------------------------------

@@ -1,0 +1,137 @@
+// Host launchers of one (lattice, storage) instantiation and its Ops table.
+#pragma once
+
+#include <cstdio>
+
+#include "lbm_kernels.cuh"
+#include "lbm_tma.cuh"
+
+namespace lbm {
+
+// ---- host launchers ------------------------------------------------------------------------------------
+inline dim3 bulk_block(const Args& a) {
+  int bx = a.nx >= 128 ? 128 : ((a.nx + 31) / 32) * 32;
+  int by = BULK_THREADS / bx;
+  if (by < 1) by = 1;
+  return dim3(bx, by, 1);
+}
+inline dim3 bulk_grid(const Args& a) {
+  dim3 b = bulk_block(a);
+  return dim3((a.nx + b.x - 1) / b.x, (a.ny + b.y - 1) / b.y, a.nz);
+}
+inline unsigned blocks_for(long long n, int t) { return unsigned((n + t - 1) / t); }
+
+template <int Q, class S>
+struct Impl {
+  using C = typename Codec<S>::C;
+  // Shared-memory layout of the staged kernel, or stages = 0 when the shape does not allow it.
+  static TmaLayout tma_layout(const Args& a) {
+    TmaLayout L{};
+    if (a.kernel != 0 || a.nx % 32 != 0 || a.nx > 512) return L;
+    L.pop_bytes = unsigned(a.nx * sizeof(S));
+    L.type_off = unsigned(Q) * L.pop_bytes;
+    unsigned end = L.type_off + unsigned(a.nx);
+    if (a.gamma) {
+      L.gamma_off = (end + 15u) & ~15u;
+      end = L.gamma_off + unsigned(a.nx * sizeof(C));
+    }
+    L.stage_bytes = (end + 127u) & ~127u;
+    L.tx_bytes = unsigned(Q) * L.pop_bytes + unsigned(a.nx) + (a.gamma ? unsigned(a.nx * sizeof(C)) : 0u);
+    int st = int((100u * 1024u) / L.stage_bytes);
+    if (st > 8) st = 8;
+    if (st < 2) st = (2u * L.stage_bytes <= 200u * 1024u) ? 2 : 0;
+    L.stages = st;
+    return L;
+  }
+  template <bool ODD>
+  static bool launch_tma(const Args& a, const TmaLayout& L, cudaStream_t s) {
+    auto kern = k_bulk_tma<Q, S, ODD>;
+    const size_t dyn = (size_t)L.stages * L.stage_bytes;
+    static size_t configured = 0;
+    static int per_sm = 0;
+    static int nsm = 0;
+    if (configured != dyn) {
+      if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(dyn)) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+      }
+      int dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, a.nx, dyn) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        return false;
+      }
+      configured = dyn;
+    }
+    const long long rows = (long long)a.ny * a.nz;
+    long long grid = (long long)per_sm * nsm;
+    if (grid > rows) grid = rows;
+    kern<<<unsigned(grid), a.nx, dyn, s>>>(a, L, a.debug_stall);
+    return true;
+  }
+  static void step_bulk(const Args& a, int odd, cudaStream_t s) {
+    const TmaLayout L = tma_layout(a);
+    if (L.stages >= 2) {
+      if (odd ? launch_tma<true>(a, L, s) : launch_tma<false>(a, L, s)) return;
+    }
+    if (odd) k_bulk<Q, S, true><<<bulk_grid(a), bulk_block(a), 0, s>>>(a);
+    else k_bulk<Q, S, false><<<bulk_grid(a), bulk_block(a), 0, s>>>(a);
+  }
+  static void step_list(const Args& a, int odd, cudaStream_t s) {
+    if (a.n_list <= 0) return;
+    if (odd) k_list<Q, S, true><<<blocks_for(a.n_list, LIST_THREADS), LIST_THREADS, 0, s>>>(a);
+    else k_list<Q, S, false><<<blocks_for(a.n_list, LIST_THREADS), LIST_THREADS, 0, s>>>(a);
+  }
+  static void init_eq(const Args& a, const void* rho, const void* u, int dtype, cudaStream_t s) {
+    k_init_eq<Q, S><<<blocks_for(a.N, 256), 256, 0, s>>>(a, rho, u, dtype);
+  }
+  static void moments(const Args& a, int swapped, void* rho, void* u, int dtype, cudaStream_t s) {
+    k_moments<Q, S><<<blocks_for(a.N, 128), 128, 0, s>>>(a, swapped, rho, u, dtype);
+  }
+  static void get_pops(const Args& a, int swapped, void* out, int dtype, cudaStream_t s) {
+    k_get_pops<Q, S><<<blocks_for(a.N, 128), 128, 0, s>>>(a, swapped, out, dtype);
+  }
+  static void set_pops(const Args& a, int swapped, const void* in, int dtype, cudaStream_t s) {
+    k_set_pops<Q, S><<<blocks_for(a.N, 128), 128, 0, s>>>(a, swapped, in, dtype);
+  }
+  static void ref_fill(const Args& a, int swapped, void* ref, cudaStream_t s) {
+    if (a.n_list <= 0) return;
+    k_ref_fill<Q, S><<<blocks_for(a.n_list, 128), 128, 0, s>>>(a, swapped, ref);
+  }
+  static void reduce(const Args& a, int swapped, double* partial, int nblk, cudaStream_t s) {
+    k_reduce<Q, S><<<nblk, 256, 0, s>>>(a, swapped, partial);
+  }
+  static void list_aux(const Args& a, const int* nsum, const float* wd, void* wnrm, void* wyw, cudaStream_t s) {
+    if (a.n_list <= 0) return;
+    k_list_aux<C><<<blocks_for(a.n_list, 128), 128, 0, s>>>(a, nsum, wd, static_cast<C*>(wnrm), static_cast<C*>(wyw));
+  }
+  static void step_oop(const Args& a, const void* fin, void* fout, cudaStream_t s) {
+    k_step_oop<Q, S><<<bulk_grid(a), bulk_block(a), 0, s>>>(a, static_cast<const S*>(fin), static_cast<S*>(fout));
+  }
+  static void reverse(const Args& a, const AdjArgs& d, cudaStream_t s) {
+    k_reverse<Q, S><<<bulk_grid(a), bulk_block(a), 0, s>>>(a, d);
+  }
+  static void plane_rho(const Args& a, const void* state, int swapped, int xa, int xb, double* acc, double wa, double wb,
+                        cudaStream_t s) {
+    k_plane_rho<Q, S><<<1, 1024, 0, s>>>(a, static_cast<const S*>(state), swapped, xa, xb, acc, wa, wb);
+  }
+  static void seed(const Args& a, void* lam, int xa, int xb, double wa, double wb, cudaStream_t s) {
+    k_seed<C><<<blocks_for(a.N, 256), 256, 0, s>>>(a, static_cast<C*>(lam), xa, xb, wa, wb, Q);
+  }
+  static void convert(const void* in, int idt, void* out, int odt, long long n, cudaStream_t s) {
+    const unsigned g = blocks_for(n, 256);
+    if (idt == 0 && odt == 0) k_convert<double, double><<<g, 256, 0, s>>>((const double*)in, (double*)out, n);
+    else if (idt == 0) k_convert<double, float><<<g, 256, 0, s>>>((const double*)in, (float*)out, n);
+    else if (odt == 0) k_convert<float, double><<<g, 256, 0, s>>>((const float*)in, (double*)out, n);
+    else k_convert<float, float><<<g, 256, 0, s>>>((const float*)in, (float*)out, n);
+  }
+  static const Ops* table() {
+    static const Ops ops = {Q,        int(sizeof(S)), int(sizeof(C)), step_bulk, step_list, init_eq,   moments,
+                            get_pops, set_pops,       ref_fill,       reduce,    list_aux,  step_oop,  reverse,
+                            plane_rho, seed,           convert};
+    return &ops;
+  }
+};
+
+}  // namespace lbm

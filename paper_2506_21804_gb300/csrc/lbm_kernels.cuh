@@ -161,7 +161,7 @@ __device__ __forceinline__ void apply_bc(const Args& a, int kind, int y, int z, 
     const long long pl = (long long)a.ny * a.nz, p = y + (long long)a.ny * z;
     bc_inlet<Q, C>(h, ub[p], ub[pl + p], ub[2 * pl + p]);
   } else if (kind == K_OUTFLOW) {
-    bc_outlet<Q, C>(h, C(a.rho_out));
+    bc_outlet<Q, C>(h, C(a.rho_out), C(a.drho_out));
   }
 }
 
@@ -509,7 +509,7 @@ __global__ void __launch_bounds__(BULK_THREADS) k_reverse(const Args a, const Ad
       const long long pl = (long long)a.ny * a.nz, p = y + (long long)a.ny * z;
       bc_inlet_vjp<Q, C>(h, ub[p], ub[pl + p], ub[2 * pl + p], gh, lam, gub);
     } else {
-      bc_outlet_vjp<Q, C>(h, C(a.rho_out), gh, lam);
+      bc_outlet_vjp<Q, C>(h, C(a.rho_out), C(a.drho_out), gh, lam);
     }
   } else {
     collide_fluid_vjp<Q, C>(h, gam, a, mu, lam, ggam);
@@ -546,81 +546,5 @@ __global__ void k_convert(const A* in, B* out, long long n) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i < n) out[i] = B(in[i]);
 }
-
-// ---- host launchers ------------------------------------------------------------------------------------
-inline dim3 bulk_block(const Args& a) {
-  int bx = a.nx >= 128 ? 128 : ((a.nx + 31) / 32) * 32;
-  int by = BULK_THREADS / bx;
-  if (by < 1) by = 1;
-  return dim3(bx, by, 1);
-}
-inline dim3 bulk_grid(const Args& a) {
-  dim3 b = bulk_block(a);
-  return dim3((a.nx + b.x - 1) / b.x, (a.ny + b.y - 1) / b.y, a.nz);
-}
-inline unsigned blocks_for(long long n, int t) { return unsigned((n + t - 1) / t); }
-
-template <int Q, class S>
-struct Impl {
-  using C = typename Codec<S>::C;
-  static void step_bulk(const Args& a, int odd, cudaStream_t s) {
-    if (odd) k_bulk<Q, S, true><<<bulk_grid(a), bulk_block(a), 0, s>>>(a);
-    else k_bulk<Q, S, false><<<bulk_grid(a), bulk_block(a), 0, s>>>(a);
-  }
-  static void step_list(const Args& a, int odd, cudaStream_t s) {
-    if (a.n_list <= 0) return;
-    if (odd) k_list<Q, S, true><<<blocks_for(a.n_list, LIST_THREADS), LIST_THREADS, 0, s>>>(a);
-    else k_list<Q, S, false><<<blocks_for(a.n_list, LIST_THREADS), LIST_THREADS, 0, s>>>(a);
-  }
-  static void init_eq(const Args& a, const void* rho, const void* u, int dtype, cudaStream_t s) {
-    k_init_eq<Q, S><<<blocks_for(a.N, 256), 256, 0, s>>>(a, rho, u, dtype);
-  }
-  static void moments(const Args& a, int swapped, void* rho, void* u, int dtype, cudaStream_t s) {
-    k_moments<Q, S><<<blocks_for(a.N, 128), 128, 0, s>>>(a, swapped, rho, u, dtype);
-  }
-  static void get_pops(const Args& a, int swapped, void* out, int dtype, cudaStream_t s) {
-    k_get_pops<Q, S><<<blocks_for(a.N, 128), 128, 0, s>>>(a, swapped, out, dtype);
-  }
-  static void set_pops(const Args& a, int swapped, const void* in, int dtype, cudaStream_t s) {
-    k_set_pops<Q, S><<<blocks_for(a.N, 128), 128, 0, s>>>(a, swapped, in, dtype);
-  }
-  static void ref_fill(const Args& a, int swapped, void* ref, cudaStream_t s) {
-    if (a.n_list <= 0) return;
-    k_ref_fill<Q, S><<<blocks_for(a.n_list, 128), 128, 0, s>>>(a, swapped, ref);
-  }
-  static void reduce(const Args& a, int swapped, double* partial, int nblk, cudaStream_t s) {
-    k_reduce<Q, S><<<nblk, 256, 0, s>>>(a, swapped, partial);
-  }
-  static void list_aux(const Args& a, const int* nsum, const float* wd, void* wnrm, void* wyw, cudaStream_t s) {
-    if (a.n_list <= 0) return;
-    k_list_aux<C><<<blocks_for(a.n_list, 128), 128, 0, s>>>(a, nsum, wd, static_cast<C*>(wnrm), static_cast<C*>(wyw));
-  }
-  static void step_oop(const Args& a, const void* fin, void* fout, cudaStream_t s) {
-    k_step_oop<Q, S><<<bulk_grid(a), bulk_block(a), 0, s>>>(a, static_cast<const S*>(fin), static_cast<S*>(fout));
-  }
-  static void reverse(const Args& a, const AdjArgs& d, cudaStream_t s) {
-    k_reverse<Q, S><<<bulk_grid(a), bulk_block(a), 0, s>>>(a, d);
-  }
-  static void plane_rho(const Args& a, const void* state, int swapped, int xa, int xb, double* acc, double wa, double wb,
-                        cudaStream_t s) {
-    k_plane_rho<Q, S><<<1, 1024, 0, s>>>(a, static_cast<const S*>(state), swapped, xa, xb, acc, wa, wb);
-  }
-  static void seed(const Args& a, void* lam, int xa, int xb, double wa, double wb, cudaStream_t s) {
-    k_seed<C><<<blocks_for(a.N, 256), 256, 0, s>>>(a, static_cast<C*>(lam), xa, xb, wa, wb, Q);
-  }
-  static void convert(const void* in, int idt, void* out, int odt, long long n, cudaStream_t s) {
-    const unsigned g = blocks_for(n, 256);
-    if (idt == 0 && odt == 0) k_convert<double, double><<<g, 256, 0, s>>>((const double*)in, (double*)out, n);
-    else if (idt == 0) k_convert<double, float><<<g, 256, 0, s>>>((const double*)in, (float*)out, n);
-    else if (odt == 0) k_convert<float, double><<<g, 256, 0, s>>>((const float*)in, (double*)out, n);
-    else k_convert<float, float><<<g, 256, 0, s>>>((const float*)in, (float*)out, n);
-  }
-  static const Ops* table() {
-    static const Ops ops = {Q,        int(sizeof(S)), int(sizeof(C)), step_bulk, step_list, init_eq,   moments,
-                            get_pops, set_pops,       ref_fill,       reduce,    list_aux,  step_oop,  reverse,
-                            plane_rho, seed,           convert};
-    return &ops;
-  }
-};
 
 }  // namespace lbm

@@ -1,5 +1,5 @@
 // Kernel instantiations for population storage type __nv_bfloat16.
-#include "lbm_kernels.cuh"
+#include "lbm_impl.cuh"
 
 namespace lbm {
 const Ops* ops_bf16(int q) {

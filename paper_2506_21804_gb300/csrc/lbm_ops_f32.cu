@@ -1,5 +1,5 @@
 // Kernel instantiations for population storage type float.
-#include "lbm_kernels.cuh"
+#include "lbm_impl.cuh"
 
 namespace lbm {
 const Ops* ops_f32(int q) {

@@ -1,0 +1,194 @@
+// Interior-cell step kernel with the populations of one x-row staged in shared memory by bulk
+// asynchronous copies (cp.async.bulk, completion through mbarriers), for rows whose byte sizes are
+// multiples of 16 (nx a multiple of 32, at most 512: one thread per cell of the row).
+//
+// A persistent CTA walks the rows r = blockIdx.x + j*gridDim.x; tile j goes to stage j % S of a ring
+// of S shared-memory stages. Thread 0 issues the copies of tile j + S as soon as every thread has
+// read tile j, so S - 1 tiles are in flight while one is computed. Per tile and direction i the
+// copied segment is the whole source row: on an even step the cell's own row of population i, on
+// an odd step row (y - c_iy, z - c_iz) of population opp(i), from which cell x takes element
+// (x - c_ix) mod nx. Every element of such a row is a slot owned by a cell of this tile (the AA
+// pattern gives each slot one owner), so the copy never races with another CTA's stores. Results
+// go straight to global memory with coalesced per-cell stores. Cells next to solids or outer faces
+// (NEAR) read through the general slot map instead of the staged row.
+//
+// Every wait is bounded in time; a wait that runs out sets ST_TIMEOUT in the status word, waits
+// (again bounded) for the copies this CTA has issued, and ends the kernel.
+#pragma once
+
+#include "lbm_kernels.cuh"  // gather, scatter, collide_fluid
+
+namespace lbm {
+
+constexpr unsigned ST_TIMEOUT = 4u;
+constexpr unsigned long long WAIT_LIMIT_NS = 1000000000ull;  // 1 s
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return static_cast<unsigned>(__cvta_generic_to_shared(p)); }
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for phase `parity` of the barrier, at most WAIT_LIMIT_NS; false if the limit ran out.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer();
+  for (;;) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (globaltimer() - t0 > WAIT_LIMIT_NS) return false;
+  }
+}
+
+// Global -> shared bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned), completing
+// on the barrier's transaction count.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+struct TmaLayout {
+  int stages;
+  unsigned pop_bytes;    // nx * sizeof(S)
+  unsigned stage_bytes;  // Q * pop_bytes + type row + gamma row, rounded up to 128
+  unsigned gamma_off;    // offset of the gamma row in a stage (0: none)
+  unsigned type_off;
+  unsigned tx_bytes;     // bytes delivered per tile
+};
+
+template <int Q, class S, bool ODD>
+__global__ void __launch_bounds__(512) k_bulk_tma(const Args a, const TmaLayout L, int debug_stall) {
+  using C = typename Codec<S>::C;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ unsigned long long full[8];
+  __shared__ unsigned long long never;
+  __shared__ int abort_flag;
+  const int tid = threadIdx.x;
+  const long long nrows = (long long)a.ny * a.nz;
+  const int G = gridDim.x;
+  S* f = static_cast<S*>(a.f);
+  if (tid == 0) {
+    for (int s = 0; s < L.stages; ++s) mbar_init(&full[s], 1);
+    mbar_init(&never, 1);
+    abort_flag = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  auto issue = [&](long long j) {
+    const long long r = blockIdx.x + j * G;
+    if (r >= nrows) return;
+    const int s = int(j % L.stages);
+    unsigned char* st = smem + (size_t)s * L.stage_bytes;
+    const int y = int(r % a.ny), z = int(r / a.ny);
+    fence_proxy_async();
+    mbar_expect_tx(&full[s], L.tx_bytes);
+    sfor<0, Q>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      long long row;
+      int p;
+      if constexpr (ODD) {
+        int sy = y - Lat<Q>::cy(i), sz = z - Lat<Q>::cz(i);
+        sy = sy < 0 ? sy + a.ny : (sy >= a.ny ? sy - a.ny : sy);
+        sz = sz < 0 ? sz + a.nz : (sz >= a.nz ? sz - a.nz : sz);
+        row = sy + (long long)a.ny * sz;
+        p = opp<Q>(i);
+      } else {
+        row = r;
+        p = i;
+      }
+      bulk_g2s(st + (size_t)i * L.pop_bytes, f + (long long)p * a.stride + row * a.nx, L.pop_bytes, &full[s]);
+    });
+    bulk_g2s(st + L.type_off, a.type + r * a.nx, (unsigned)a.nx, &full[s]);
+    if (L.gamma_off) bulk_g2s(st + L.gamma_off, static_cast<const C*>(a.gamma) + r * a.nx, unsigned(a.nx * sizeof(C)), &full[s]);
+  };
+
+  if (tid == 0)
+    for (int j = 0; j < L.stages; ++j) issue(j);
+
+  const int x = tid;
+  long long issued_hi = L.stages;  // tiles [0, issued_hi) have been issued
+  for (long long j = 0;; ++j) {
+    const long long r = blockIdx.x + j * G;
+    if (r >= nrows) break;
+    const int s = int(j % L.stages);
+    const unsigned parity = unsigned((j / L.stages) & 1);
+    bool ok = mbar_wait_bounded(&full[s], parity);
+    if (ok && debug_stall && j == 0) ok = mbar_wait_bounded(&never, 0);
+    if (!ok) abort_flag = 1;
+    __syncthreads();
+    if (abort_flag) {
+      if (tid == 0) {
+        atomicOr(a.status, ST_TIMEOUT);
+        // let the copies this CTA issued land before the CTA exits (bounded)
+        for (long long k = j; k < issued_hi; ++k) {
+          const long long rk = blockIdx.x + k * G;
+          if (rk >= nrows) break;
+          mbar_wait_bounded(&full[k % L.stages], unsigned((k / L.stages) & 1));
+        }
+      }
+      __syncthreads();
+      return;
+    }
+    const unsigned char* st = smem + (size_t)s * L.stage_bytes;
+    const uint8_t t = st[L.type_off + x];
+    const bool active = x < a.nx && !(t & (T_LIST | T_KIND));
+    const bool near = (t & T_NEAR) != 0;
+    const int y = int(r % a.ny), z = int(r / a.ny);
+    const long long n = r * a.nx + x;
+    C h[Q];
+    C gam = C(1);
+    if (active && !near) {
+      const S* sp = reinterpret_cast<const S*>(st);
+      const int xm = x == 0 ? a.nx - 1 : x - 1, xp = x == a.nx - 1 ? 0 : x + 1;
+      sfor<0, Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        const int xs = ODD ? (Lat<Q>::cx(i) > 0 ? xm : (Lat<Q>::cx(i) < 0 ? xp : x)) : x;
+        h[i] = Codec<S>::ld(sp + (size_t)i * a.nx + xs);
+      });
+      if (L.gamma_off) gam = reinterpret_cast<const C*>(st + L.gamma_off)[x];
+    }
+    __syncthreads();
+    if (tid == 0 && issued_hi < j + 1 + L.stages) {
+      issue(j + L.stages);
+      issued_hi = j + 1 + L.stages;
+    }
+    if (!active) continue;
+    if (near) {
+      gather<Q, S, ODD ? LOAD_SLOTS : LOAD_LOCAL>(a, f, x, y, z, n, true, h);
+      gam = gamma_at<C>(a, n);
+    }
+    C rho, urx, ury, urz;
+    collide_fluid<Q, C>(h, gam, a, rho, urx, ury, urz);
+    if (!finite_all<C>(rho, urx, ury, urz)) atomicOr(a.status, ST_NAN);
+    scatter<Q, S, ODD ? STORE_SLOTS : STORE_MIRROR>(a, f, x, y, z, n, near, h);
+  }
+}
+
+}  // namespace lbm

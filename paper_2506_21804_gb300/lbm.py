@@ -20,6 +20,8 @@ DTYPE_F64, DTYPE_F32 = 0, 1
 FACE_PERIODIC, FACE_WALL, FACE_SLIP, FACE_OPEN = 0, 1, 2, 3
 KIND_FLUID, KIND_SOLID, KIND_WALL, KIND_INFLOW, KIND_OUTFLOW = 0, 1, 2, 3, 4
 T_KIND, T_REF, T_NEAR, T_LIST = 7, 8, 16, 32
+OPT_KERNEL, OPT_DEBUG_STALL = 1, 2
+KERNEL_AUTO, KERNEL_PLAIN = 0, 1
 STORAGE_NAMES = {"f64": F64, "f32": F32, "f16": F16, "bf16": BF16}
 
 _ERR_NAMES = {EINVAL: "LBM_EINVAL", ENOMEM: "LBM_ENOMEM", ECUDA: "LBM_ECUDA", ENAN: "LBM_ENAN",
@@ -70,6 +72,7 @@ SIGNATURES = {
     "lbm_load": (_i, [_p, _p, ctypes.c_size_t]),
     "lbm_set_stream": (_i, [_p, _p]),
     "lbm_info": (_i, [_p, _p]),
+    "lbm_set_option": (_i, [_p, _i, _i]),
     "lbm_debug_dump": (_i, [_p, _i, _p, ctypes.c_size_t]),
 }
 
@@ -231,6 +234,9 @@ class Lattice:
     def set_populations(self, f):
         a = _Arr(f)
         _check(lib().lbm_set_populations(self.h, a.ptr, a.code))
+
+    def set_option(self, option, value):
+        _check(lib().lbm_set_option(self.h, int(option), int(value)))
 
     def info(self):
         out = np.zeros(10, np.int64)

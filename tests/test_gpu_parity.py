@@ -437,3 +437,46 @@ def test_full_size_canopy_512_sampled(q):
     w = I.canopy(nx=512, ny=512, nz=256, q=q, seed=2506, dtype=np.float32)
     er, eu = _sampled_full_size(w, lbm.F32, steps=2, samples=32, R=5, seed=2)
     assert er < 1e-6 and eu < 1e-5, (er, eu)
+
+
+# ---- staged interior kernel (bulk copies into shared memory) -----------------------------------------------
+@pytest.mark.parametrize("q,storage", [(19, lbm.F32), (27, lbm.F32), (19, lbm.F16), (19, lbm.F64)])
+def test_staged_kernel_matches_plain_kernel(q, storage):
+    """nx a multiple of 32 selects the staged kernel; it must give the plain kernel's results."""
+    cases = [I.channel(nx=64, ny=34, nz=12, q=q, seed=5, dtype=np.float64),
+             I.canopy(nx=128, ny=64, nz=40, q=q, seed=2506, crop=(64, 0, 0), domain=(1024, 512, 256), dtype=np.float64),
+             with_features(I.random_box(32, 12, 10, seed=6, q=q, solid_frac=0.1, tau=0.6, cs=0.1, faces=(0, 0, 2, 2, 1, 2)))]
+    for w in cases:
+        a = gpu_from(w, storage)
+        b = gpu_from(w, storage)
+        b.set_option(lbm.OPT_KERNEL, lbm.KERNEL_PLAIN)
+        for steps in (1, 2, 9):
+            a.step(steps)
+            b.step(steps)
+            fa = a.get_populations()
+            fb = b.get_populations()
+            tol = {lbm.F64: 1e-14, lbm.F32: 2e-7, lbm.F16: 2e-3}[storage]
+            assert np.abs(fa - fb).max() <= tol, (w.name, steps, np.abs(fa - fb).max())
+        a.sync()
+        b.sync()
+
+
+def test_staged_kernel_bounded_wait_reports_timeout_and_recovers():
+    """The staged kernel's waits are bounded: with a barrier that nothing completes, the step ends
+    after the one-second limit, the status reads LBM_ETIMEOUT, and the context stays usable."""
+    w = I.channel(nx=64, ny=18, nz=8, seed=5, dtype=np.float32)
+    g = gpu_from(w, lbm.F32)
+    g.set_option(lbm.OPT_DEBUG_STALL, 1)
+    g.step(1)
+    with pytest.raises(lbm.LBMError) as e:
+        g.sync()
+    assert e.value.code == lbm.ETIMEOUT
+    g.set_option(lbm.OPT_DEBUG_STALL, 0)
+    g.init_equilibrium(np.asarray(w.rho0, np.float32), np.asarray(w.u0, np.float32))
+    g.step(4)
+    g.sync()
+    o = oracle_from(w, cast32=True)
+    o.step(4)
+    rg, _ = g.moments()
+    ro, _ = o.moments()
+    assert np.abs(rg - ro).max() < 1e-6
