@@ -153,7 +153,8 @@ int lbm_load(lbm_ctx* ctx, const void* buf, size_t len);
 int lbm_set_stream(lbm_ctx* ctx, void* cuda_stream);
 
 /* Options. LBM_OPT_KERNEL: 0 (default) runs interior cells with the shared-memory staged kernel
- * (bulk asynchronous copies of whole x-rows) when nx is a multiple of 32 and at most 512, else
+ * (bulk asynchronous copies of 128-cell x-segments) when nx is a multiple of 128 and the storage
+ * is not LBM_F64, else
  * the plain kernel; 1 always runs the plain kernel. LBM_OPT_DEBUG_STALL: 1 makes the staged kernel
  * also wait on a barrier that nothing completes, so that its bounded wait (one second) runs out:
  * the step then ends early, the status word records it and the next synchronising call returns

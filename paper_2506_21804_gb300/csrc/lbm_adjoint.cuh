@@ -132,8 +132,15 @@ __device__ __forceinline__ void collide_fluid_vjp(const C* h, C gamma, const Arg
   grho -= (gux * ux + guy * uy + guz * uz) * ir;
   sfor<0, Q>([&](auto I) {
     constexpr int i = decltype(I)::value, cx = Lat<Q>::cx(i), cy = Lat<Q>::cy(i), cz = Lat<Q>::cz(i);
-    lam[i] = k * mu[i] + grho + C(cx) * gjx + C(cy) * gjy + C(cz) * gjz + C(cx * cx) * gsxx + C(cy * cy) * gsyy +
-             C(cz * cz) * gszz + C(cx * cy) * gsxy + C(cx * cz) * gsxz + C(cy * cz) * gsyz;
+    C v = k * mu[i] + grho;
+    if constexpr (i != 0) v += cdot_i<Q, i>(gjx, gjy, gjz);
+    if constexpr (cx != 0) v += gsxx;
+    if constexpr (cy != 0) v += gsyy;
+    if constexpr (cz != 0) v += gszz;
+    if constexpr (cx * cy != 0) v += cmul<cx * cy>(gsxy);
+    if constexpr (cx * cz != 0) v += cmul<cx * cz>(gsxz);
+    if constexpr (cy * cz != 0) v += cmul<cy * cz>(gsyz);
+    lam[i] = v;
   });
 }
 
@@ -157,8 +164,14 @@ __device__ __forceinline__ void regularise_vjp(C rho, C ux, C uy, C uz, const C*
   C gne[Q];
   sfor<0, Q>([&](auto I) {
     constexpr int i = decltype(I)::value, cx = Lat<Q>::cx(i), cy = Lat<Q>::cy(i), cz = Lat<Q>::cz(i);
-    gne[i] = C(cx * cx) * gpxx + C(cy * cy) * gpyy + C(cz * cz) * gpzz + C(cx * cy) * gpxy + C(cx * cz) * gpxz +
-             C(cy * cz) * gpyz;
+    C v = C(0);
+    if constexpr (cx != 0) v += gpxx;
+    if constexpr (cy != 0) v += gpyy;
+    if constexpr (cz != 0) v += gpzz;
+    if constexpr (cx * cy != 0) v += cmul<cx * cy>(gpxy);
+    if constexpr (cx * cz != 0) v += cmul<cx * cz>(gpxz);
+    if constexpr (cy * cz != 0) v += cmul<cy * cz>(gpyz);
+    gne[i] = v;
   });
   sfor<0, Q>([&](auto I) {
     constexpr int i = decltype(I)::value;

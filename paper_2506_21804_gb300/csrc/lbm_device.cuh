@@ -195,12 +195,36 @@ __device__ __forceinline__ void slot_of(const Args& a, int x, int y, int z, long
 }
 
 // ---- per-cell physics ------------------------------------------------------------------------------------
+// Products with the integer lattice components written so that zero terms never appear: IEEE
+// arithmetic does not allow a compiler to drop 0*x or 0+x, so the tables are folded here.
+template <int A, class C> __device__ __forceinline__ C cmul(C v) {
+  if constexpr (A == 1) return v;
+  else if constexpr (A == -1) return -v;
+  else return C(A) * v;
+}
+template <int X, int Y, int Z, class C> __device__ __forceinline__ C cdot(C x, C y, C z) {
+  if constexpr (X == 0 && Y == 0 && Z == 0) return C(0);
+  else if constexpr (Y == 0 && Z == 0) return cmul<X>(x);
+  else if constexpr (X == 0 && Z == 0) return cmul<Y>(y);
+  else if constexpr (X == 0 && Y == 0) return cmul<Z>(z);
+  else if constexpr (Z == 0) return cmul<X>(x) + cmul<Y>(y);
+  else if constexpr (Y == 0) return cmul<X>(x) + cmul<Z>(z);
+  else if constexpr (X == 0) return cmul<Y>(y) + cmul<Z>(z);
+  else return cmul<X>(x) + cmul<Y>(y) + cmul<Z>(z);
+}
+template <int Q, int I, class C> __device__ __forceinline__ C cdot_i(C x, C y, C z) {
+  return cdot<Lat<Q>::cx(I), Lat<Q>::cy(I), Lat<Q>::cz(I)>(x, y, z);
+}
+
 // Equilibrium deviation f_i^eq(rho, v) - w_i = w_i (drho + rho (3 c.v + 4.5 (c.v)^2 - 1.5 v.v)).
 template <int Q, class C, int I>
 __device__ __forceinline__ C heq(C drho, C rho, C vx, C vy, C vz, C vsq) {
-  constexpr int cx = Lat<Q>::cx(I), cy = Lat<Q>::cy(I), cz = Lat<Q>::cz(I);
-  C cv = C(cx) * vx + C(cy) * vy + C(cz) * vz;
-  return wgt<Q, C>(I) * (drho + rho * (C(3) * cv + C(4.5) * cv * cv - C(1.5) * vsq));
+  if constexpr (I == 0) {
+    return wgt<Q, C>(I) * (drho - rho * (C(1.5) * vsq));
+  } else {
+    const C cv = cdot_i<Q, I>(vx, vy, vz);
+    return wgt<Q, C>(I) * (drho + rho * (C(3) * cv + C(4.5) * cv * cv - C(1.5) * vsq));
+  }
 }
 
 template <int Q, class C>
@@ -219,9 +243,14 @@ __device__ __forceinline__ void sums(const C* h, C& drho, C& jx, C& jy, C& jz) {
 template <int Q, class C, int I>
 __device__ __forceinline__ C qcontract(C axx, C ayy, C azz, C axy, C axz, C ayz) {
   constexpr int cx = Lat<Q>::cx(I), cy = Lat<Q>::cy(I), cz = Lat<Q>::cz(I);
-  C tr = (axx + ayy + azz) * C(1.0 / 3.0);
-  return C(cx * cx) * axx + C(cy * cy) * ayy + C(cz * cz) * azz + C(2 * cx * cy) * axy + C(2 * cx * cz) * axz +
-         C(2 * cy * cz) * ayz - tr;
+  C r = -(axx + ayy + azz) * C(1.0 / 3.0);
+  if constexpr (cx != 0) r += axx;
+  if constexpr (cy != 0) r += ayy;
+  if constexpr (cz != 0) r += azz;
+  if constexpr (cx * cy != 0) r += cmul<2 * cx * cy>(axy);
+  if constexpr (cx * cz != 0) r += cmul<2 * cx * cz>(axz);
+  if constexpr (cy * cz != 0) r += cmul<2 * cy * cz>(ayz);
+  return r;
 }
 
 // BGK + Smagorinsky + porosity + exact-difference force on the deviations h (in place).

@@ -27,20 +27,19 @@ struct Impl {
   // Shared-memory layout of the staged kernel, or stages = 0 when the shape does not allow it.
   static TmaLayout tma_layout(const Args& a) {
     TmaLayout L{};
-    if (a.kernel != 0 || a.nx % 32 != 0 || a.nx > 512) return L;
-    L.pop_bytes = unsigned(a.nx * sizeof(S));
+    if (a.kernel != 0 || a.nx % TMA_W != 0 || sizeof(S) == 8) return L;  // FP64 (reference form) stays plain
+    L.pop_bytes = unsigned(TMA_W * sizeof(S));
     L.type_off = unsigned(Q) * L.pop_bytes;
-    unsigned end = L.type_off + unsigned(a.nx);
+    unsigned end = L.type_off + unsigned(TMA_W);
     if (a.gamma) {
       L.gamma_off = (end + 15u) & ~15u;
-      end = L.gamma_off + unsigned(a.nx * sizeof(C));
+      end = L.gamma_off + unsigned(TMA_W * sizeof(C));
     }
     L.stage_bytes = (end + 127u) & ~127u;
-    L.tx_bytes = unsigned(Q) * L.pop_bytes + unsigned(a.nx) + (a.gamma ? unsigned(a.nx * sizeof(C)) : 0u);
-    int st = int((100u * 1024u) / L.stage_bytes);
-    if (st > 8) st = 8;
-    if (st < 2) st = (2u * L.stage_bytes <= 200u * 1024u) ? 2 : 0;
-    L.stages = st;
+    L.tx_bytes = unsigned(Q) * L.pop_bytes + unsigned(TMA_W) + (a.gamma ? unsigned(TMA_W * sizeof(C)) : 0u);
+    // two stages: the copies of one tile land while the other is computed; shared memory is better
+    // spent on more resident CTAs (latency hiding for the collision) than on deeper rings
+    L.stages = 2;
     return L;
   }
   template <bool ODD>
@@ -58,16 +57,16 @@ struct Impl {
       int dev = 0;
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, a.nx, dyn) != cudaSuccess || per_sm < 1) {
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TMA_W + 32, dyn) != cudaSuccess || per_sm < 1) {
         cudaGetLastError();
         return false;
       }
       configured = dyn;
     }
-    const long long rows = (long long)a.ny * a.nz;
+    const long long tiles = (long long)a.ny * a.nz * (a.nx / TMA_W);
     long long grid = (long long)per_sm * nsm;
-    if (grid > rows) grid = rows;
-    kern<<<unsigned(grid), a.nx, dyn, s>>>(a, L, a.debug_stall);
+    if (grid > tiles) grid = tiles;
+    kern<<<unsigned(grid), TMA_W + 32, dyn, s>>>(a, L, a.debug_stall);
     return true;
   }
   static void step_bulk(const Args& a, int odd, cudaStream_t s) {

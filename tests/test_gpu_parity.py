@@ -440,12 +440,12 @@ def test_full_size_canopy_512_sampled(q):
 
 
 # ---- staged interior kernel (bulk copies into shared memory) -----------------------------------------------
-@pytest.mark.parametrize("q,storage", [(19, lbm.F32), (27, lbm.F32), (19, lbm.F16), (19, lbm.F64)])
+@pytest.mark.parametrize("q,storage", [(19, lbm.F32), (27, lbm.F32), (19, lbm.F16), (19, lbm.BF16)])
 def test_staged_kernel_matches_plain_kernel(q, storage):
-    """nx a multiple of 32 selects the staged kernel; it must give the plain kernel's results."""
-    cases = [I.channel(nx=64, ny=34, nz=12, q=q, seed=5, dtype=np.float64),
+    """nx a multiple of 128 selects the staged kernel; it must give the plain kernel's results."""
+    cases = [I.channel(nx=256, ny=34, nz=6, q=q, seed=5, dtype=np.float64),
              I.canopy(nx=128, ny=64, nz=40, q=q, seed=2506, crop=(64, 0, 0), domain=(1024, 512, 256), dtype=np.float64),
-             with_features(I.random_box(32, 12, 10, seed=6, q=q, solid_frac=0.1, tau=0.6, cs=0.1, faces=(0, 0, 2, 2, 1, 2)))]
+             with_features(I.random_box(128, 9, 7, seed=6, q=q, solid_frac=0.1, tau=0.6, cs=0.1, faces=(0, 0, 2, 2, 1, 2)))]
     for w in cases:
         a = gpu_from(w, storage)
         b = gpu_from(w, storage)
@@ -455,7 +455,7 @@ def test_staged_kernel_matches_plain_kernel(q, storage):
             b.step(steps)
             fa = a.get_populations()
             fb = b.get_populations()
-            tol = {lbm.F64: 1e-14, lbm.F32: 2e-7, lbm.F16: 2e-3}[storage]
+            tol = {lbm.F32: 2e-7, lbm.F16: 2e-3, lbm.BF16: 2e-2}[storage]
             assert np.abs(fa - fb).max() <= tol, (w.name, steps, np.abs(fa - fb).max())
         a.sync()
         b.sync()
@@ -464,7 +464,7 @@ def test_staged_kernel_matches_plain_kernel(q, storage):
 def test_staged_kernel_bounded_wait_reports_timeout_and_recovers():
     """The staged kernel's waits are bounded: with a barrier that nothing completes, the step ends
     after the one-second limit, the status reads LBM_ETIMEOUT, and the context stays usable."""
-    w = I.channel(nx=64, ny=18, nz=8, seed=5, dtype=np.float32)
+    w = I.channel(nx=128, ny=18, nz=8, seed=5, dtype=np.float32)
     g = gpu_from(w, lbm.F32)
     g.set_option(lbm.OPT_DEBUG_STALL, 1)
     g.step(1)
