@@ -173,6 +173,28 @@ int lbm_info(lbm_ctx* ctx, int64_t out[10]);
  * (i, n) (q*N each, i-major; f_i(n, t+1) = f*_j(m, t); -1 for solid cells). */
 int lbm_debug_dump(lbm_ctx* ctx, int which, int64_t* out, size_t count);
 
+/* Allocation-free reduction (no counterpart in the paper: an addition for callers of this library).
+ * Some callers cannot let a library allocate device memory: applications whose pool allocator owns
+ * all device memory, codes running at the memory limit, loops that must not pay for an allocation
+ * between steps. lbm_reduce_static serves them: it sums mass = sum_i f_i and momentum
+ * sum_i f_i c_i over the cells of a caller-owned population array, keeping its partial sums in a
+ * fixed static device array (4 doubles per 65536 cells, 128 KiB, held by every GPU that loads the
+ * library until the process exits) and calling no cudaMalloc, cudaFree or allocating routine.
+ *   lattice: 19 or 27 (velocity order as above); f: device pointer to q*n_cells values of dtype
+ *   (LBM_DTYPE_F32 or LBM_DTYPE_F64), f[i*n_cells + n] (populations, not deviations);
+ *   mask: device pointer to n_cells mask bytes (cells with code LBM_CELL_SOLID are skipped) or NULL;
+ *   n_cells: 1..LBM_REDUCE_STATIC_MAX_CELLS, larger sizes are rejected with LBM_EINVAL;
+ *   out: 4 doubles (mass, momentum x, y, z), device memory (written on the stream) or host memory
+ *   (the call then synchronises the stream); stream: cudaStream_t or NULL for the default stream.
+ * The first call made on a device looks up the static array's device address (make that first
+ * call before any stream capture). All calls share the array, so calls that overlap on the GPU
+ * race; each call overwrites the partial sums it reads. Errors: LBM_EINVAL (arguments), LBM_ECUDA;
+ * message in lbm_reduce_static_error(). */
+#define LBM_REDUCE_STATIC_MAX_CELLS 268435456LL
+int lbm_reduce_static(int lattice, const void* f, int dtype, const uint8_t* mask, int64_t n_cells, double* out,
+                      void* stream);
+const char* lbm_reduce_static_error(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -73,6 +73,8 @@ SIGNATURES = {
     "lbm_set_stream": (_i, [_p, _p]),
     "lbm_info": (_i, [_p, _p]),
     "lbm_set_option": (_i, [_p, _i, _i]),
+    "lbm_reduce_static": (_i, [_i, _p, _i, _p, ctypes.c_int64, _p, _p]),
+    "lbm_reduce_static_error": (ctypes.c_char_p, []),
     "lbm_debug_dump": (_i, [_p, _i, _p, ctypes.c_size_t]),
 }
 
