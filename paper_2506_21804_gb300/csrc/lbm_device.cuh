@@ -253,28 +253,40 @@ __device__ __forceinline__ C qcontract(C axx, C ayy, C azz, C axy, C axz, C ayz)
   return r;
 }
 
+template <class C> __device__ __forceinline__ C rcp(C x) { return C(1) / x; }
+template <> __device__ __forceinline__ float rcp<float>(float x) { return __fdividef(1.0f, x); }
+
 // BGK + Smagorinsky + porosity + exact-difference force on the deviations h (in place).
 // Returns the density and the reported velocity u + F/(2 rho).
+//
+// Written over opposite pairs (i, i + H): with s = h_i + h_i', d = h_i - h_i' the moments are
+// drho = h_0 + sum s, j = sum c d, sum c c h = sum c c s; and with
+//   h*_i = f^eq_i(v) - w_i + k (h_i - (f^eq_i(u) - w_i)),   k = 1 - 1/tau,
+// f^eq_i(v) - k f^eq_i(u) - (1 - k) w_i = w_i [sym +- anti] where the sign flips with c_i:
+//   sym  = (1 - k) drho - 1.5 rho (v.v - k u.u) + 4.5 rho ((c.v)^2 - k (c.u)^2)
+//   anti = 3 rho (c.v - k c.u).
 template <int Q, class C>
 __device__ __forceinline__ void collide_fluid(C* h, C gamma, const Args& a, C& rho_o, C& urx, C& ury, C& urz) {
-  C drho, jx, jy, jz;
-  sums<Q, C>(h, drho, jx, jy, jz);
-  const C rho = C(1) + drho, ir = C(1) / rho;
+  constexpr int H = Lat<Q>::H;
+  C drho = h[0], jx = C(0), jy = C(0), jz = C(0);
+  C sxx = C(0), syy = C(0), szz = C(0), sxy = C(0), sxz = C(0), syz = C(0);
+  sfor<1, H + 1>([&](auto I) {
+    constexpr int i = decltype(I)::value, cx = Lat<Q>::cx(i), cy = Lat<Q>::cy(i), cz = Lat<Q>::cz(i);
+    const C sp = h[i] + h[i + H], dp = h[i] - h[i + H];
+    drho += sp;
+    if constexpr (cx != 0) { jx += cmul<cx>(dp); sxx += sp; }
+    if constexpr (cy != 0) { jy += cmul<cy>(dp); syy += sp; }
+    if constexpr (cz != 0) { jz += cmul<cz>(dp); szz += sp; }
+    if constexpr (cx * cy != 0) sxy += cmul<cx * cy>(sp);
+    if constexpr (cx * cz != 0) sxz += cmul<cx * cz>(sp);
+    if constexpr (cy * cz != 0) syz += cmul<cy * cz>(sp);
+  });
+  const C rho = C(1) + drho, ir = rcp(rho);
   const C ux = jx * ir, uy = jy * ir, uz = jz * ir;
   const C usq = ux * ux + uy * uy + uz * uz;
   C tau = C(a.tau0);
   if (a.smag > 0.0) {
     // Pi^neq = sum c c h - drho/3 I - rho u u (second moment of the 2nd-order equilibrium).
-    C sxx = 0, syy = 0, szz = 0, sxy = 0, sxz = 0, syz = 0;
-    sfor<0, Q>([&](auto I) {
-      constexpr int i = decltype(I)::value, cx = Lat<Q>::cx(i), cy = Lat<Q>::cy(i), cz = Lat<Q>::cz(i);
-      if (cx) sxx += h[i];
-      if (cy) syy += h[i];
-      if (cz) szz += h[i];
-      if (cx * cy) sxy += C(cx * cy) * h[i];
-      if (cx * cz) sxz += C(cx * cz) * h[i];
-      if (cy * cz) syz += C(cy * cz) * h[i];
-    });
     const C d3 = drho * C(1.0 / 3.0);
     const C pxx = sxx - d3 - rho * ux * ux, pyy = syy - d3 - rho * uy * uy, pzz = szz - d3 - rho * uz * uz;
     const C pxy = sxy - rho * ux * uy, pxz = sxz - rho * ux * uz, pyz = syz - rho * uy * uz;
@@ -282,14 +294,19 @@ __device__ __forceinline__ void collide_fluid(C* h, C gamma, const Args& a, C& r
     const C t0 = C(a.tau0);
     tau = C(0.5) * (t0 + sqrt(t0 * t0 + C(a.smag) * pn * ir));
   }
-  const C k = C(1) - C(1) / tau;
+  const C k = C(1) - rcp(tau);
   const C vx = gamma * ux + C(a.fx) * ir, vy = gamma * uy + C(a.fy) * ir, vz = gamma * uz + C(a.fz) * ir;
   const C vsq = vx * vx + vy * vy + vz * vz;
-  sfor<0, Q>([&](auto I) {
+  const C base = (C(1) - k) * drho - C(1.5) * rho * (vsq - k * usq);
+  const C r45 = C(4.5) * rho, r3 = C(3) * rho;
+  h[0] = k * h[0] + wgt<Q, C>(0) * base;
+  sfor<1, H + 1>([&](auto I) {
     constexpr int i = decltype(I)::value;
-    const C eu = heq<Q, C, i>(drho, rho, ux, uy, uz, usq);
-    const C ev = heq<Q, C, i>(drho, rho, vx, vy, vz, vsq);
-    h[i] = ev + k * (h[i] - eu);
+    const C cu = cdot_i<Q, i>(ux, uy, uz), cv = cdot_i<Q, i>(vx, vy, vz);
+    const C sym = base + r45 * (cv * cv - k * (cu * cu));
+    const C anti = r3 * (cv - k * cu);
+    h[i] = k * h[i] + wgt<Q, C>(i) * (sym + anti);
+    h[i + H] = k * h[i + H] + wgt<Q, C>(i) * (sym - anti);
   });
   rho_o = rho;
   const C hf = C(0.5) * ir;
