@@ -266,7 +266,7 @@ def main():
                     help="grid size (the headline channel is 256 256 256; other sizes are for profiling)")
     ap.add_argument("--workload", default="channel", choices=["channel", "canopy"],
                     help="channel (headline) or the urban canopy (for profiling the boundary-list kernel)")
-    ap.add_argument("--kernel", default="auto", choices=["auto", "plain"], help="interior kernel variant")
+    ap.add_argument("--kernel", default="plain", choices=["plain", "staged"], help="interior kernel variant")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -296,8 +296,8 @@ def main():
     stream = torch.cuda.current_stream()
     lat = lbm.Lattice.from_workload(w, storage=lbm.F32)
     lat.set_stream(stream)
-    if args.kernel == "plain":
-        lat.set_option(lbm.OPT_KERNEL, lbm.KERNEL_PLAIN)
+    if args.kernel == "staged":
+        lat.set_option(lbm.OPT_KERNEL, lbm.KERNEL_STAGED)
     info = lat.info()
     lat.step(args.warmup)
     lat.sync()
@@ -348,7 +348,7 @@ def main():
         "config": {"workload": wname, "kernel": args.kernel, "cells": w.N, "parallelism": f"replicas x{world}",
                    "l2": "state of 2.6 GB > 129 MB L2 between steps, no flush needed",
                    "non_solid_cells": info["N"] - info["n_solid"], "boundary_list_cells": info["n_list"]},
-        "roofline": {"bound": "hbm", "kernel": ("k_bulk_tma" if (args.kernel == "auto" and w.nx % 32 == 0 and w.nx <= 512) else "k_bulk") + " (interior cells)", "achieved": achieved, "peak": peak,
+        "roofline": {"bound": "hbm", "kernel": ("k_bulk_tma" if (args.kernel == "staged" and w.nx % 128 == 0) else "k_bulk") + " (interior cells)", "achieved": achieved, "peak": peak,
                      "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "bytes_per_launch": bytes_bulk, "launch_ms": bulk_ms,
                      "share_of_step": ms[0] / ms[2]},

@@ -152,13 +152,13 @@ int lbm_load(lbm_ctx* ctx, const void* buf, size_t len);
 /* Stream for all work of the context (e.g. torch.cuda.current_stream().cuda_stream); 0 = default. */
 int lbm_set_stream(lbm_ctx* ctx, void* cuda_stream);
 
-/* Options. LBM_OPT_KERNEL: 0 (default) runs interior cells with the shared-memory staged kernel
- * (bulk asynchronous copies of 128-cell x-segments) when nx is a multiple of 128 and the storage
- * is not LBM_F64, else
- * the plain kernel; 1 always runs the plain kernel. LBM_OPT_DEBUG_STALL: 1 makes the staged kernel
- * also wait on a barrier that nothing completes, so that its bounded wait (one second) runs out:
- * the step then ends early, the status word records it and the next synchronising call returns
- * LBM_ETIMEOUT (the state must be re-initialised); used to test that path without a GPU fault. */
+/* Options. LBM_OPT_KERNEL: 0 (default) runs interior cells with the plain kernel (one thread per
+ * cell, direct coalesced loads and stores); 2 runs them with the shared-memory staged kernel (bulk
+ * asynchronous copies of 128-cell x-segments) when nx is a multiple of 128 and the storage is not
+ * LBM_F64, else the plain one. LBM_OPT_DEBUG_STALL: 1 makes the staged kernel also wait on a
+ * barrier that nothing completes, so that its bounded wait (one second) runs out: the step then
+ * ends early, the status word records it and the next synchronising call returns LBM_ETIMEOUT
+ * (the state must be re-initialised); used to test that path without a GPU fault. */
 enum { LBM_OPT_KERNEL = 1, LBM_OPT_DEBUG_STALL = 2 };
 int lbm_set_option(lbm_ctx* ctx, int option, int value);
 

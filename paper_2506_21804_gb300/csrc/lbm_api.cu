@@ -165,6 +165,7 @@ Args make_args(const lbm_ctx* c) {
   a.kappa = c->kappa;
   a.E = c->E;
   a.kernel = c->kernel;
+  a.idx32 = ((unsigned long long)c->q * (unsigned long long)c->stride < (1ull << 32) && c->N < (1ll << 31)) ? 1 : 0;
   a.debug_stall = c->debug_stall;
   return a;
 }
@@ -694,7 +695,7 @@ int lbm_set_option(lbm_ctx* c, int option, int value) {
   if (!c) return fail(LBM_EINVAL, "null context");
   switch (option) {
     case LBM_OPT_KERNEL:
-      if (value != 0 && value != 1) return fail(LBM_EINVAL, "LBM_OPT_KERNEL takes 0 (auto) or 1 (plain)");
+      if (value != 0 && value != 2) return fail(LBM_EINVAL, "LBM_OPT_KERNEL takes 0 (plain) or 2 (staged)");
       c->kernel = value;
       return LBM_OK;
     case LBM_OPT_DEBUG_STALL:

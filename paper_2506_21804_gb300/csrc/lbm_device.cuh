@@ -149,7 +149,8 @@ struct Args {
   double rho_out;
   double drho_out;         // rho_out - 1, formed in double precision
   int wm;                  // wall model on
-  int kernel;              // interior kernel: 0 staged (bulk copies into shared memory) where the shape allows, 1 plain
+  int kernel;              // interior kernel: 0 plain, 2 staged (bulk copies into shared memory) where the shape allows
+  int idx32;               // 1: every population index q*stride fits in 32 bits (32-bit index arithmetic)
   int debug_stall;         // 1: the staged kernel also waits on a barrier nobody completes (tests the bounded wait)
   double kappa, E;
 };

@@ -25,6 +25,35 @@ template <class C> __device__ __forceinline__ C gamma_at(const Args& a, long lon
   return a.gamma ? static_cast<const C*>(a.gamma)[n] : C(1);
 }
 
+// Neighbour index offsets of an interior cell in 32-bit arithmetic (periodic wrap folded into the
+// six per-axis deltas); valid when every population index fits in 32 bits (Args::idx32).
+struct Nbr32 {
+  unsigned n;
+  int dxm, dxp, dym, dyp, dzm, dzp;
+  __device__ __forceinline__ Nbr32(const Args& a, int x, int y, int z, long long n_) {
+    n = unsigned(n_);
+    const int nx = a.nx, nxy = int(a.nxy);
+    dxm = x == 0 ? nx - 1 : -1;
+    dxp = x == nx - 1 ? 1 - nx : 1;
+    dym = y == 0 ? (a.ny - 1) * nx : -nx;
+    dyp = y == a.ny - 1 ? (1 - a.ny) * nx : nx;
+    dzm = z == 0 ? (a.nz - 1) * nxy : -nxy;
+    dzp = z == a.nz - 1 ? (1 - a.nz) * nxy : nxy;
+  }
+  // index of population p at the cell displaced by (dx, dy, dz)
+  template <int DX, int DY, int DZ>
+  __device__ __forceinline__ unsigned at(unsigned pbase) const {
+    unsigned r = pbase + n;
+    if constexpr (DX < 0) r += unsigned(dxm);
+    if constexpr (DX > 0) r += unsigned(dxp);
+    if constexpr (DY < 0) r += unsigned(dym);
+    if constexpr (DY > 0) r += unsigned(dyp);
+    if constexpr (DZ < 0) r += unsigned(dzm);
+    if constexpr (DZ > 0) r += unsigned(dzp);
+    return r;
+  }
+};
+
 // Gather the Q deviations of cell n. LOAD_LOCAL: h_i from slot (i, n) of src (natural layout);
 // LOAD_SLOTS: h_i from the AA slot of direction i (state after an even step).
 template <int Q, class S, int LOAD>
@@ -32,12 +61,27 @@ __device__ __forceinline__ void gather(const Args& a, const S* src, int x, int y
                                        typename Codec<S>::C* h) {
   using C = typename Codec<S>::C;
   if constexpr (LOAD == LOAD_LOCAL) {
-    sfor<0, Q>([&](auto I) {
-      constexpr int i = decltype(I)::value;
-      h[i] = Codec<S>::ld(src + (long long)i * a.stride + n);
-    });
+    if (a.idx32) {
+      const unsigned us = unsigned(a.stride), un = unsigned(n);
+      sfor<0, Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        h[i] = Codec<S>::ld(src + (unsigned(i) * us + un));
+      });
+    } else {
+      sfor<0, Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        h[i] = Codec<S>::ld(src + (long long)i * a.stride + n);
+      });
+    }
   } else {
-    if (!near) {
+    if (!near && a.idx32) {
+      const Nbr32 nb(a, x, y, z, n);
+      const unsigned us = unsigned(a.stride);
+      sfor<0, Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        h[i] = Codec<S>::ld(src + nb.at<-Lat<Q>::cx(i), -Lat<Q>::cy(i), -Lat<Q>::cz(i)>(unsigned(opp<Q>(i)) * us));
+      });
+    } else if (!near) {
       const int xm = x == 0 ? a.nx - 1 : x - 1, xp = x == a.nx - 1 ? 0 : x + 1;
       const long long y0 = (long long)y * a.nx;
       const long long ym = (long long)(y == 0 ? a.ny - 1 : y - 1) * a.nx, yp = (long long)(y == a.ny - 1 ? 0 : y + 1) * a.nx;
@@ -68,12 +112,27 @@ template <int Q, class S, int STORE>
 __device__ __forceinline__ void scatter(const Args& a, S* dst, int x, int y, int z, long long n, bool near,
                                         const typename Codec<S>::C* h) {
   if constexpr (STORE == STORE_MIRROR) {
-    sfor<0, Q>([&](auto I) {
-      constexpr int i = decltype(I)::value;
-      Codec<S>::st(dst + (long long)opp<Q>(i) * a.stride + n, h[i]);
-    });
+    if (a.idx32) {
+      const unsigned us = unsigned(a.stride), un = unsigned(n);
+      sfor<0, Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        Codec<S>::st(dst + (unsigned(opp<Q>(i)) * us + un), h[i]);
+      });
+    } else {
+      sfor<0, Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        Codec<S>::st(dst + (long long)opp<Q>(i) * a.stride + n, h[i]);
+      });
+    }
   } else {
-    if (!near) {
+    if (!near && a.idx32) {
+      const Nbr32 nb(a, x, y, z, n);
+      const unsigned us = unsigned(a.stride);
+      sfor<0, Q>([&](auto I) {
+        constexpr int k = decltype(I)::value;  // outgoing direction: f*_k goes to slot (k, x + c_k)
+        Codec<S>::st(dst + nb.at<Lat<Q>::cx(k), Lat<Q>::cy(k), Lat<Q>::cz(k)>(unsigned(k) * us), h[k]);
+      });
+    } else if (!near) {
       const int xm = x == 0 ? a.nx - 1 : x - 1, xp = x == a.nx - 1 ? 0 : x + 1;
       const long long y0 = (long long)y * a.nx;
       const long long ym = (long long)(y == 0 ? a.ny - 1 : y - 1) * a.nx, yp = (long long)(y == a.ny - 1 ? 0 : y + 1) * a.nx;

@@ -21,7 +21,7 @@ FACE_PERIODIC, FACE_WALL, FACE_SLIP, FACE_OPEN = 0, 1, 2, 3
 KIND_FLUID, KIND_SOLID, KIND_WALL, KIND_INFLOW, KIND_OUTFLOW = 0, 1, 2, 3, 4
 T_KIND, T_REF, T_NEAR, T_LIST = 7, 8, 16, 32
 OPT_KERNEL, OPT_DEBUG_STALL = 1, 2
-KERNEL_AUTO, KERNEL_PLAIN = 0, 1
+KERNEL_PLAIN, KERNEL_STAGED = 0, 2
 STORAGE_NAMES = {"f64": F64, "f32": F32, "f16": F16, "bf16": BF16}
 
 _ERR_NAMES = {EINVAL: "LBM_EINVAL", ENOMEM: "LBM_ENOMEM", ECUDA: "LBM_ECUDA", ENAN: "LBM_ENAN",

@@ -448,8 +448,8 @@ def test_staged_kernel_matches_plain_kernel(q, storage):
              with_features(I.random_box(128, 9, 7, seed=6, q=q, solid_frac=0.1, tau=0.6, cs=0.1, faces=(0, 0, 2, 2, 1, 2)))]
     for w in cases:
         a = gpu_from(w, storage)
+        a.set_option(lbm.OPT_KERNEL, lbm.KERNEL_STAGED)
         b = gpu_from(w, storage)
-        b.set_option(lbm.OPT_KERNEL, lbm.KERNEL_PLAIN)
         for steps in (1, 2, 9):
             a.step(steps)
             b.step(steps)
@@ -466,6 +466,7 @@ def test_staged_kernel_bounded_wait_reports_timeout_and_recovers():
     after the one-second limit, the status reads LBM_ETIMEOUT, and the context stays usable."""
     w = I.channel(nx=128, ny=18, nz=8, seed=5, dtype=np.float32)
     g = gpu_from(w, lbm.F32)
+    g.set_option(lbm.OPT_KERNEL, lbm.KERNEL_STAGED)
     g.set_option(lbm.OPT_DEBUG_STALL, 1)
     g.step(1)
     with pytest.raises(lbm.LBMError) as e:
