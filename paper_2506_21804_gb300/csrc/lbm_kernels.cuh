@@ -61,18 +61,10 @@ __device__ __forceinline__ void gather(const Args& a, const S* src, int x, int y
                                        typename Codec<S>::C* h) {
   using C = typename Codec<S>::C;
   if constexpr (LOAD == LOAD_LOCAL) {
-    if (a.idx32) {
-      const unsigned us = unsigned(a.stride), un = unsigned(n);
-      sfor<0, Q>([&](auto I) {
-        constexpr int i = decltype(I)::value;
-        h[i] = Codec<S>::ld(src + (unsigned(i) * us + un));
-      });
-    } else {
-      sfor<0, Q>([&](auto I) {
-        constexpr int i = decltype(I)::value;
-        h[i] = Codec<S>::ld(src + (long long)i * a.stride + n);
-      });
-    }
+    sfor<0, Q>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      h[i] = Codec<S>::ld(src + (long long)i * a.stride + n);
+    });
   } else {
     if (!near && a.idx32) {
       const Nbr32 nb(a, x, y, z, n);
@@ -112,18 +104,10 @@ template <int Q, class S, int STORE>
 __device__ __forceinline__ void scatter(const Args& a, S* dst, int x, int y, int z, long long n, bool near,
                                         const typename Codec<S>::C* h) {
   if constexpr (STORE == STORE_MIRROR) {
-    if (a.idx32) {
-      const unsigned us = unsigned(a.stride), un = unsigned(n);
-      sfor<0, Q>([&](auto I) {
-        constexpr int i = decltype(I)::value;
-        Codec<S>::st(dst + (unsigned(opp<Q>(i)) * us + un), h[i]);
-      });
-    } else {
-      sfor<0, Q>([&](auto I) {
-        constexpr int i = decltype(I)::value;
-        Codec<S>::st(dst + (long long)opp<Q>(i) * a.stride + n, h[i]);
-      });
-    }
+    sfor<0, Q>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      Codec<S>::st(dst + (long long)opp<Q>(i) * a.stride + n, h[i]);
+    });
   } else {
     if (!near && a.idx32) {
       const Nbr32 nb(a, x, y, z, n);
