@@ -106,9 +106,9 @@ int lbm_init_equilibrium_ex(lbm_ctx* ctx, const void* rho, const void* u, int dt
 
 /* Advance n time steps (stream-ordered, asynchronous). Returns the sticky status seen so far. */
 int lbm_step(lbm_ctx* ctx, int n);
-/* Same (n >= 1), timed with CUDA events on the context stream around each launch: adds the device
- * time of the interior-cell kernels to ms[0], of the boundary-list kernels to ms[1], and the time
- * from the first launch's start to the last launch's end to ms[2]. Synchronises. */
+/* Same (n >= 1), timed with CUDA events on the context stream: adds the device time of the
+ * interior-cell kernels to ms[0], of the rest of each step (wall-model pass, boundary-list kernel)
+ * to ms[1], and the time from the first step's start to the last step's end to ms[2]. Synchronises. */
 int lbm_step_timed(lbm_ctx* ctx, int n, double ms[3]);
 /* Wait for the context stream; returns LBM_ENAN if a step has seen a non-finite density. */
 int lbm_sync(lbm_ctx* ctx);

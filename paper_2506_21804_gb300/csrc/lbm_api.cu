@@ -84,6 +84,8 @@ struct lbm_ctx {
   unsigned status_seen = 0;
   // device buffers
   DevBuf f, type, mask, wdist, gamma, uin, lcell, nsum, wref, lxyz, lcode, wnrm, wyw, ref0, ref1, status, red, redout, stage;
+  DevBuf lidx, lsub, lwall, wst;
+  int n_sub = 0, n_wall = 0;
   bool has_gamma = false, has_wdist = false;
   int n_list = 0;
   long long counts[8] = {0};  // wall, ref, inflow, outflow, solid
@@ -100,7 +102,7 @@ struct lbm_ctx {
   double adj_ms[2] = {0, 0};
 
   ~lbm_ctx() {
-    DevBuf* all[] = {&f, &type, &mask, &wdist, &gamma, &uin, &lcell, &nsum, &wref, &lxyz, &lcode, &wnrm, &wyw, &ref0, &ref1, &status, &red,
+    DevBuf* all[] = {&lidx, &lsub, &lwall, &wst, &f, &type, &mask, &wdist, &gamma, &uin, &lcell, &nsum, &wref, &lxyz, &lcode, &wnrm, &wyw, &ref0, &ref1, &status, &red,
                      &redout, &stage, &lamA, &lamB, &dgam, &duin};
     for (DevBuf* b : all) b->release();
     for (auto& b : ckpts) b.release();
@@ -165,6 +167,13 @@ Args make_args(const lbm_ctx* c) {
   a.kappa = c->kappa;
   a.E = c->E;
   a.kernel = c->kernel;
+  a.fuse = c->kernel == 0 ? 1 : 0;
+  a.lidx = static_cast<const int*>(c->lidx.p);
+  a.lsub = a.fuse ? static_cast<const int*>(c->lsub.p) : nullptr;
+  a.n_sub = c->n_sub;
+  a.lwall = static_cast<const int*>(c->lwall.p);
+  a.n_wall = c->n_wall;
+  a.wst = c->wst.p;
   a.idx32 = ((unsigned long long)c->q * (unsigned long long)c->stride < (1ull << 32) && c->N < (1ll << 31)) ? 1 : 0;
   a.debug_stall = c->debug_stall;
   return a;
@@ -289,6 +298,32 @@ int build_geometry(lbm_ctx* c) {
   c->ops->list_aux(a, static_cast<const int*>(c->nsum.p), c->has_wdist ? static_cast<const float*>(c->wdist.p) : nullptr,
                    c->wnrm.p, c->wyw.p, s);
   CK(cudaGetLastError());
+  // list position of every cell, and the sub-lists of INFLOW/OUTFLOW and WALL entries
+  CK(c->lidx.ensure((size_t)c->N * sizeof(int)));
+  CK(cudaMemsetAsync(c->lidx.p, 0xFF, (size_t)c->N * sizeof(int), s));
+  geo_list_index(static_cast<const long long*>(c->lcell.p), c->n_list, static_cast<int*>(c->lidx.p), s);
+  CK(c->wst.ensure(nl * WALL_STATE * c->ops->celem));
+  CK(cudaMemsetAsync(c->wst.p, 0, nl * WALL_STATE * c->ops->celem, s));
+  {
+    std::vector<long long> cells(c->n_list);
+    std::vector<uint8_t> tl(c->N);
+    if (c->n_list) CK(cudaMemcpyAsync(cells.data(), c->lcell.p, c->n_list * sizeof(long long), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(tl.data(), c->type.p, c->N, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    std::vector<int> sub, wall;
+    for (int k = 0; k < c->n_list; ++k) {
+      const int kind = tl[cells[k]] & T_KIND;
+      if (kind == K_INFLOW || kind == K_OUTFLOW) sub.push_back(k);
+      if (kind == K_WALL) wall.push_back(k);
+    }
+    c->n_sub = int(sub.size());
+    c->n_wall = int(wall.size());
+    CK(c->lsub.ensure(std::max<size_t>(1, sub.size()) * sizeof(int)));
+    CK(c->lwall.ensure(std::max<size_t>(1, wall.size()) * sizeof(int)));
+    if (!sub.empty()) CK(cudaMemcpyAsync(c->lsub.p, sub.data(), sub.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    if (!wall.empty()) CK(cudaMemcpyAsync(c->lwall.p, wall.data(), wall.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+  }
   // host copy of the type bytes and counters
   c->type_host.resize(c->N);
   CK(cudaMemcpyAsync(c->type_host.data(), c->type.p, c->N, cudaMemcpyDeviceToHost, s));
@@ -303,6 +338,19 @@ int build_geometry(lbm_ctx* c) {
   }
   c->counts[0] = nw; c->counts[1] = nr; c->counts[2] = ni; c->counts[3] = no; c->counts[4] = ns;
   return LBM_OK;
+}
+
+// One time step: in fused mode the wall-model states of the WALL entries first, then the interior
+// kernel, then the boundary-list kernel. Events (optional) bracket the interior kernel.
+void launch_step(lbm_ctx* c, cudaEvent_t before_bulk = nullptr, cudaEvent_t after_bulk = nullptr) {
+  const Args a = make_args(c);
+  const int odd = int(c->t & 1);
+  if (a.fuse && a.wm) c->ops->wall_pass(a, c->stream);
+  if (before_bulk) cudaEventRecord(before_bulk, c->stream);
+  c->ops->step_bulk(a, odd, c->stream);
+  if (after_bulk) cudaEventRecord(after_bulk, c->stream);
+  c->ops->step_list(a, odd, c->stream);
+  ++c->t;
 }
 
 // State to rest (f = w), step counter 0, reference buffers from that state.
@@ -564,13 +612,7 @@ int lbm_init_equilibrium(lbm_ctx* c, const float* rho, const float* u) {
 int lbm_step(lbm_ctx* c, int n) {
   if (!c) return fail(LBM_EINVAL, "null context");
   if (n < 0) return fail(LBM_EINVAL, "n must be >= 0");
-  for (int s = 0; s < n; ++s) {
-    const Args a = make_args(c);
-    const int odd = int(c->t & 1);
-    c->ops->step_bulk(a, odd, c->stream);
-    c->ops->step_list(a, odd, c->stream);
-    ++c->t;
-  }
+  for (int s = 0; s < n; ++s) launch_step(c);
   CK(cudaGetLastError());
   return status_code(c);
 }
@@ -578,29 +620,24 @@ int lbm_step(lbm_ctx* c, int n) {
 int lbm_step_timed(lbm_ctx* c, int n, double ms[3]) {
   if (!c || !ms) return fail(LBM_EINVAL, "null argument");
   if (n < 1) return fail(LBM_EINVAL, "n must be >= 1");
-  std::vector<cudaEvent_t> ev(3 * (size_t)n);
+  std::vector<cudaEvent_t> ev(4 * (size_t)n);
   for (auto& e : ev) CK(cudaEventCreate(&e));
   for (int s = 0; s < n; ++s) {
-    const Args a = make_args(c);
-    const int odd = int(c->t & 1);
-    CK(cudaEventRecord(ev[3 * s], c->stream));
-    c->ops->step_bulk(a, odd, c->stream);
-    CK(cudaEventRecord(ev[3 * s + 1], c->stream));
-    c->ops->step_list(a, odd, c->stream);
-    CK(cudaEventRecord(ev[3 * s + 2], c->stream));
-    ++c->t;
+    CK(cudaEventRecord(ev[4 * s], c->stream));
+    launch_step(c, ev[4 * s + 1], ev[4 * s + 2]);
+    CK(cudaEventRecord(ev[4 * s + 3], c->stream));
   }
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(c->stream));
   for (int s = 0; s < n; ++s) {
-    float t0 = 0, t1 = 0;
-    CK(cudaEventElapsedTime(&t0, ev[3 * s], ev[3 * s + 1]));
-    CK(cudaEventElapsedTime(&t1, ev[3 * s + 1], ev[3 * s + 2]));
-    ms[0] += t0;
-    ms[1] += t1;
+    float all = 0, bulk = 0;
+    CK(cudaEventElapsedTime(&all, ev[4 * s], ev[4 * s + 3]));
+    CK(cudaEventElapsedTime(&bulk, ev[4 * s + 1], ev[4 * s + 2]));
+    ms[0] += bulk;
+    ms[1] += all - bulk;
   }
   float tot = 0;
-  CK(cudaEventElapsedTime(&tot, ev[0], ev[3 * (size_t)n - 1]));
+  CK(cudaEventElapsedTime(&tot, ev[0], ev[4 * (size_t)n - 1]));
   ms[2] += tot;
   for (auto& e : ev) cudaEventDestroy(e);
   int rc = read_status(c);
@@ -835,11 +872,7 @@ int lbm_objective_forward(lbm_ctx* c, int T, int W, int xa, int xb, int ckpt, do
   CK(cudaMemsetAsync(c->redout.p, 0, sizeof(double), c->stream));
   for (int s = 0; s < T; ++s) {
     if (s % ckpt == 0) CK(cudaMemcpyAsync(c->ckpts[s / ckpt].p, c->f.p, sb, cudaMemcpyDeviceToDevice, c->stream));
-    const Args a = make_args(c);
-    const int odd = int(c->t & 1);
-    c->ops->step_bulk(a, odd, c->stream);
-    c->ops->step_list(a, odd, c->stream);
-    ++c->t;
+    launch_step(c);
     if (s + 1 > T - W) {
       const Args b = make_args(c);
       c->ops->plane_rho(b, c->f.p, int(c->t & 1), xa, xb, static_cast<double*>(c->redout.p), wa, wb, c->stream);

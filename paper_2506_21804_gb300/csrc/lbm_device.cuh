@@ -149,6 +149,14 @@ struct Args {
   double rho_out;
   double drho_out;         // rho_out - 1, formed in double precision
   int wm;                  // wall model on
+  int fuse;                // 1: WALL and reference cells are updated by the interior kernel; the
+                           //    boundary-list kernel then runs over INFLOW/OUTFLOW entries only
+  const int* lidx;         // list position of every cell (-1 off the list)
+  const int* lsub;         // list positions handled by the boundary-list kernel (fused mode)
+  int n_sub;
+  const int* lwall;        // list positions of WALL entries (wall-state pass)
+  int n_wall;
+  void* wst;               // wall-model state per list entry (WALL_STATE values)
   int kernel;              // interior kernel: 0 plain, 2 staged (bulk copies into shared memory) where the shape allows
   int idx32;               // 1: every population index q*stride fits in 32 bits (32-bit index arithmetic)
   int debug_stall;         // 1: the staged kernel also waits on a barrier nobody completes (tests the bounded wait)
@@ -428,21 +436,14 @@ template <class C> __device__ C sp_solve_y(C yp, C k, C E) {
   return u;
 }
 
-// Wall-model update of a WALL cell (sigma = 0, Sec. 2.2.1): from the reference velocity ur at
-// distance yw + 1 along the unit normal n, the solid velocity u^B and modelled shear du/dn; then
-// f* = f^eq(rho, u^B + F/rho) + (1 - 1/tau) f^(1,FD), f^(1,FD)_i = -(w_i rho tau / cs^2) Q_i : S,
-// S = (du/dn)/2 (t n^T + n t^T), tau = tau0 + 3 C_S^2 |du/dn|.
-template <int Q, class C>
-__device__ __forceinline__ void collide_wall(C* h, const Args& a, const C* nrm, C yw, const C* ur, bool has_ref, C& rho_o,
-                                             C& urx, C& ury, C& urz) {
-  C drho, jx, jy, jz;
-  sums<Q, C>(h, drho, jx, jy, jz);
-  const C rho = C(1) + drho, ir = C(1) / rho;
-  rho_o = rho;
-  const C hf = C(0.5) * ir;
-  urx = jx * ir + C(a.fx) * hf;
-  ury = jy * ir + C(a.fy) * hf;
-  urz = jz * ir + C(a.fz) * hf;
+// Wall-model state of a WALL cell (Sec. 2.2.1): from the reference velocity ur at distance yw + 1
+// along the unit normal n, the solid velocity u^B, the modelled strain S = (du/dn)/2 (t n^T + n t^T)
+// with du/dn = (u_tau^2/nu) / (dy+/du+)(u+_w), and tau = tau0 + 3 C_S^2 |du/dn|.
+// Layout of the 10 values: u^B (3), tau, S_xx, S_yy, S_zz, S_xy, S_xz, S_yz.
+constexpr int WALL_STATE = 10;
+
+template <class C>
+__device__ __forceinline__ void wall_state(const Args& a, const C* nrm, C yw, const C* ur, bool has_ref, C* ws) {
   C ubx = 0, uby = 0, ubz = 0, dudn = 0, tx = 0, ty = 0, tz = 0;
   const C nx = nrm[0], ny = nrm[1], nz = nrm[2];
   if (has_ref && (nx != C(0) || ny != C(0) || nz != C(0))) {
@@ -461,17 +462,43 @@ __device__ __forceinline__ void collide_wall(C* h, const Args& a, const C* nrm, 
       dudn = (utau * utau / nu) / sp_dy<C>(upw, k, E);
     }
   }
-  const C tau = C(a.tau0) + C(3) * C(a.cs2smag) * fabs(dudn);
   const C hd = C(0.5) * dudn;
-  const C sxx = hd * C(2) * tx * nx, syy = hd * C(2) * ty * ny, szz = hd * C(2) * tz * nz;
-  const C sxy = hd * (tx * ny + nx * ty), sxz = hd * (tx * nz + nx * tz), syz = hd * (ty * nz + ny * tz);
-  const C vx = ubx + C(a.fx) * ir, vy = uby + C(a.fy) * ir, vz = ubz + C(a.fz) * ir;
+  ws[0] = ubx; ws[1] = uby; ws[2] = ubz;
+  ws[3] = C(a.tau0) + C(3) * C(a.cs2smag) * fabs(dudn);
+  ws[4] = hd * C(2) * tx * nx; ws[5] = hd * C(2) * ty * ny; ws[6] = hd * C(2) * tz * nz;
+  ws[7] = hd * (tx * ny + nx * ty); ws[8] = hd * (tx * nz + nx * tz); ws[9] = hd * (ty * nz + ny * tz);
+}
+
+// sigma = 0 reconstruction of a WALL cell from its wall-model state:
+// f* = f^eq(rho, u^B + F/rho) + (1 - 1/tau) f^(1,FD), f^(1,FD)_i = -(w_i rho tau / cs^2) Q_i : S.
+template <int Q, class C>
+__device__ __forceinline__ void collide_wall_state(C* h, const Args& a, const C* ws, C& rho_o, C& urx, C& ury, C& urz) {
+  C drho, jx, jy, jz;
+  sums<Q, C>(h, drho, jx, jy, jz);
+  const C rho = C(1) + drho, ir = rcp(rho);
+  rho_o = rho;
+  const C hf = C(0.5) * ir;
+  urx = jx * ir + C(a.fx) * hf;
+  ury = jy * ir + C(a.fy) * hf;
+  urz = jz * ir + C(a.fz) * hf;
+  const C tau = ws[3];
+  const C sxx = ws[4], syy = ws[5], szz = ws[6], sxy = ws[7], sxz = ws[8], syz = ws[9];
+  const C vx = ws[0] + C(a.fx) * ir, vy = ws[1] + C(a.fy) * ir, vz = ws[2] + C(a.fz) * ir;
   const C vsq = vx * vx + vy * vy + vz * vz;
   const C g = -C(3) * rho * (tau - C(1));  // (1 - 1/tau) * (-rho tau / cs^2)
   sfor<0, Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
     h[i] = heq<Q, C, i>(drho, rho, vx, vy, vz, vsq) + g * wgt<Q, C>(i) * qcontract<Q, C, i>(sxx, syy, szz, sxy, sxz, syz);
   });
+}
+
+// Both in one (boundary-list path).
+template <int Q, class C>
+__device__ __forceinline__ void collide_wall(C* h, const Args& a, const C* nrm, C yw, const C* ur, bool has_ref, C& rho_o,
+                                             C& urx, C& ury, C& urz) {
+  C ws[WALL_STATE];
+  wall_state<C>(a, nrm, yw, ur, has_ref, ws);
+  collide_wall_state<Q, C>(h, a, ws, rho_o, urx, ury, urz);
 }
 
 template <class C> __device__ __forceinline__ bool finite_all(C a, C b, C c, C d) {

@@ -221,6 +221,11 @@ __global__ void k_source_map(const Args a, int64_t* sdir, int64_t* scell) {
   });
 }
 
+__global__ void k_list_index(const long long* lcell, int n_list, int* lidx) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n_list) lidx[lcell[k]] = k;
+}
+
 __global__ void k_reduce_final(const double* partial, int nblk, double* out) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double s[4] = {0, 0, 0, 0};
@@ -268,6 +273,11 @@ void geo_source_map(const GeoArgs& g, const uint8_t* type, int64_t* sdir, int64_
   for (int f = 0; f < 6; ++f) a.face[f] = g.face[f];
   if (g.q == 19) k_source_map<19><<<nblocks(g.N, 128), 128, 0, s>>>(a, sdir, scell);
   else k_source_map<27><<<nblocks(g.N, 128), 128, 0, s>>>(a, sdir, scell);
+}
+
+void geo_list_index(const long long* lcell, int n_list, int* lidx, cudaStream_t s) {
+  if (n_list <= 0) return;
+  k_list_index<<<nblocks(n_list, 256), 256, 0, s>>>(lcell, n_list, lidx);
 }
 
 void reduce_final(const double* partial, int nblk, double* out, cudaStream_t s) {

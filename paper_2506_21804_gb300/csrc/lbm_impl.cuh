@@ -78,9 +78,14 @@ struct Impl {
     else k_bulk<Q, S, false><<<bulk_grid(a), bulk_block(a), 0, s>>>(a);
   }
   static void step_list(const Args& a, int odd, cudaStream_t s) {
-    if (a.n_list <= 0) return;
-    if (odd) k_list<Q, S, true><<<blocks_for(a.n_list, LIST_THREADS), LIST_THREADS, 0, s>>>(a);
-    else k_list<Q, S, false><<<blocks_for(a.n_list, LIST_THREADS), LIST_THREADS, 0, s>>>(a);
+    const int nj = a.lsub ? a.n_sub : a.n_list;
+    if (nj <= 0) return;
+    if (odd) k_list<Q, S, true><<<blocks_for(nj, LIST_THREADS), LIST_THREADS, 0, s>>>(a);
+    else k_list<Q, S, false><<<blocks_for(nj, LIST_THREADS), LIST_THREADS, 0, s>>>(a);
+  }
+  static void wall_pass(const Args& a, cudaStream_t s) {
+    if (a.n_wall <= 0) return;
+    k_wall_state<C><<<blocks_for(a.n_wall, 128), 128, 0, s>>>(a);
   }
   static void init_eq(const Args& a, const void* rho, const void* u, int dtype, cudaStream_t s) {
     k_init_eq<Q, S><<<blocks_for(a.N, 256), 256, 0, s>>>(a, rho, u, dtype);
@@ -126,7 +131,7 @@ struct Impl {
     else k_convert<float, float><<<g, 256, 0, s>>>((const float*)in, (float*)out, n);
   }
   static const Ops* table() {
-    static const Ops ops = {Q,        int(sizeof(S)), int(sizeof(C)), step_bulk, step_list, init_eq,   moments,
+    static const Ops ops = {Q,        int(sizeof(S)), int(sizeof(C)), step_bulk, step_list, wall_pass, init_eq,   moments,
                             get_pops, set_pops,       ref_fill,       reduce,    list_aux,  step_oop,  reverse,
                             plane_rho, seed,           convert};
     return &ops;

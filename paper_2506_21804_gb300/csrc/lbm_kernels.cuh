@@ -231,9 +231,44 @@ __device__ __forceinline__ void collide_any(const Args& a, int kind, uint8_t t, 
 }
 
 // ---- the step kernels ----------------------------------------------------------------------------------
-// Interior kernel: every FLUID cell that is not on the boundary list. Threads map to (x, y, z).
+// WALL or reference cell handled inside the interior kernel (fused mode): its list entry gives the
+// slot codes, the precomputed wall-model state and the reference-buffer position.
 template <int Q, class S, bool ODD>
-__global__ void __launch_bounds__(BULK_THREADS) k_bulk(const Args a) {
+__device__ __forceinline__ void list_cell_inline(const Args& a, S* f, int x, int y, int z, long long n, uint8_t t) {
+  using C = typename Codec<S>::C;
+  const int k = a.lidx[n];
+  const int kind = t & T_KIND;
+  C h[Q];
+  unsigned long long code = 0;
+  if constexpr (ODD) {
+    code = a.lcode[k];
+    gather_coded<Q, S>(a, f, x, y, z, n, code, h);
+  } else {
+    gather<Q, S, LOAD_LOCAL>(a, f, x, y, z, n, false, h);
+  }
+  C rho, urx, ury, urz;
+  if (kind == K_WALL && a.wm) collide_wall_state<Q, C>(h, a, cptr<C>(a.wst) + (long long)WALL_STATE * k, rho, urx, ury, urz);
+  else collide_fluid<Q, C>(h, gamma_at<C>(a, n), a, rho, urx, ury, urz);
+  if (t & T_REF) {
+    C* w = cptr<C>(a.ref_wr) + 3 * (long long)k;
+    w[0] = urx; w[1] = ury; w[2] = urz;
+  }
+  if (!finite_all<C>(rho, urx, ury, urz)) atomicOr(a.status, ST_NAN);
+  if constexpr (ODD) scatter_coded<Q, S>(a, f, x, y, z, n, code, h);
+  else scatter<Q, S, STORE_MIRROR>(a, f, x, y, z, n, false, h);
+}
+
+// Interior kernel: every FLUID cell off the boundary list, and in fused mode also the WALL and
+// reference cells of the list. Threads map to (x, y, z).
+// Occupancy target of the interior kernel (CTAs of 128 threads per SM): D3Q19 10 on even steps
+// (<= 51 registers) and 8 on odd steps (<= 64), D3Q27 5; the register cap falls on the rarely
+// taken boundary-cell path. The FP64 (reference) form is left unconstrained.
+template <int Q, class S, bool ODD> constexpr int bulk_min_blocks() {
+  return sizeof(S) == 8 ? 1 : (Q == 19 ? (ODD ? 8 : 10) : 5);
+}
+
+template <int Q, class S, bool ODD>
+__global__ void __launch_bounds__(BULK_THREADS, (bulk_min_blocks<Q, S, ODD>())) k_bulk(const Args a) {
   using C = typename Codec<S>::C;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -241,8 +276,13 @@ __global__ void __launch_bounds__(BULK_THREADS) k_bulk(const Args a) {
   if (x >= a.nx || y >= a.ny) return;
   const long long n = x + (long long)y * a.nx + (long long)z * a.nxy;
   const uint8_t t = a.type[n];
-  if (t & (T_LIST | T_KIND)) return;
   S* f = static_cast<S*>(a.f);
+  if (t & (T_LIST | T_KIND)) {
+    const int kind = t & T_KIND;
+    if ((t & T_LIST) && a.fuse && kind != K_INFLOW && kind != K_OUTFLOW)
+      list_cell_inline<Q, S, ODD>(a, f, x, y, z, n, t);
+    return;
+  }
   const bool near = (t & T_NEAR) != 0;
   C h[Q];
   gather<Q, S, ODD ? LOAD_SLOTS : LOAD_LOCAL>(a, f, x, y, z, n, near, h);
@@ -252,12 +292,28 @@ __global__ void __launch_bounds__(BULK_THREADS) k_bulk(const Args a) {
   scatter<Q, S, ODD ? STORE_SLOTS : STORE_MIRROR>(a, f, x, y, z, n, near, h);
 }
 
-// Boundary-list kernel: WALL, INFLOW, OUTFLOW and reference cells, one thread per list entry.
+// Wall-model state of every WALL entry from the previous step's reference velocities (fused mode).
+template <class C>
+__global__ void k_wall_state(const Args a) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= a.n_wall) return;
+  const int k = a.lwall[j];
+  const int r = a.wref[k];
+  const C z3[3] = {C(0), C(0), C(0)};
+  const C* ur = r >= 0 ? cptr<C>(a.ref_rd) + 3 * (long long)r : z3;
+  wall_state<C>(a, cptr<C>(a.wnrm) + 3 * (long long)k, cptr<C>(a.wyw)[k], ur, r >= 0,
+                cptr<C>(a.wst) + (long long)WALL_STATE * k);
+}
+
+// Boundary-list kernel, one thread per list entry: every entry, or in fused mode the INFLOW/OUTFLOW
+// entries named by Args::lsub.
 template <int Q, class S, bool ODD>
 __global__ void __launch_bounds__(LIST_THREADS) k_list(const Args a) {
   using C = typename Codec<S>::C;
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= a.n_list) return;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nj = a.lsub ? a.n_sub : a.n_list;
+  if (j >= nj) return;
+  const int k = a.lsub ? a.lsub[j] : j;
   const long long n = a.lcell[k];
   const int x = a.lxyz[3 * k], y = a.lxyz[3 * k + 1], z = a.lxyz[3 * k + 2];
   const uint8_t t = a.type[n];

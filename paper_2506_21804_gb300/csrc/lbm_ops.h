@@ -16,6 +16,8 @@ struct Ops {
   // one step: interior kernel then boundary-list kernel; parity odd = step counter & 1
   void (*step_bulk)(const Args&, int odd, cudaStream_t);
   void (*step_list)(const Args&, int odd, cudaStream_t);
+  // fused mode: wall-model state of the WALL entries before the interior kernel
+  void (*wall_pass)(const Args&, cudaStream_t);
   // state access; swapped = state stored in the after-even-step form
   void (*init_eq)(const Args&, const void* rho, const void* u, int dtype, cudaStream_t);
   void (*moments)(const Args&, int swapped, void* rho, void* u, int dtype, cudaStream_t);
@@ -55,6 +57,8 @@ void geo_list_count(const GeoArgs&, uint8_t* type, int* counts, cudaStream_t);
 void geo_list_write(const GeoArgs&, const uint8_t* type, const int* offsets, long long* lcell, cudaStream_t);
 void geo_list_meta(const GeoArgs&, const uint8_t* type, const long long* lcell, int n_list, int* nsum, int* wref,
                    int* lxyz, unsigned long long* lcode, cudaStream_t);
+// list position of every cell (-1 off the list)
+void geo_list_index(const long long* lcell, int n_list, int* lidx, cudaStream_t);
 // source map (debug): for each (i, n): source population and cell, -1 for solid cells
 void geo_source_map(const GeoArgs&, const uint8_t* type, int64_t* src_dir, int64_t* src_cell, cudaStream_t);
 // FP64 final reduction of nblk partials (4 doubles each) into out[4], fixed order
