@@ -305,16 +305,35 @@ int build_geometry(lbm_ctx* c) {
   CK(c->wst.ensure(nl * WALL_STATE * c->ops->celem));
   CK(cudaMemsetAsync(c->wst.p, 0, nl * WALL_STATE * c->ops->celem, s));
   {
+    // Inline (fused-mode) choice per 32-cell x-group: WALL and reference cells are updated by the
+    // interior kernel when their group holds at least INLINE_MIN list cells; INFLOW/OUTFLOW cells
+    // and isolated list cells stay with the boundary-list kernel.
+    constexpr int INLINE_MIN = 8;
     std::vector<long long> cells(c->n_list);
     std::vector<uint8_t> tl(c->N);
     if (c->n_list) CK(cudaMemcpyAsync(cells.data(), c->lcell.p, c->n_list * sizeof(long long), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(tl.data(), c->type.p, c->N, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    for (long long row = 0; row < (long long)c->ny * c->nz; ++row) {
+      const long long base = row * c->nx;
+      for (int g0 = 0; g0 < c->nx; g0 += 32) {
+        const int g1 = std::min(c->nx, g0 + 32);
+        int cnt = 0;
+        for (int x = g0; x < g1; ++x) cnt += (tl[base + x] & T_LIST) != 0;
+        if (cnt < INLINE_MIN) continue;
+        for (int x = g0; x < g1; ++x) {
+          uint8_t& t = tl[base + x];
+          const int kind = t & T_KIND;
+          if ((t & T_LIST) && kind != K_INFLOW && kind != K_OUTFLOW) t |= T_INLINE;
+        }
+      }
+    }
+    CK(cudaMemcpyAsync(c->type.p, tl.data(), c->N, cudaMemcpyHostToDevice, s));
     std::vector<int> sub, wall;
     for (int k = 0; k < c->n_list; ++k) {
-      const int kind = tl[cells[k]] & T_KIND;
-      if (kind == K_INFLOW || kind == K_OUTFLOW) sub.push_back(k);
-      if (kind == K_WALL) wall.push_back(k);
+      const uint8_t t = tl[cells[k]];
+      if (!(t & T_INLINE)) sub.push_back(k);
+      else if ((t & T_KIND) == K_WALL) wall.push_back(k);
     }
     c->n_sub = int(sub.size());
     c->n_wall = int(wall.size());

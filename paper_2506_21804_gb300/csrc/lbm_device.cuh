@@ -24,7 +24,8 @@ namespace lbm {
 constexpr uint8_t T_KIND = 7;    // bits 0-2: kind
 constexpr uint8_t T_REF = 8;     // wall-model reference cell (writes its velocity)
 constexpr uint8_t T_NEAR = 16;   // some source position is solid or outside the domain
-constexpr uint8_t T_LIST = 32;   // handled by the boundary-list kernel
+constexpr uint8_t T_LIST = 32;   // on the boundary list
+constexpr uint8_t T_INLINE = 64; // list cell updated inside the interior kernel (fused mode)
 enum { K_FLUID = 0, K_SOLID = 1, K_WALL = 2, K_INFLOW = 3, K_OUTFLOW = 4 };
 enum { F_PERIODIC = 0, F_WALL = 1, F_SLIP = 2, F_OPEN = 3 };
 constexpr unsigned ST_NAN = 1u, ST_BADMASK = 2u;
@@ -149,8 +150,8 @@ struct Args {
   double rho_out;
   double drho_out;         // rho_out - 1, formed in double precision
   int wm;                  // wall model on
-  int fuse;                // 1: WALL and reference cells are updated by the interior kernel; the
-                           //    boundary-list kernel then runs over INFLOW/OUTFLOW entries only
+  int fuse;                // 1: list cells flagged T_INLINE are updated by the interior kernel; the
+                           //    boundary-list kernel then runs over the other entries only
   const int* lidx;         // list position of every cell (-1 off the list)
   const int* lsub;         // list positions handled by the boundary-list kernel (fused mode)
   int n_sub;

@@ -258,8 +258,9 @@ __device__ __forceinline__ void list_cell_inline(const Args& a, S* f, int x, int
   else scatter<Q, S, STORE_MIRROR>(a, f, x, y, z, n, false, h);
 }
 
-// Interior kernel: every FLUID cell off the boundary list, and in fused mode also the WALL and
-// reference cells of the list. Threads map to (x, y, z).
+// Interior kernel: every FLUID cell off the boundary list, and in fused mode also the list cells
+// flagged T_INLINE (WALL and reference cells in 32-cell x-groups dense in list cells, where the
+// extra path costs little divergence). Threads map to (x, y, z).
 // Occupancy target of the interior kernel (CTAs of 128 threads per SM): D3Q19 10 on even steps
 // (<= 51 registers) and 8 on odd steps (<= 64), D3Q27 5; the register cap falls on the rarely
 // taken boundary-cell path. The FP64 (reference) form is left unconstrained.
@@ -278,9 +279,7 @@ __global__ void __launch_bounds__(BULK_THREADS, (bulk_min_blocks<Q, S, ODD>())) 
   const uint8_t t = a.type[n];
   S* f = static_cast<S*>(a.f);
   if (t & (T_LIST | T_KIND)) {
-    const int kind = t & T_KIND;
-    if ((t & T_LIST) && a.fuse && kind != K_INFLOW && kind != K_OUTFLOW)
-      list_cell_inline<Q, S, ODD>(a, f, x, y, z, n, t);
+    if ((t & T_INLINE) && a.fuse) list_cell_inline<Q, S, ODD>(a, f, x, y, z, n, t);
     return;
   }
   const bool near = (t & T_NEAR) != 0;
@@ -305,8 +304,8 @@ __global__ void k_wall_state(const Args a) {
                 cptr<C>(a.wst) + (long long)WALL_STATE * k);
 }
 
-// Boundary-list kernel, one thread per list entry: every entry, or in fused mode the INFLOW/OUTFLOW
-// entries named by Args::lsub.
+// Boundary-list kernel, one thread per list entry: every entry, or in fused mode the entries not
+// handled inline (Args::lsub: INFLOW/OUTFLOW entries and list cells in sparse x-groups).
 template <int Q, class S, bool ODD>
 __global__ void __launch_bounds__(LIST_THREADS) k_list(const Args a) {
   using C = typename Codec<S>::C;
