@@ -200,6 +200,31 @@ def timed_glups(lat, steps, warmup):
     return lat.N * steps / (ms[2] * 1e-3) / 1e9, ms
 
 
+def adjoint_run(lbm, I, n, T, ckpt, W=None):
+    """Differentiation workload: duct n^3, objective over the last W of T steps, checkpoint interval
+    ckpt. The forward and backward are run twice (the first call allocates the checkpoints and the
+    ring); GLUPS from the second call's device times."""
+    W = W or max(1, T // 10)
+    wd = I.duct(n=n, u_in=0.04, tau=0.6, sigma=8.0, dtype=np.float32)
+    lat = lbm.Lattice.from_workload(wd, storage=lbm.F32)
+    res = {}
+    for rep in range(2):
+        lat.init_equilibrium(np.asarray(wd.rho0, np.float32), np.asarray(wd.u0, np.float32))
+        J = lat.objective_forward(T, W, 1, wd.nx - 2, ckpt=ckpt)
+        g, _ = lat.objective_backward()
+        rec, rev, fwd = lat.adjoint_timing()
+        cells = wd.N * T
+        res = {"cells": wd.N, "steps": T, "window": W, "checkpoint_interval": ckpt, "J": J,
+               "forward_glups": cells / (fwd * 1e-3) / 1e9,
+               "backward_glups": cells / ((rec + rev) * 1e-3) / 1e9,
+               "recompute_glups": cells / (rec * 1e-3) / 1e9,
+               "reverse_kernel_glups": cells / (rev * 1e-3) / 1e9,
+               "backward_over_forward": fwd / (rec + rev),
+               "grad_l2": float(np.linalg.norm(g))}
+    lat.close()
+    return res
+
+
 def secondary(lbm, I, torch):
     """Shorter runs of the other forms of the metric."""
     out = {}
@@ -234,24 +259,7 @@ def secondary(lbm, I, torch):
                                                  "interior_ms": ms[0] / 20, "list_ms": ms[1] / 20}
         lat.close()
     # adjoint on the 128^3 duct: forward with checkpoints, backward = recompute + reverse
-    wd = I.duct(n=128, u_in=0.04, tau=0.6, sigma=8.0, dtype=np.float32)
-    lat = lbm.Lattice.from_workload(wd, storage=lbm.F32)
-    T, W = 128, 16
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    lat.objective_forward(T, W, 1, wd.nx - 2, ckpt=32)
-    t1 = time.perf_counter()
-    lat.objective_backward()
-    t2 = time.perf_counter()
-    rec, rev = lat.adjoint_timing()
-    out["duct128_adjoint"] = {
-        "steps": T, "checkpoint_interval": 32,
-        "forward_glups_wall": wd.N * T / (t1 - t0) / 1e9,
-        "backward_glups_wall": wd.N * T / (t2 - t1) / 1e9,
-        "backward_glups_device": wd.N * T / ((rec + rev) * 1e-3) / 1e9,
-        "reverse_kernel_glups": wd.N * T / (rev * 1e-3) / 1e9,
-    }
-    lat.close()
+    out["duct128_adjoint"] = adjoint_run(lbm, I, 128, 128, 32)
     return out
 
 
@@ -264,9 +272,12 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the secondary forms and the CPU baseline")
     ap.add_argument("--size", type=int, nargs=3, default=None, metavar=("NX", "NY", "NZ"),
                     help="grid size (the headline channel is 256 256 256; other sizes are for profiling)")
-    ap.add_argument("--workload", default="channel", choices=["channel", "canopy"],
-                    help="channel (headline) or the urban canopy (for profiling the boundary-list kernel)")
+    ap.add_argument("--workload", default="channel", choices=["channel", "canopy", "duct"],
+                    help="channel (headline); the urban canopy or the differentiation duct (profiling)")
     ap.add_argument("--kernel", default="plain", choices=["plain", "staged"], help="interior kernel variant")
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"],
+                    help="population storage (the headline is f32; the others are for profiling)")
+    ap.add_argument("--lattice", type=int, default=19, choices=[19, 27], help="velocity set (profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -284,17 +295,27 @@ def main():
     build.build()
     lbm.lib()
 
-    headline = args.workload == "channel" and args.size in (None, [256, 256, 256])
+    if args.workload == "duct":
+        n = (args.size or (128, 128, 128))[0]
+        res = adjoint_run(lbm, I, n, max(args.steps, 2), 32 if args.steps >= 64 else 2)
+        print(json.dumps({"metric": "adjoint GLUPS (duct, checkpointed backward)", "value": res["backward_glups"],
+                          "unit": "GLUPS", "config": {"workload": f"duct {n}^3 D3Q19 FP32 porosity"}, "adjoint": res}))
+        return
+    headline = (args.workload == "channel" and args.size in (None, [256, 256, 256]) and args.storage == "f32"
+                and args.lattice == 19)
+    storage = {"f32": lbm.F32, "f16": lbm.F16, "bf16": lbm.BF16}[args.storage]
+    esize = 4 if args.storage == "f32" else 2
     if args.workload == "channel":
         nx, ny, nz = args.size or (256, 256, 256)
-        w = I.channel(nx=nx, ny=ny, nz=nz, seed=550 + rank, dtype=np.float32)
-        wname = WORKLOAD.replace("256x256x256", f"{nx}x{ny}x{nz}")
+        w = I.channel(nx=nx, ny=ny, nz=nz, seed=550 + rank, q=args.lattice, dtype=np.float32)
+        wname = WORKLOAD.replace("256x256x256", f"{nx}x{ny}x{nz}").replace("D3Q19", f"D3Q{args.lattice}").replace(
+            "FP32 storage", f"{args.storage.upper()} storage")
     else:
         nx, ny, nz = args.size or (512, 512, 256)
-        w = I.canopy(nx=nx, ny=ny, nz=nz, seed=2506, dtype=np.float32)
-        wname = f"urban canopy {nx}x{ny}x{nz} D3Q19 Smagorinsky + wall function, log-law inlet, FP32"
+        w = I.canopy(nx=nx, ny=ny, nz=nz, q=args.lattice, seed=2506, dtype=np.float32)
+        wname = f"urban canopy {nx}x{ny}x{nz} D3Q{args.lattice} Smagorinsky + wall function, log-law inlet, {args.storage.upper()}"
     stream = torch.cuda.current_stream()
-    lat = lbm.Lattice.from_workload(w, storage=lbm.F32)
+    lat = lbm.Lattice.from_workload(w, storage=storage)
     lat.set_stream(stream)
     if args.kernel == "staged":
         lat.set_option(lbm.OPT_KERNEL, lbm.KERNEL_STAGED)
@@ -315,12 +336,13 @@ def main():
     t_ms = max_over_ranks(ms[2], world)
     value = world * w.N * args.steps / (t_ms * 1e-3) / 1e9
     n_bulk = info["N"] - info["n_solid"] - info["n_list"]
-    bytes_bulk = n_bulk * Q19_FP32_BYTES + info["N"] * 1
+    per_cell = 2 * w.q * esize
+    bytes_bulk = n_bulk * per_cell + info["N"] * 1
     bulk_ms = ms[0] / args.steps
     peak, peak_src = peaks()
     achieved = bytes_bulk / (bulk_ms * 1e-3) / 1e9
     traffic = kernel_traffic("k_bulk", "channel256") if headline else None
-    step_bytes = (info["N"] - info["n_solid"]) * Q19_FP32_BYTES + info["N"]
+    step_bytes = (info["N"] - info["n_solid"]) * per_cell + info["N"]
 
     # end to end through the C ABI with host buffers: geometry + initial state in, fields out
     rho_h = np.asarray(w.rho0, np.float32)
@@ -344,7 +366,7 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
         "config": {"workload": wname, "kernel": args.kernel, "cells": w.N, "parallelism": f"replicas x{world}",
                    "l2": "state of 2.6 GB > 129 MB L2 between steps, no flush needed",
                    "non_solid_cells": info["N"] - info["n_solid"], "boundary_list_cells": info["n_list"]},

@@ -140,8 +140,9 @@ int lbm_objective_backward(lbm_ctx* ctx, double* dJ_dgamma, double* dJ_duin);
  * natural layout, dtype LBM_DTYPE_*), and adds (dS_{t+1}/dgamma)^T lam_in to dgamma (N, FP64) and
  * (dS_{t+1}/du_in)^T lam_in to duin (3*ny*nz, FP64); both nullable. */
 int lbm_adjoint_step(lbm_ctx* ctx, const void* lam_in, void* lam_out, int dtype, double* dgamma, double* duin);
-/* Device time of the adjoint kernels of the last backward: ms[0] recompute, ms[1] reverse. */
-int lbm_adjoint_timing(lbm_ctx* ctx, double ms[2]);
+/* Device times (CUDA events) of the last differentiation run: ms[0] segment recomputation and
+ * ms[1] reverse sweep of lbm_objective_backward, ms[2] the whole lbm_objective_forward. */
+int lbm_adjoint_timing(lbm_ctx* ctx, double ms[3]);
 
 /* Checkpoint of the whole state (populations, step counter, reference buffer). With buf == NULL,
  * *len receives the size needed. lbm_load restores a buffer written by lbm_save of a context with

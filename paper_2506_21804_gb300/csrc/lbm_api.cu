@@ -99,7 +99,7 @@ struct lbm_ctx {
   int adj_T = 0, adj_W = 0, adj_xa = 0, adj_xb = 0, adj_ck = 0;
   double adj_wa = 0, adj_wb = 0;
   long long adj_t0 = -1;
-  double adj_ms[2] = {0, 0};
+  double adj_ms[3] = {0, 0, 0};
 
   ~lbm_ctx() {
     DevBuf* all[] = {&lidx, &lsub, &lwall, &wst, &f, &type, &mask, &wdist, &gamma, &uin, &lcell, &nsum, &wref, &lxyz, &lcode, &wnrm, &wyw, &ref0, &ref1, &status, &red,
@@ -889,6 +889,10 @@ int lbm_objective_forward(lbm_ctx* c, int T, int W, int xa, int xb, int ckpt, do
     if (e != cudaSuccess) return fail(e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, "checkpoints: %s", cudaGetErrorString(e));
   }
   CK(cudaMemsetAsync(c->redout.p, 0, sizeof(double), c->stream));
+  cudaEvent_t f0, f1;
+  CK(cudaEventCreate(&f0));
+  CK(cudaEventCreate(&f1));
+  CK(cudaEventRecord(f0, c->stream));
   for (int s = 0; s < T; ++s) {
     if (s % ckpt == 0) CK(cudaMemcpyAsync(c->ckpts[s / ckpt].p, c->f.p, sb, cudaMemcpyDeviceToDevice, c->stream));
     launch_step(c);
@@ -897,9 +901,15 @@ int lbm_objective_forward(lbm_ctx* c, int T, int W, int xa, int xb, int ckpt, do
       c->ops->plane_rho(b, c->f.p, int(c->t & 1), xa, xb, static_cast<double*>(c->redout.p), wa, wb, c->stream);
     }
   }
+  CK(cudaEventRecord(f1, c->stream));
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(c->red_h, c->redout.p, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   if ((rc = read_status(c)) != LBM_OK) return rc;
+  float fms = 0;
+  CK(cudaEventElapsedTime(&fms, f0, f1));
+  c->adj_ms[2] = fms;
+  cudaEventDestroy(f0);
+  cudaEventDestroy(f1);
   *J = c->red_h[0];
   c->adj_T = T; c->adj_W = W; c->adj_xa = xa; c->adj_xb = xb; c->adj_ck = ckpt;
   c->adj_wa = wa; c->adj_wb = wb;
@@ -1045,10 +1055,11 @@ int lbm_adjoint_step(lbm_ctx* c, const void* lam_in, void* lam_out, int dtype, d
   return LBM_OK;
 }
 
-int lbm_adjoint_timing(lbm_ctx* c, double ms[2]) {
+int lbm_adjoint_timing(lbm_ctx* c, double ms[3]) {
   if (!c || !ms) return fail(LBM_EINVAL, "null argument");
   ms[0] = c->adj_ms[0];
   ms[1] = c->adj_ms[1];
+  ms[2] = c->adj_ms[2];
   return LBM_OK;
 }
 

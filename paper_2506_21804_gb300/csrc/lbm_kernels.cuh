@@ -262,10 +262,10 @@ __device__ __forceinline__ void list_cell_inline(const Args& a, S* f, int x, int
 // flagged T_INLINE (WALL and reference cells in 32-cell x-groups dense in list cells, where the
 // extra path costs little divergence). Threads map to (x, y, z).
 // Occupancy target of the interior kernel (CTAs of 128 threads per SM): D3Q19 10 on even steps
-// (<= 51 registers) and 8 on odd steps (<= 64), D3Q27 5; the register cap falls on the rarely
-// taken boundary-cell path. The FP64 (reference) form is left unconstrained.
+// (<= 51 registers) and 8 on odd steps (<= 64), D3Q27 8 and 6; the register cap falls on the
+// rarely taken boundary-cell path. The FP64 (reference) form is left unconstrained.
 template <int Q, class S, bool ODD> constexpr int bulk_min_blocks() {
-  return sizeof(S) == 8 ? 1 : (Q == 19 ? (ODD ? 8 : 10) : 5);
+  return sizeof(S) == 8 ? 1 : (Q == 19 ? (ODD ? 8 : 10) : (ODD ? 6 : 8));
 }
 
 template <int Q, class S, bool ODD>

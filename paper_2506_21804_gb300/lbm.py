@@ -287,7 +287,8 @@ class Lattice:
         return out, g, u.reshape(3, self.ny * self.nz)
 
     def adjoint_timing(self):
-        ms = np.zeros(2)
+        """[recompute ms, reverse ms, forward ms] of the last objective forward/backward."""
+        ms = np.zeros(3)
         _check(lib().lbm_adjoint_timing(self.h, ms.ctypes.data_as(_p)))
         return ms
 
