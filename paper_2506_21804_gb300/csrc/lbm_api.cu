@@ -84,8 +84,8 @@ struct lbm_ctx {
   unsigned status_seen = 0;
   // device buffers
   DevBuf f, type, mask, wdist, gamma, uin, lcell, nsum, wref, lxyz, lcode, wnrm, wyw, ref0, ref1, status, red, redout, stage;
-  DevBuf lidx, lsub, lwall, wst;
-  int n_sub = 0, n_wall = 0;
+  DevBuf lidx, lsub, lwall, lbc, wst;
+  int n_sub = 0, n_wall = 0, n_bc = 0;
   bool has_gamma = false, has_wdist = false;
   int n_list = 0;
   long long counts[8] = {0};  // wall, ref, inflow, outflow, solid
@@ -102,7 +102,7 @@ struct lbm_ctx {
   double adj_ms[3] = {0, 0, 0};
 
   ~lbm_ctx() {
-    DevBuf* all[] = {&lidx, &lsub, &lwall, &wst, &f, &type, &mask, &wdist, &gamma, &uin, &lcell, &nsum, &wref, &lxyz, &lcode, &wnrm, &wyw, &ref0, &ref1, &status, &red,
+    DevBuf* all[] = {&lidx, &lsub, &lwall, &lbc, &wst, &f, &type, &mask, &wdist, &gamma, &uin, &lcell, &nsum, &wref, &lxyz, &lcode, &wnrm, &wyw, &ref0, &ref1, &status, &red,
                      &redout, &stage, &lamA, &lamB, &dgam, &duin};
     for (DevBuf* b : all) b->release();
     for (auto& b : ckpts) b.release();
@@ -172,6 +172,8 @@ Args make_args(const lbm_ctx* c) {
   a.lsub = a.fuse ? static_cast<const int*>(c->lsub.p) : nullptr;
   a.n_sub = c->n_sub;
   a.lwall = static_cast<const int*>(c->lwall.p);
+  a.lbc = static_cast<const int*>(c->lbc.p);
+  a.n_bc = c->n_bc;
   a.n_wall = c->n_wall;
   a.wst = c->wst.p;
   a.idx32 = ((unsigned long long)c->q * (unsigned long long)c->stride < (1ull << 32) && c->N < (1ll << 31)) ? 1 : 0;
@@ -329,12 +331,16 @@ int build_geometry(lbm_ctx* c) {
       }
     }
     CK(cudaMemcpyAsync(c->type.p, tl.data(), c->N, cudaMemcpyHostToDevice, s));
-    std::vector<int> sub, wall;
+    std::vector<int> sub, wall, bc;
     for (int k = 0; k < c->n_list; ++k) {
       const uint8_t t = tl[cells[k]];
       if (!(t & T_INLINE)) sub.push_back(k);
       else if ((t & T_KIND) == K_WALL) wall.push_back(k);
+      if ((t & T_KIND) == K_INFLOW || (t & T_KIND) == K_OUTFLOW) bc.push_back(k);
     }
+    c->n_bc = int(bc.size());
+    CK(c->lbc.ensure(std::max<size_t>(1, bc.size()) * sizeof(int)));
+    if (!bc.empty()) CK(cudaMemcpyAsync(c->lbc.p, bc.data(), bc.size() * sizeof(int), cudaMemcpyHostToDevice, s));
     c->n_sub = int(sub.size());
     c->n_wall = int(wall.size());
     CK(c->lsub.ensure(std::max<size_t>(1, sub.size()) * sizeof(int)));

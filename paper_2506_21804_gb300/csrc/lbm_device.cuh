@@ -155,6 +155,8 @@ struct Args {
   const int* lidx;         // list position of every cell (-1 off the list)
   const int* lsub;         // list positions handled by the boundary-list kernel (fused mode)
   int n_sub;
+  const int* lbc;          // list positions of INFLOW/OUTFLOW entries
+  int n_bc;
   const int* lwall;        // list positions of WALL entries (wall-state pass)
   int n_wall;
   void* wst;               // wall-model state per list entry (WALL_STATE values)

@@ -74,6 +74,19 @@ struct Impl {
     if (L.stages >= 2) {
       if (odd ? launch_tma<true>(a, L, s) : launch_tma<false>(a, L, s)) return;
     }
+    if constexpr (sizeof(S) == 2) {
+      if (a.idx32 && a.nx % 2 == 0) {
+        Args h = a;
+        h.nx = a.nx;  // launch shape over cell pairs
+        dim3 b = bulk_block(a);
+        int bx = (a.nx / 2) >= 64 ? 64 : (((a.nx / 2) + 31) / 32) * 32;
+        b = dim3(bx, BULK_THREADS / bx, 1);
+        const dim3 g((a.nx / 2 + b.x - 1) / b.x, (a.ny + b.y - 1) / b.y, a.nz);
+        if (odd) k_bulk2<Q, S, true><<<g, b, 0, s>>>(h);
+        else k_bulk2<Q, S, false><<<g, b, 0, s>>>(h);
+        return;
+      }
+    }
     if (odd) k_bulk<Q, S, true><<<bulk_grid(a), bulk_block(a), 0, s>>>(a);
     else k_bulk<Q, S, false><<<bulk_grid(a), bulk_block(a), 0, s>>>(a);
   }
@@ -112,9 +125,13 @@ struct Impl {
   }
   static void step_oop(const Args& a, const void* fin, void* fout, cudaStream_t s) {
     k_step_oop<Q, S><<<bulk_grid(a), bulk_block(a), 0, s>>>(a, static_cast<const S*>(fin), static_cast<S*>(fout));
+    if (a.n_bc > 0)
+      k_step_oop_bc<Q, S><<<blocks_for(a.n_bc, LIST_THREADS), LIST_THREADS, 0, s>>>(a, static_cast<const S*>(fin),
+                                                                                   static_cast<S*>(fout));
   }
   static void reverse(const Args& a, const AdjArgs& d, cudaStream_t s) {
     k_reverse<Q, S><<<bulk_grid(a), bulk_block(a), 0, s>>>(a, d);
+    if (a.n_bc > 0) k_reverse_bc<Q, S><<<blocks_for(a.n_bc, LIST_THREADS), LIST_THREADS, 0, s>>>(a, d);
   }
   static void plane_rho(const Args& a, const void* state, int swapped, int xa, int xb, double* acc, double wa, double wb,
                         cudaStream_t s) {

@@ -161,9 +161,24 @@ struct Nbr {
   }
 };
 
+// Bit mask of the directions whose code is 2 (the general rule is needed).
+__device__ __forceinline__ bool has_general(unsigned long long code) { return (code & 0xAAAAAAAAAAAAAAAAull) != 0; }
+
 template <int Q, class S>
 __device__ __forceinline__ void gather_coded(const Args& a, const S* src, int x, int y, int z, long long n,
                                              unsigned long long code, typename Codec<S>::C* h) {
+  if (!has_general(code) && a.idx32) {
+    // codes 0/1 only: the plain neighbour slot or the cell's own slot, chosen without branches
+    const Nbr32 nb(a, x, y, z, n);
+    const unsigned us = unsigned(a.stride), un = unsigned(n);
+    sfor<0, Q>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      const unsigned plain = nb.at<-Lat<Q>::cx(i), -Lat<Q>::cy(i), -Lat<Q>::cz(i)>(unsigned(opp<Q>(i)) * us);
+      const unsigned own = unsigned(i) * us + un;
+      h[i] = Codec<S>::ld(src + (((code >> (2 * i)) & 1ull) ? own : plain));
+    });
+    return;
+  }
   const Nbr nb(a, x, y, z);
   sfor<0, Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
@@ -180,6 +195,17 @@ __device__ __forceinline__ void gather_coded(const Args& a, const S* src, int x,
 template <int Q, class S>
 __device__ __forceinline__ void scatter_coded(const Args& a, S* dst, int x, int y, int z, long long n,
                                               unsigned long long code, const typename Codec<S>::C* h) {
+  if (!has_general(code) && a.idx32) {
+    const Nbr32 nb(a, x, y, z, n);
+    const unsigned us = unsigned(a.stride), un = unsigned(n);
+    sfor<0, Q>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      const unsigned plain = nb.at<-Lat<Q>::cx(i), -Lat<Q>::cy(i), -Lat<Q>::cz(i)>(unsigned(opp<Q>(i)) * us);
+      const unsigned own = unsigned(i) * us + un;
+      Codec<S>::st(dst + (((code >> (2 * i)) & 1ull) ? own : plain), h[opp<Q>(i)]);
+    });
+    return;
+  }
   const Nbr nb(a, x, y, z);
   sfor<0, Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
@@ -191,6 +217,13 @@ __device__ __forceinline__ void scatter_coded(const Args& a, S* dst, int x, int 
     else slot_of<Q>(a, x, y, z, n, i, p, m);
     Codec<S>::st(dst + (long long)p * a.stride + m, h[opp<Q>(i)]);
   });
+}
+
+// Slot code of a cell for the adjoint and recompute passes: list cells carry theirs; other cells
+// use plain slots unless they are NEAR (then the general rule, returned as all-2 codes).
+__device__ __forceinline__ unsigned long long cell_code(const Args& a, long long n, uint8_t t) {
+  if (t & T_LIST) return a.lcode[a.lidx[n]];
+  return (t & T_NEAR) ? 0xAAAAAAAAAAAAAAAAull : 0ull;
 }
 
 template <class C> __device__ __forceinline__ const C* cptr(const void* p) { return static_cast<const C*>(p); }
@@ -269,15 +302,8 @@ template <int Q, class S, bool ODD> constexpr int bulk_min_blocks() {
 }
 
 template <int Q, class S, bool ODD>
-__global__ void __launch_bounds__(BULK_THREADS, (bulk_min_blocks<Q, S, ODD>())) k_bulk(const Args a) {
+__device__ __forceinline__ void bulk_cell(const Args& a, S* f, int x, int y, int z, long long n, uint8_t t) {
   using C = typename Codec<S>::C;
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  const int z = blockIdx.z;
-  if (x >= a.nx || y >= a.ny) return;
-  const long long n = x + (long long)y * a.nx + (long long)z * a.nxy;
-  const uint8_t t = a.type[n];
-  S* f = static_cast<S*>(a.f);
   if (t & (T_LIST | T_KIND)) {
     if ((t & T_INLINE) && a.fuse) list_cell_inline<Q, S, ODD>(a, f, x, y, z, n, t);
     return;
@@ -289,6 +315,102 @@ __global__ void __launch_bounds__(BULK_THREADS, (bulk_min_blocks<Q, S, ODD>())) 
   collide_fluid<Q, C>(h, gamma_at<C>(a, n), a, rho, urx, ury, urz);
   if (!finite_all<C>(rho, urx, ury, urz)) atomicOr(a.status, ST_NAN);
   scatter<Q, S, ODD ? STORE_SLOTS : STORE_MIRROR>(a, f, x, y, z, n, near, h);
+}
+
+template <int Q, class S, bool ODD>
+__global__ void __launch_bounds__(BULK_THREADS, (bulk_min_blocks<Q, S, ODD>())) k_bulk(const Args a) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= a.nx || y >= a.ny) return;
+  const long long n = x + (long long)y * a.nx + (long long)z * a.nxy;
+  bulk_cell<Q, S, ODD>(a, static_cast<S*>(a.f), x, y, z, n, a.type[n]);
+}
+
+// ---- 16-bit storage, two cells per thread -------------------------------------------------------------
+template <class S> struct Pair;
+template <> struct Pair<__half> {
+  using V = __half2;
+  static __device__ __forceinline__ float2 ld(const __half* p) { return __half22float2(*reinterpret_cast<const __half2*>(p)); }
+  static __device__ __forceinline__ void st(__half* p, float a, float b) { *reinterpret_cast<__half2*>(p) = __floats2half2_rn(a, b); }
+};
+template <> struct Pair<__nv_bfloat16> {
+  using V = __nv_bfloat162;
+  static __device__ __forceinline__ float2 ld(const __nv_bfloat16* p) {
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
+  }
+  static __device__ __forceinline__ void st(__nv_bfloat16* p, float a, float b) {
+    *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(a, b);
+  }
+};
+
+// Interior kernel for 16-bit storage (nx even, 32-bit indices): the thread owns cells x0 = 2j and
+// x0 + 1. When both are plain FLUID cells, directions without an x-component move both cells'
+// values with one 32-bit access and the others with two 16-bit accesses; otherwise each cell takes
+// the per-cell path.
+template <int Q, class S, bool ODD>
+__global__ void __launch_bounds__(BULK_THREADS, (Q == 19 ? 6 : 4)) k_bulk2(const Args a) {
+  const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x0 >= a.nx || y >= a.ny) return;
+  const long long n0 = x0 + (long long)y * a.nx + (long long)z * a.nxy;
+  S* f = static_cast<S*>(a.f);
+  const unsigned short tt = *reinterpret_cast<const unsigned short*>(a.type + n0);
+  const uint8_t t0 = uint8_t(tt & 0xff), t1 = uint8_t(tt >> 8);
+  if (t0 | t1) {
+    bulk_cell<Q, S, ODD>(a, f, x0, y, z, n0, t0);
+    bulk_cell<Q, S, ODD>(a, f, x0 + 1, y, z, n0 + 1, t1);
+    return;
+  }
+  float h0[Q], h1[Q];
+  const unsigned us = unsigned(a.stride), un = unsigned(n0);
+  if constexpr (!ODD) {
+    sfor<0, Q>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      const float2 v = Pair<S>::ld(f + (unsigned(i) * us + un));
+      h0[i] = v.x;
+      h1[i] = v.y;
+    });
+  } else {
+    const Nbr32 nb0(a, x0, y, z, n0), nb1(a, x0 + 1, y, z, n0 + 1);
+    sfor<0, Q>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      constexpr int cx = -Lat<Q>::cx(i), cy = -Lat<Q>::cy(i), cz = -Lat<Q>::cz(i);
+      const unsigned pb = unsigned(opp<Q>(i)) * us;
+      if constexpr (cx == 0) {
+        const float2 v = Pair<S>::ld(f + nb0.at<0, cy, cz>(pb));
+        h0[i] = v.x;
+        h1[i] = v.y;
+      } else {
+        h0[i] = Codec<S>::ld(f + nb0.at<cx, cy, cz>(pb));
+        h1[i] = Codec<S>::ld(f + nb1.at<cx, cy, cz>(pb));
+      }
+    });
+  }
+  float r0, u0x, u0y, u0z, r1, u1x, u1y, u1z;
+  collide_fluid<Q, float>(h0, gamma_at<float>(a, n0), a, r0, u0x, u0y, u0z);
+  collide_fluid<Q, float>(h1, gamma_at<float>(a, n0 + 1), a, r1, u1x, u1y, u1z);
+  if (!finite_all<float>(r0, u0x, u0y, u0z) || !finite_all<float>(r1, u1x, u1y, u1z)) atomicOr(a.status, ST_NAN);
+  if constexpr (!ODD) {
+    sfor<0, Q>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      Pair<S>::st(f + (unsigned(opp<Q>(i)) * us + un), h0[i], h1[i]);
+    });
+  } else {
+    const Nbr32 nb0(a, x0, y, z, n0), nb1(a, x0 + 1, y, z, n0 + 1);
+    sfor<0, Q>([&](auto I) {
+      constexpr int k = decltype(I)::value;  // f*_k goes to slot (k, x + c_k)
+      constexpr int cx = Lat<Q>::cx(k), cy = Lat<Q>::cy(k), cz = Lat<Q>::cz(k);
+      const unsigned pb = unsigned(k) * us;
+      if constexpr (cx == 0) {
+        Pair<S>::st(f + nb0.at<0, cy, cz>(pb), h0[k], h1[k]);
+      } else {
+        Codec<S>::st(f + nb0.at<cx, cy, cz>(pb), h0[k]);
+        Codec<S>::st(f + nb1.at<cx, cy, cz>(pb), h1[k]);
+      }
+    });
+  }
 }
 
 // Wall-model state of every WALL entry from the previous step's reference velocities (fused mode).
@@ -332,10 +454,23 @@ __global__ void __launch_bounds__(LIST_THREADS) k_list(const Args a) {
 }
 
 // Out-of-place step for the adjoint's recomputation: natural-layout state fin -> natural-layout fout.
-// Handles every cell kind (the wall model is excluded by the host).
+// The wall model is excluded by the host; INFLOW/OUTFLOW cells go to k_step_oop_bc.
+template <int Q, class S>
+__device__ __forceinline__ void oop_cell(const Args& a, const S* fin, S* fout, int x, int y, int z, long long n, uint8_t t) {
+  using C = typename Codec<S>::C;
+  const int kind = t & T_KIND;
+  C h[Q];
+  gather<Q, S, LOAD_LOCAL>(a, fin, x, y, z, n, false, h);
+  apply_bc<Q, C>(a, kind, y, z, h);
+  C rho, urx, ury, urz;
+  collide_fluid<Q, C>(h, gamma_at<C>(a, n), a, rho, urx, ury, urz);
+  if (!finite_all<C>(rho, urx, ury, urz)) atomicOr(a.status, ST_NAN);
+  if (!(t & (T_LIST | T_NEAR))) scatter<Q, S, STORE_SLOTS>(a, fout, x, y, z, n, false, h);
+  else scatter_coded<Q, S>(a, fout, x, y, z, n, cell_code(a, n, t), h);
+}
+
 template <int Q, class S>
 __global__ void __launch_bounds__(BULK_THREADS) k_step_oop(const Args a, const S* __restrict__ fin, S* __restrict__ fout) {
-  using C = typename Codec<S>::C;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
@@ -343,15 +478,17 @@ __global__ void __launch_bounds__(BULK_THREADS) k_step_oop(const Args a, const S
   const long long n = x + (long long)y * a.nx + (long long)z * a.nxy;
   const uint8_t t = a.type[n];
   const int kind = t & T_KIND;
-  if (kind == K_SOLID) return;
-  const bool near = (t & T_NEAR) != 0;
-  C h[Q];
-  gather<Q, S, LOAD_LOCAL>(a, fin, x, y, z, n, near, h);
-  apply_bc<Q, C>(a, kind, y, z, h);
-  C rho, urx, ury, urz;
-  collide_fluid<Q, C>(h, gamma_at<C>(a, n), a, rho, urx, ury, urz);
-  if (!finite_all<C>(rho, urx, ury, urz)) atomicOr(a.status, ST_NAN);
-  scatter<Q, S, STORE_SLOTS>(a, fout, x, y, z, n, near, h);
+  if (kind == K_SOLID || kind == K_INFLOW || kind == K_OUTFLOW) return;
+  oop_cell<Q, S>(a, fin, fout, x, y, z, n, t);
+}
+
+template <int Q, class S>
+__global__ void __launch_bounds__(LIST_THREADS) k_step_oop_bc(const Args a, const S* __restrict__ fin, S* __restrict__ fout) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= a.n_bc) return;
+  const int k = a.lbc[j];
+  const long long n = a.lcell[k];
+  oop_cell<Q, S>(a, fin, fout, a.lxyz[3 * k], a.lxyz[3 * k + 1], a.lxyz[3 * k + 2], n, a.type[n]);
 }
 
 // ---- state access ------------------------------------------------------------------------------------
@@ -566,27 +703,15 @@ __global__ void __launch_bounds__(1024) k_plane_rho(const Args a, const S* state
 // lam_out(n) = (d f*(n) / d f(n))^T mu(n) (+ objective weights), mu_k(n) = lam_in at the slot that
 // f*_k(n) streams into; gamma and inlet-velocity sensitivities accumulate in C precision.
 template <int Q, class S>
-__global__ void __launch_bounds__(BULK_THREADS) k_reverse(const Args a, const AdjArgs d) {
+__device__ __forceinline__ void reverse_cell(const Args& a, const AdjArgs& d, int x, int y, int z, long long n, uint8_t t) {
   using C = typename Codec<S>::C;
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  const int z = blockIdx.z;
-  if (x >= a.nx || y >= a.ny) return;
-  const long long n = x + (long long)y * a.nx + (long long)z * a.nxy;
-  const uint8_t t = a.type[n];
   const int kind = t & T_KIND;
-  C* lo = cptr<C>(d.lam_out);
-  if (kind == K_SOLID) {
-    sfor<0, Q>([&](auto I) { lo[(long long)I * a.stride + n] = C(0); });
-    return;
-  }
-  const bool near = (t & T_NEAR) != 0;
-  // mu_opp(i) from slot of direction i (where f*_opp(i) went), read from the natural-layout lam_in
-  const C* li = cptr<C>(d.lam_in);
+  const unsigned long long code = cell_code(a, n, t);
+  // mu_opp(i) from the slot of direction i (where f*_opp(i) streamed to) of the natural-layout lam_in
   C mu[Q];
   {
     C tmp[Q];
-    gather<Q, C, LOAD_SLOTS>(a, li, x, y, z, n, near, tmp);
+    gather_coded<Q, C>(a, cptr<C>(d.lam_in), x, y, z, n, code, tmp);
     sfor<0, Q>([&](auto I) {
       constexpr int i = decltype(I)::value;
       mu[opp<Q>(i)] = tmp[i];
@@ -616,6 +741,7 @@ __global__ void __launch_bounds__(BULK_THREADS) k_reverse(const Args a, const Ad
     const C w = C(x == d.xa ? d.wa : 0.0) + C(x == d.xb ? d.wb : 0.0);
     sfor<0, Q>([&](auto I) { lam[I] += w; });
   }
+  C* lo = cptr<C>(d.lam_out);
   sfor<0, Q>([&](auto I) { lo[(long long)I * a.stride + n] = lam[I]; });
   if (d.dgam) cptr<C>(d.dgam)[n] += ggam;
   if (kind == K_INFLOW && d.duin) {
@@ -625,6 +751,37 @@ __global__ void __launch_bounds__(BULK_THREADS) k_reverse(const Args a, const Ad
     atomicAdd(du + pl + p, gub[1]);
     atomicAdd(du + 2 * pl + p, gub[2]);
   }
+}
+
+// Reverse step over every non-solid cell except INFLOW/OUTFLOW cells (k_reverse_bc handles those,
+// so that their boundary-condition reverse does not diverge the warps of the interior).
+template <int Q, class S>
+__global__ void __launch_bounds__(BULK_THREADS) k_reverse(const Args a, const AdjArgs d) {
+  using C = typename Codec<S>::C;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= a.nx || y >= a.ny) return;
+  const long long n = x + (long long)y * a.nx + (long long)z * a.nxy;
+  const uint8_t t = a.type[n];
+  const int kind = t & T_KIND;
+  if (kind == K_SOLID) {
+    C* lo = cptr<C>(d.lam_out);
+    sfor<0, Q>([&](auto I) { lo[(long long)I * a.stride + n] = C(0); });
+    return;
+  }
+  if (kind == K_INFLOW || kind == K_OUTFLOW) return;
+  reverse_cell<Q, S>(a, d, x, y, z, n, t);
+}
+
+// Reverse step of the INFLOW/OUTFLOW entries (Args::lbc).
+template <int Q, class S>
+__global__ void __launch_bounds__(LIST_THREADS) k_reverse_bc(const Args a, const AdjArgs d) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= a.n_bc) return;
+  const int k = a.lbc[j];
+  const long long n = a.lcell[k];
+  reverse_cell<Q, S>(a, d, a.lxyz[3 * k], a.lxyz[3 * k + 1], a.lxyz[3 * k + 2], n, a.type[n]);
 }
 
 // Adjoint seed lambda_T = dJ/dS_T: weight wa on every population of the non-solid cells of plane
