@@ -328,28 +328,41 @@ __global__ void __launch_bounds__(BULK_THREADS, (bulk_min_blocks<Q, S, ODD>())) 
 }
 
 // ---- 16-bit storage, two cells per thread -------------------------------------------------------------
+// A pair register holds the same population of cells x0 (low half) and x0 + 1 (high half).
 template <class S> struct Pair;
 template <> struct Pair<__half> {
   using V = __half2;
-  static __device__ __forceinline__ float2 ld(const __half* p) { return __half22float2(*reinterpret_cast<const __half2*>(p)); }
-  static __device__ __forceinline__ void st(__half* p, float a, float b) { *reinterpret_cast<__half2*>(p) = __floats2half2_rn(a, b); }
+  static __device__ __forceinline__ V ld(const __half* p) { return *reinterpret_cast<const __half2*>(p); }
+  static __device__ __forceinline__ void st(__half* p, V v) { *reinterpret_cast<__half2*>(p) = v; }
+  static __device__ __forceinline__ V make(__half lo, __half hi) { return __halves2half2(lo, hi); }
+  static __device__ __forceinline__ __half lo(V v) { return __low2half(v); }
+  static __device__ __forceinline__ __half hi(V v) { return __high2half(v); }
+  static __device__ __forceinline__ float lof(V v) { return __low2float(v); }
+  static __device__ __forceinline__ float hif(V v) { return __high2float(v); }
+  static __device__ __forceinline__ V with_lo(V v, float x) { return __halves2half2(__float2half_rn(x), __high2half(v)); }
+  static __device__ __forceinline__ V with_hi(V v, float x) { return __halves2half2(__low2half(v), __float2half_rn(x)); }
 };
 template <> struct Pair<__nv_bfloat16> {
   using V = __nv_bfloat162;
-  static __device__ __forceinline__ float2 ld(const __nv_bfloat16* p) {
-    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
-  }
-  static __device__ __forceinline__ void st(__nv_bfloat16* p, float a, float b) {
-    *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(a, b);
-  }
+  static __device__ __forceinline__ V ld(const __nv_bfloat16* p) { return *reinterpret_cast<const __nv_bfloat162*>(p); }
+  static __device__ __forceinline__ void st(__nv_bfloat16* p, V v) { *reinterpret_cast<__nv_bfloat162*>(p) = v; }
+  static __device__ __forceinline__ V make(__nv_bfloat16 lo, __nv_bfloat16 hi) { return __halves2bfloat162(lo, hi); }
+  static __device__ __forceinline__ __nv_bfloat16 lo(V v) { return __low2bfloat16(v); }
+  static __device__ __forceinline__ __nv_bfloat16 hi(V v) { return __high2bfloat16(v); }
+  static __device__ __forceinline__ float lof(V v) { return __low2float(v); }
+  static __device__ __forceinline__ float hif(V v) { return __high2float(v); }
+  static __device__ __forceinline__ V with_lo(V v, float x) { return __halves2bfloat162(__float2bfloat16_rn(x), __high2bfloat16(v)); }
+  static __device__ __forceinline__ V with_hi(V v, float x) { return __halves2bfloat162(__low2bfloat16(v), __float2bfloat16_rn(x)); }
 };
 
 // Interior kernel for 16-bit storage (nx even, 32-bit indices): the thread owns cells x0 = 2j and
 // x0 + 1. When both are plain FLUID cells, directions without an x-component move both cells'
-// values with one 32-bit access and the others with two 16-bit accesses; otherwise each cell takes
-// the per-cell path.
+// values with one 32-bit access and the others with two 16-bit accesses; the pair stays packed in
+// registers and the two cells are collided one after the other. Otherwise each cell takes the
+// per-cell path.
 template <int Q, class S, bool ODD>
-__global__ void __launch_bounds__(BULK_THREADS, (Q == 19 ? 6 : 4)) k_bulk2(const Args a) {
+__global__ void __launch_bounds__(BULK_THREADS, (Q == 19 ? 8 : 4)) k_bulk2(const Args a) {
+  using P = Pair<S>;
   const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
@@ -363,14 +376,12 @@ __global__ void __launch_bounds__(BULK_THREADS, (Q == 19 ? 6 : 4)) k_bulk2(const
     bulk_cell<Q, S, ODD>(a, f, x0 + 1, y, z, n0 + 1, t1);
     return;
   }
-  float h0[Q], h1[Q];
+  typename P::V raw[Q];
   const unsigned us = unsigned(a.stride), un = unsigned(n0);
   if constexpr (!ODD) {
     sfor<0, Q>([&](auto I) {
       constexpr int i = decltype(I)::value;
-      const float2 v = Pair<S>::ld(f + (unsigned(i) * us + un));
-      h0[i] = v.x;
-      h1[i] = v.y;
+      raw[i] = P::ld(f + (unsigned(i) * us + un));
     });
   } else {
     const Nbr32 nb0(a, x0, y, z, n0), nb1(a, x0 + 1, y, z, n0 + 1);
@@ -378,24 +389,34 @@ __global__ void __launch_bounds__(BULK_THREADS, (Q == 19 ? 6 : 4)) k_bulk2(const
       constexpr int i = decltype(I)::value;
       constexpr int cx = -Lat<Q>::cx(i), cy = -Lat<Q>::cy(i), cz = -Lat<Q>::cz(i);
       const unsigned pb = unsigned(opp<Q>(i)) * us;
-      if constexpr (cx == 0) {
-        const float2 v = Pair<S>::ld(f + nb0.at<0, cy, cz>(pb));
-        h0[i] = v.x;
-        h1[i] = v.y;
-      } else {
-        h0[i] = Codec<S>::ld(f + nb0.at<cx, cy, cz>(pb));
-        h1[i] = Codec<S>::ld(f + nb1.at<cx, cy, cz>(pb));
-      }
+      if constexpr (cx == 0) raw[i] = P::ld(f + nb0.at<0, cy, cz>(pb));
+      else raw[i] = P::make(f[nb0.at<cx, cy, cz>(pb)], f[nb1.at<cx, cy, cz>(pb)]);
     });
   }
-  float r0, u0x, u0y, u0z, r1, u1x, u1y, u1z;
-  collide_fluid<Q, float>(h0, gamma_at<float>(a, n0), a, r0, u0x, u0y, u0z);
-  collide_fluid<Q, float>(h1, gamma_at<float>(a, n0 + 1), a, r1, u1x, u1y, u1z);
-  if (!finite_all<float>(r0, u0x, u0y, u0z) || !finite_all<float>(r1, u1x, u1y, u1z)) atomicOr(a.status, ST_NAN);
+  bool ok = true;
+  {
+    float h[Q], r, ux, uy, uz;
+    sfor<0, Q>([&](auto I) { h[I] = P::lof(raw[I]); });
+    collide_fluid<Q, float>(h, gamma_at<float>(a, n0), a, r, ux, uy, uz);
+    ok = finite_all<float>(r, ux, uy, uz);
+    sfor<0, Q>([&](auto I) { raw[I] = P::with_lo(raw[I], h[I]); });
+  }
+  {
+    float h[Q], r, ux, uy, uz;
+    sfor<0, Q>([&](auto I) { h[I] = P::hif(raw[I]); });
+    collide_fluid<Q, float>(h, gamma_at<float>(a, n0 + 1), a, r, ux, uy, uz);
+    ok = ok && finite_all<float>(r, ux, uy, uz);
+    sfor<0, Q>([&](auto I) { raw[I] = P::with_hi(raw[I], h[I]); });
+  }
+  if (!ok) atomicOr(a.status, ST_NAN);
   if constexpr (!ODD) {
+    // The store addresses equal the load addresses; an opaque copy of the cell index makes the
+    // compiler recompute them instead of holding 19 pointers live across the two collisions.
+    unsigned un2;
+    asm volatile("mov.u32 %0, %1;" : "=r"(un2) : "r"(un));
     sfor<0, Q>([&](auto I) {
       constexpr int i = decltype(I)::value;
-      Pair<S>::st(f + (unsigned(opp<Q>(i)) * us + un), h0[i], h1[i]);
+      P::st(f + (unsigned(opp<Q>(i)) * us + un2), raw[i]);
     });
   } else {
     const Nbr32 nb0(a, x0, y, z, n0), nb1(a, x0 + 1, y, z, n0 + 1);
@@ -404,10 +425,10 @@ __global__ void __launch_bounds__(BULK_THREADS, (Q == 19 ? 6 : 4)) k_bulk2(const
       constexpr int cx = Lat<Q>::cx(k), cy = Lat<Q>::cy(k), cz = Lat<Q>::cz(k);
       const unsigned pb = unsigned(k) * us;
       if constexpr (cx == 0) {
-        Pair<S>::st(f + nb0.at<0, cy, cz>(pb), h0[k], h1[k]);
+        P::st(f + nb0.at<0, cy, cz>(pb), raw[k]);
       } else {
-        Codec<S>::st(f + nb0.at<cx, cy, cz>(pb), h0[k]);
-        Codec<S>::st(f + nb1.at<cx, cy, cz>(pb), h1[k]);
+        f[nb0.at<cx, cy, cz>(pb)] = P::lo(raw[k]);
+        f[nb1.at<cx, cy, cz>(pb)] = P::hi(raw[k]);
       }
     });
   }
