@@ -94,7 +94,7 @@ struct lbm_ctx {
   unsigned* status_h = nullptr;
   double* red_h = nullptr;
   // adjoint state
-  DevBuf lamA, lamB, dgam, duin;
+  DevBuf lamA, lamB, dgam, duin, plane;
   std::vector<DevBuf> ckpts, ring;
   int adj_T = 0, adj_W = 0, adj_xa = 0, adj_xb = 0, adj_ck = 0;
   double adj_wa = 0, adj_wb = 0;
@@ -103,7 +103,7 @@ struct lbm_ctx {
 
   ~lbm_ctx() {
     DevBuf* all[] = {&lidx, &lsub, &lwall, &lbc, &wst, &f, &type, &mask, &wdist, &gamma, &uin, &lcell, &nsum, &wref, &lxyz, &lcode, &wnrm, &wyw, &ref0, &ref1, &status, &red,
-                     &redout, &stage, &lamA, &lamB, &dgam, &duin};
+                     &redout, &stage, &lamA, &lamB, &dgam, &duin, &plane};
     for (DevBuf* b : all) b->release();
     for (auto& b : ckpts) b.release();
     for (auto& b : ring) b.release();
@@ -895,6 +895,8 @@ int lbm_objective_forward(lbm_ctx* c, int T, int W, int xa, int xb, int ckpt, do
     if (e != cudaSuccess) return fail(e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, "checkpoints: %s", cudaGetErrorString(e));
   }
   CK(cudaMemsetAsync(c->redout.p, 0, sizeof(double), c->stream));
+  const size_t plane_blocks = (2 * (size_t)c->ny * c->nz + 255) / 256;
+  CK(c->plane.ensure(plane_blocks * sizeof(double)));
   cudaEvent_t f0, f1;
   CK(cudaEventCreate(&f0));
   CK(cudaEventCreate(&f1));
@@ -904,7 +906,8 @@ int lbm_objective_forward(lbm_ctx* c, int T, int W, int xa, int xb, int ckpt, do
     launch_step(c);
     if (s + 1 > T - W) {
       const Args b = make_args(c);
-      c->ops->plane_rho(b, c->f.p, int(c->t & 1), xa, xb, static_cast<double*>(c->redout.p), wa, wb, c->stream);
+      c->ops->plane_rho(b, c->f.p, int(c->t & 1), xa, xb, static_cast<double*>(c->redout.p),
+                        static_cast<double*>(c->plane.p), wa, wb, c->stream);
     }
   }
   CK(cudaEventRecord(f1, c->stream));

@@ -125,17 +125,17 @@ struct Impl {
   }
   static void step_oop(const Args& a, const void* fin, void* fout, cudaStream_t s) {
     k_step_oop<Q, S><<<bulk_grid(a), bulk_block(a), 0, s>>>(a, static_cast<const S*>(fin), static_cast<S*>(fout));
-    if (a.n_bc > 0)
-      k_step_oop_bc<Q, S><<<blocks_for(a.n_bc, LIST_THREADS), LIST_THREADS, 0, s>>>(a, static_cast<const S*>(fin),
-                                                                                   static_cast<S*>(fout));
   }
   static void reverse(const Args& a, const AdjArgs& d, cudaStream_t s) {
     k_reverse<Q, S><<<bulk_grid(a), bulk_block(a), 0, s>>>(a, d);
-    if (a.n_bc > 0) k_reverse_bc<Q, S><<<blocks_for(a.n_bc, LIST_THREADS), LIST_THREADS, 0, s>>>(a, d);
   }
-  static void plane_rho(const Args& a, const void* state, int swapped, int xa, int xb, double* acc, double wa, double wb,
-                        cudaStream_t s) {
-    k_plane_rho<Q, S><<<1, 1024, 0, s>>>(a, static_cast<const S*>(state), swapped, xa, xb, acc, wa, wb);
+  // acc += the plane sums; scratch holds one partial per 256 plane cells (2 ny nz / 256 doubles)
+  static void plane_rho(const Args& a, const void* state, int swapped, int xa, int xb, double* acc, double* scratch,
+                        double wa, double wb, cudaStream_t s) {
+    const long long cells = 2LL * a.ny * a.nz;
+    const int nblk = int((cells + 255) / 256);
+    k_plane_rho<Q, S><<<nblk, 256, 0, s>>>(a, static_cast<const S*>(state), swapped, xa, xb, scratch, wa, wb);
+    k_plane_final<<<1, 32, 0, s>>>(scratch, nblk, acc);
   }
   static void seed(const Args& a, void* lam, int xa, int xb, double wa, double wb, cudaStream_t s) {
     k_seed<C><<<blocks_for(a.N, 256), 256, 0, s>>>(a, static_cast<C*>(lam), xa, xb, wa, wb, Q);

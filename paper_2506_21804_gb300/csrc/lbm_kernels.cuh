@@ -475,7 +475,7 @@ __global__ void __launch_bounds__(LIST_THREADS) k_list(const Args a) {
 }
 
 // Out-of-place step for the adjoint's recomputation: natural-layout state fin -> natural-layout fout.
-// The wall model is excluded by the host; INFLOW/OUTFLOW cells go to k_step_oop_bc.
+// The wall model is excluded by the host.
 template <int Q, class S>
 __device__ __forceinline__ void oop_cell(const Args& a, const S* fin, S* fout, int x, int y, int z, long long n, uint8_t t) {
   using C = typename Codec<S>::C;
@@ -498,18 +498,8 @@ __global__ void __launch_bounds__(BULK_THREADS) k_step_oop(const Args a, const S
   if (x >= a.nx || y >= a.ny) return;
   const long long n = x + (long long)y * a.nx + (long long)z * a.nxy;
   const uint8_t t = a.type[n];
-  const int kind = t & T_KIND;
-  if (kind == K_SOLID || kind == K_INFLOW || kind == K_OUTFLOW) return;
+  if ((t & T_KIND) == K_SOLID) return;
   oop_cell<Q, S>(a, fin, fout, x, y, z, n, t);
-}
-
-template <int Q, class S>
-__global__ void __launch_bounds__(LIST_THREADS) k_step_oop_bc(const Args a, const S* __restrict__ fin, S* __restrict__ fout) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= a.n_bc) return;
-  const int k = a.lbc[j];
-  const long long n = a.lcell[k];
-  oop_cell<Q, S>(a, fin, fout, a.lxyz[3 * k], a.lxyz[3 * k + 1], a.lxyz[3 * k + 2], n, a.type[n]);
 }
 
 // ---- state access ------------------------------------------------------------------------------------
@@ -686,38 +676,49 @@ __global__ void k_list_aux(const Args a, const int* nsum, const float* wall_dist
   wyw[k] = wall_dist ? C(wall_dist[n]) : C(0.5);
 }
 
-// Objective plane sums: acc += wa * sum_{x=xa} rho + wb * sum_{x=xb} rho over non-solid cells
-// (one block, fixed summation order).
+// Objective plane sums: partial[b] = wa * sum_{x=xa} rho + wb * sum_{x=xb} rho over the non-solid
+// cells of block b's share of the two planes (256 cells per block); k_plane_final adds the partials
+// to the accumulator in a fixed order.
 template <int Q, class S>
-__global__ void __launch_bounds__(1024) k_plane_rho(const Args a, const S* state, int swapped, int xa, int xb, double* acc,
-                                                    double wa, double wb) {
+__global__ void __launch_bounds__(256) k_plane_rho(const Args a, const S* state, int swapped, int xa, int xb,
+                                                   double* partial, double wa, double wb) {
   using C = typename Codec<S>::C;
   Args b = a;
   b.f = const_cast<S*>(state);
   const long long pl = (long long)a.ny * a.nz;
+  const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   double s = 0.0;
-  for (long long q = threadIdx.x; q < 2 * pl; q += blockDim.x) {
+  if (q < 2 * pl) {
     const int which = q >= pl;
     const long long p = which ? q - pl : q;
     const int y = int(p % a.ny), z = int(p / a.ny);
-    const long long n = (which ? xb : xa) + (long long)y * a.nx + (long long)z * a.nxy;
-    if ((a.type[n] & T_KIND) == K_SOLID) continue;
-    C h[Q];
-    if (swapped) gather<Q, S, LOAD_SLOTS>(b, state, which ? xb : xa, y, z, n, true, h);
-    else gather<Q, S, LOAD_LOCAL>(b, state, which ? xb : xa, y, z, n, false, h);
-    C drho = C(0);
-    sfor<0, Q>([&](auto I) { drho += h[I]; });
-    s += (which ? wb : wa) * (1.0 + double(drho));
+    const int x = which ? xb : xa;
+    const long long n = x + (long long)y * a.nx + (long long)z * a.nxy;
+    if ((a.type[n] & T_KIND) != K_SOLID) {
+      C h[Q];
+      if (swapped) gather<Q, S, LOAD_SLOTS>(b, state, x, y, z, n, true, h);
+      else gather<Q, S, LOAD_LOCAL>(b, state, x, y, z, n, false, h);
+      C drho = C(0);
+      sfor<0, Q>([&](auto I) { drho += h[I]; });
+      s = (which ? wb : wa) * (1.0 + double(drho));
+    }
   }
-  __shared__ double sm[32];
+  __shared__ double sm[8];
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
   if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = s;
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0;
     for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += sm[i];
-    *acc += t;
+    partial[blockIdx.x] = t;
   }
+}
+
+static __global__ void k_plane_final(const double* partial, int nblk, double* acc) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double t = 0;
+  for (int b = 0; b < nblk; ++b) t += partial[b];
+  *acc += t;
 }
 
 // ---- adjoint reverse step ---------------------------------------------------------------------------------
@@ -774,8 +775,8 @@ __device__ __forceinline__ void reverse_cell(const Args& a, const AdjArgs& d, in
   }
 }
 
-// Reverse step over every non-solid cell except INFLOW/OUTFLOW cells (k_reverse_bc handles those,
-// so that their boundary-condition reverse does not diverge the warps of the interior).
+// Reverse step over every cell (inlet/outlet cells included: their extra boundary-condition reverse
+// costs less as a divergent branch than as a separate, latency-bound pass over a sparse plane).
 template <int Q, class S>
 __global__ void __launch_bounds__(BULK_THREADS) k_reverse(const Args a, const AdjArgs d) {
   using C = typename Codec<S>::C;
@@ -791,18 +792,7 @@ __global__ void __launch_bounds__(BULK_THREADS) k_reverse(const Args a, const Ad
     sfor<0, Q>([&](auto I) { lo[(long long)I * a.stride + n] = C(0); });
     return;
   }
-  if (kind == K_INFLOW || kind == K_OUTFLOW) return;
   reverse_cell<Q, S>(a, d, x, y, z, n, t);
-}
-
-// Reverse step of the INFLOW/OUTFLOW entries (Args::lbc).
-template <int Q, class S>
-__global__ void __launch_bounds__(LIST_THREADS) k_reverse_bc(const Args a, const AdjArgs d) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= a.n_bc) return;
-  const int k = a.lbc[j];
-  const long long n = a.lcell[k];
-  reverse_cell<Q, S>(a, d, a.lxyz[3 * k], a.lxyz[3 * k + 1], a.lxyz[3 * k + 2], n, a.type[n]);
 }
 
 // Adjoint seed lambda_T = dJ/dS_T: weight wa on every population of the non-solid cells of plane

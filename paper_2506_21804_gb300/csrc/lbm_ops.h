@@ -31,8 +31,8 @@ struct Ops {
   // adjoint: out-of-place forward from a natural-layout state, reverse step, objective plane sums
   void (*step_oop)(const Args&, const void* fin, void* fout, cudaStream_t);
   void (*reverse)(const Args&, const AdjArgs&, cudaStream_t);
-  void (*plane_rho)(const Args&, const void* state, int swapped, int xa, int xb, double* acc, double wa, double wb,
-                    cudaStream_t);
+  void (*plane_rho)(const Args&, const void* state, int swapped, int xa, int xb, double* acc, double* scratch,
+                    double wa, double wb, cudaStream_t);
   void (*seed)(const Args&, void* lam, int xa, int xb, double wa, double wb, cudaStream_t);
   void (*convert)(const void* in, int in_dtype, void* out, int out_dtype, long long n, cudaStream_t);
 };
