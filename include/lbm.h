@@ -168,7 +168,8 @@ int lbm_set_option(lbm_ctx* ctx, int option, int value);
 int lbm_info(lbm_ctx* ctx, int64_t out[10]);
 /* Integer maps for bit-exact tests: which = 0 type byte per cell (N; bits 0-2 kind, bit 3
  * reference cell, bit 4 a source position is solid or outside, bit 5 boundary list, bit 6 list cell
- * updated by the interior kernel: WALL/reference cells in 32-cell x-groups holding >= 8 list cells);
+ * updated by the interior kernel: INFLOW/OUTFLOW cells, and WALL/reference cells in 32-cell
+ * x-groups holding >= 8 list cells);
  * 1 boundary-list cells; 2 list position of each entry's reference cell (-1 none);
  * 3 integer wall-normal sums v of each entry (3 per entry, sum of W_i c_i over solid neighbours,
  * W_i = 36 w_i for D3Q19 and 216 w_i for D3Q27); 4 source population j and 5 source cell m of each

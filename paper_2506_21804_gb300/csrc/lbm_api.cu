@@ -307,9 +307,10 @@ int build_geometry(lbm_ctx* c) {
   CK(c->wst.ensure(nl * WALL_STATE * c->ops->celem));
   CK(cudaMemsetAsync(c->wst.p, 0, nl * WALL_STATE * c->ops->celem, s));
   {
-    // Inline (fused-mode) choice per 32-cell x-group: WALL and reference cells are updated by the
-    // interior kernel when their group holds at least INLINE_MIN list cells; INFLOW/OUTFLOW cells
-    // and isolated list cells stay with the boundary-list kernel.
+    // Inline (fused-mode) choice: INFLOW/OUTFLOW cells are always updated by the interior kernel
+    // (their extra work is a short reconstruction before the shared collision); WALL and reference
+    // cells when their 32-cell x-group holds at least INLINE_MIN list cells. Isolated WALL and
+    // reference cells stay with the boundary-list kernel.
     constexpr int INLINE_MIN = 8;
     std::vector<long long> cells(c->n_list);
     std::vector<uint8_t> tl(c->N);
@@ -322,11 +323,11 @@ int build_geometry(lbm_ctx* c) {
         const int g1 = std::min(c->nx, g0 + 32);
         int cnt = 0;
         for (int x = g0; x < g1; ++x) cnt += (tl[base + x] & T_LIST) != 0;
-        if (cnt < INLINE_MIN) continue;
         for (int x = g0; x < g1; ++x) {
           uint8_t& t = tl[base + x];
           const int kind = t & T_KIND;
-          if ((t & T_LIST) && kind != K_INFLOW && kind != K_OUTFLOW) t |= T_INLINE;
+          if (!(t & T_LIST)) continue;
+          if (kind == K_INFLOW || kind == K_OUTFLOW || cnt >= INLINE_MIN) t |= T_INLINE;
         }
       }
     }

@@ -264,8 +264,9 @@ __device__ __forceinline__ void collide_any(const Args& a, int kind, uint8_t t, 
 }
 
 // ---- the step kernels ----------------------------------------------------------------------------------
-// WALL or reference cell handled inside the interior kernel (fused mode): its list entry gives the
-// slot codes, the precomputed wall-model state and the reference-buffer position.
+// A list cell updated inside the interior kernel (fused mode): its entry gives the slot codes, the
+// precomputed wall-model state and the reference-buffer position. Inlet/outlet lanes add their
+// boundary reconstruction before the collision; the collision itself is shared with plain lanes.
 template <int Q, class S, bool ODD>
 __device__ __forceinline__ void list_cell_inline(const Args& a, S* f, int x, int y, int z, long long n, uint8_t t) {
   using C = typename Codec<S>::C;
@@ -279,6 +280,7 @@ __device__ __forceinline__ void list_cell_inline(const Args& a, S* f, int x, int
   } else {
     gather<Q, S, LOAD_LOCAL>(a, f, x, y, z, n, false, h);
   }
+  if (kind == K_INFLOW || kind == K_OUTFLOW) apply_bc<Q, C>(a, kind, y, z, h);
   C rho, urx, ury, urz;
   if (kind == K_WALL && a.wm) collide_wall_state<Q, C>(h, a, cptr<C>(a.wst) + (long long)WALL_STATE * k, rho, urx, ury, urz);
   else collide_fluid<Q, C>(h, gamma_at<C>(a, n), a, rho, urx, ury, urz);
@@ -292,11 +294,12 @@ __device__ __forceinline__ void list_cell_inline(const Args& a, S* f, int x, int
 }
 
 // Interior kernel: every FLUID cell off the boundary list, and in fused mode also the list cells
-// flagged T_INLINE (WALL and reference cells in 32-cell x-groups dense in list cells, where the
-// extra path costs little divergence). Threads map to (x, y, z).
-// Occupancy target of the interior kernel (CTAs of 128 threads per SM): D3Q19 10 on even steps
-// (<= 51 registers) and 8 on odd steps (<= 64), D3Q27 8 and 6; the register cap falls on the
-// rarely taken boundary-cell path. The FP64 (reference) form is left unconstrained.
+// flagged T_INLINE (inlet/outlet cells, and WALL and reference cells in 32-cell x-groups dense in
+// list cells, where the extra path costs little divergence). Threads map to (x, y, z).
+//
+// Occupancy target (CTAs of 128 threads per SM): D3Q19 10 on even steps (<= 51 registers) and 8 on
+// odd steps (<= 64), D3Q27 8 and 6; the register cap falls on the rarely taken list-cell path. The
+// FP64 (reference) form is left unconstrained.
 template <int Q, class S, bool ODD> constexpr int bulk_min_blocks() {
   return sizeof(S) == 8 ? 1 : (Q == 19 ? (ODD ? 8 : 10) : (ODD ? 6 : 8));
 }
@@ -316,7 +319,6 @@ __device__ __forceinline__ void bulk_cell(const Args& a, S* f, int x, int y, int
   if (!finite_all<C>(rho, urx, ury, urz)) atomicOr(a.status, ST_NAN);
   scatter<Q, S, ODD ? STORE_SLOTS : STORE_MIRROR>(a, f, x, y, z, n, near, h);
 }
-
 template <int Q, class S, bool ODD>
 __global__ void __launch_bounds__(BULK_THREADS, (bulk_min_blocks<Q, S, ODD>())) k_bulk(const Args a) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -743,21 +745,22 @@ __device__ __forceinline__ void reverse_cell(const Args& a, const AdjArgs& d, in
   gather<Q, S, LOAD_LOCAL>(a, static_cast<const S*>(d.fst), x, y, z, n, false, h);
   C lam[Q], ggam = C(0), gub[3] = {C(0), C(0), C(0)};
   const C gam = gamma_at<C>(a, n);
-  if (kind == K_INFLOW || kind == K_OUTFLOW) {
-    C hb[Q];
-    sfor<0, Q>([&](auto I) { hb[I] = h[I]; });
-    apply_bc<Q, C>(a, kind, y, z, hb);
-    C gh[Q];
-    collide_fluid_vjp<Q, C>(hb, gam, a, mu, gh, ggam);
-    if (kind == K_INFLOW) {
-      const C* ub = cptr<C>(a.uin);
-      const long long pl = (long long)a.ny * a.nz, p = y + (long long)a.ny * z;
-      bc_inlet_vjp<Q, C>(h, ub[p], ub[pl + p], ub[2 * pl + p], gh, lam, gub);
-    } else {
-      bc_outlet_vjp<Q, C>(h, C(a.rho_out), C(a.drho_out), gh, lam);
-    }
+  const bool bc = kind == K_INFLOW || kind == K_OUTFLOW;
+  // boundary reconstruction forward (inlet/outlet lanes only), then the collision reverse for all
+  // lanes together, then the reconstruction reverse (inlet/outlet lanes only)
+  C hb[Q];
+  sfor<0, Q>([&](auto I) { hb[I] = h[I]; });
+  if (bc) apply_bc<Q, C>(a, kind, y, z, hb);
+  C gh[Q];
+  collide_fluid_vjp<Q, C>(hb, gam, a, mu, gh, ggam);
+  if (kind == K_INFLOW) {
+    const C* ub = cptr<C>(a.uin);
+    const long long pl = (long long)a.ny * a.nz, p = y + (long long)a.ny * z;
+    bc_inlet_vjp<Q, C>(h, ub[p], ub[pl + p], ub[2 * pl + p], gh, lam, gub);
+  } else if (kind == K_OUTFLOW) {
+    bc_outlet_vjp<Q, C>(h, C(a.rho_out), C(a.drho_out), gh, lam);
   } else {
-    collide_fluid_vjp<Q, C>(h, gam, a, mu, lam, ggam);
+    sfor<0, Q>([&](auto I) { lam[I] = gh[I]; });
   }
   if (d.add_dj) {
     const C w = C(x == d.xa ? d.wa : 0.0) + C(x == d.xb ? d.wb : 0.0);
