@@ -151,8 +151,11 @@ struct Oracle {
   bool wm = false;
   double kappa = 0.41, E = 9.52;
   int storage = 0;            // 0 exact, 1 fp32, 2 fp16, 3 bf16 rounding of stored f - w
+  int model = 0;              // collision: 0 BGK, 1 hybrid recursive regularised (HRR)
+  double sigma = 1.0;         // HRR hybridisation factor (1: local stress only)
   std::vector<double> F, P, Fn;
   std::vector<double> uref_prev, uref_cur;
+  std::vector<double> uvel_prev, uvel_cur;  // 3N component-major: velocity field of the last step (HRR)
   long t = 0;
   // adjoint bookkeeping
   std::vector<std::vector<double>> hist;  // stored pre-collision states S_0..S_{T-1}
@@ -312,6 +315,117 @@ T q_contract(const Lat& L, int i, const T A[3][3]) {
   return s;
 }
 
+// ---- Third-order Hermite terms of the HRR collision (Sec. 2.2) ---------------------------------
+// Third-order Hermite polynomial H_abc(c) = c_a c_b c_c - cs^2 (c_a d_bc + c_b d_ac + c_c d_ab).
+// With unit speeds H_aaa = c_a (c_a^2 - 1) vanishes on both velocity sets, which leaves the six
+// mixed polynomials H_aab (a != b) and H_xyz; H_xyz vanishes on D3Q19 (no speed has three non-zero
+// components) and is dropped there. Reading of the third-order terms of the equilibrium and of
+// f^(1): a symmetric rank-3 tensor a enters as the weighted combination of the remaining
+// polynomials whose lattice moments sum_i (.) H_k(c_i) equal the components a_k, i.e.
+//   t_i = w_i sum_{k,l} H_k(c_i) (G^{-1})_{kl} a_l,   G_{kl} = sum_i w_i H_k(c_i) H_l(c_i).
+// Where G is diagonal (D3Q27: G = 2 cs^6 for the mixed, cs^6 for H_xyz) this is the Hermite term
+// H^(3) : a / (6 cs^6) of the expansion; on D3Q19 the mixed polynomials are not orthogonal and the
+// Gram inverse gives the projection onto what the velocity set carries.
+struct Third {
+  int n = 0;
+  int idx[7][3] = {};
+  double P[7][27] = {};
+  double Ginv[7][7] = {};
+};
+
+double hermite3(const Lat& L, int i, int a, int b, int c) {
+  const int* v = L.c[i];
+  return double(v[a] * v[b] * v[c]) - CS2 * (double(v[a]) * (b == c) + double(v[b]) * (a == c) + double(v[c]) * (a == b));
+}
+
+Third make_third(const Lat& L) {
+  Third t;
+  const int cand[7][3] = {{0, 0, 1}, {0, 0, 2}, {1, 1, 0}, {1, 1, 2}, {2, 2, 0}, {2, 2, 1}, {0, 1, 2}};
+  for (int k = 0; k < 7; ++k) {
+    double nrm = 0.0;
+    double vals[27];
+    for (int i = 0; i < L.Q; ++i) {
+      vals[i] = hermite3(L, i, cand[k][0], cand[k][1], cand[k][2]);
+      nrm += vals[i] * vals[i];
+    }
+    if (nrm == 0.0) continue;
+    for (int a = 0; a < 3; ++a) t.idx[t.n][a] = cand[k][a];
+    for (int i = 0; i < L.Q; ++i) t.P[t.n][i] = vals[i];
+    ++t.n;
+  }
+  // Gram matrix and its inverse by Gauss-Jordan elimination with partial pivoting
+  double G[7][14] = {};
+  for (int k = 0; k < t.n; ++k) {
+    for (int l = 0; l < t.n; ++l) {
+      double s = 0.0;
+      for (int i = 0; i < L.Q; ++i) s += L.w[i] * t.P[k][i] * t.P[l][i];
+      G[k][l] = s;
+    }
+    G[k][t.n + k] = 1.0;
+  }
+  for (int col = 0; col < t.n; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < t.n; ++r)
+      if (std::fabs(G[r][col]) > std::fabs(G[piv][col])) piv = r;
+    for (int m = 0; m < 2 * t.n; ++m) std::swap(G[col][m], G[piv][m]);
+    const double d = G[col][col];
+    for (int m = 0; m < 2 * t.n; ++m) G[col][m] /= d;
+    for (int r = 0; r < t.n; ++r) {
+      if (r == col) continue;
+      const double fct = G[r][col];
+      for (int m = 0; m < 2 * t.n; ++m) G[r][m] -= fct * G[col][m];
+    }
+  }
+  for (int k = 0; k < t.n; ++k)
+    for (int l = 0; l < t.n; ++l) t.Ginv[k][l] = G[k][t.n + l];
+  return t;
+}
+
+const Third& third_of(const Lat& L) {
+  static const Third t19 = make_third(make_lattice(19));
+  static const Third t27 = make_third(make_lattice(27));
+  return L.Q == 19 ? t19 : t27;
+}
+
+// w_i-weighted third-order term of population i for the symmetric tensor a (a[a][b][c]).
+template <class T>
+T third_term(const Lat& L, int i, const T a[3][3][3]) {
+  const Third& t = third_of(L);
+  T s = 0.0;
+  for (int k = 0; k < t.n; ++k)
+    for (int l = 0; l < t.n; ++l) s = s + (t.P[k][i] * t.Ginv[k][l]) * a[t.idx[l][0]][t.idx[l][1]][t.idx[l][2]];
+  return L.w[i] * s;
+}
+
+// Third-order equilibrium of Sec. 2.2: the second-order one plus the third Hermite term with
+// a_0^(3) = rho u u u.
+template <class T>
+T feq3(const Lat& L, int i, T rho, const T u[3]) {
+  T a3[3][3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b)
+      for (int c = 0; c < 3; ++c) a3[a][b][c] = rho * u[a] * u[b] * u[c];
+  return feq(L, i, rho, u) + third_term(L, i, a3);
+}
+
+// Hybrid recursive regularised update (Eq. hlbm with the Hermite expansion of f^(1), Sec. 2.2):
+//   f*_i = f^eq_i(rho, ueq) + (1 - 1/tau) f^(1)_i,
+//   f^(1)_i = w_i Q_i : A2 / (2 cs^4) + third-order term of A3,
+//   A3_abc = uh_a A2_bc + uh_b A2_ac + uh_c A2_ab (recursive third-order coefficient),
+// with A2 the (hybridised) second-order non-equilibrium coefficient and uh the homogenised
+// velocity around which f^(1) is expanded.
+template <class T>
+void collide_hrr(const Lat& L, T rho, const T ueq[3], const T uh[3], T tau, const T A2[3][3], T fs[27]) {
+  T A3[3][3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b)
+      for (int c = 0; c < 3; ++c) A3[a][b][c] = uh[a] * A2[b][c] + uh[b] * A2[a][c] + uh[c] * A2[a][b];
+  for (int i = 0; i < L.Q; ++i) {
+    T f1 = L.w[i] * q_contract(L, i, A2) / (2.0 * CS2 * CS2) + third_term(L, i, A3);
+    fs[i] = feq3(L, i, rho, ueq) + (1.0 - 1.0 / tau) * f1;
+  }
+}
+
 // Regularised boundary reconstruction (Latt et al.): given rho, u on the boundary and the known
 // populations (unknown ones are those for which known[i] is false), set f^neq of each unknown
 // population to that of its opposite, form Pi^neq = sum_i c_i c_i f^neq_i and replace every
@@ -458,6 +572,38 @@ WallState wall_state(const Oracle& o, long n, const double* uref) {
   return ws;
 }
 
+// Finite-difference rate of strain S^FD (Sec. 2.2, non-local part of the hybrid f^(1)) at cell n
+// from the velocity field of the previous step. Reading: a neighbour x +- e_b is usable when it lies
+// inside the domain (after periodic wrap) and is not SOLID; the derivative d u_a / d x_b is the
+// central difference when both are usable, the one-sided difference with the cell itself when one
+// is, and zero when neither is. S = (grad u + grad u^T) / 2.
+void strain_fd(const Oracle& o, long n, double S[3][3]) {
+  int x, y, z;
+  coords(o, n, x, y, z);
+  const int here[3] = {x, y, z};
+  double g[3][3];
+  for (int b = 0; b < 3; ++b) {
+    long nb[2] = {-1, -1};
+    for (int s = 0; s < 2; ++s) {
+      int p[3] = {here[0], here[1], here[2]};
+      p[b] += s == 0 ? 1 : -1;
+      if (resolve(o, p) != 0) continue;
+      long m = idx(o, p[0], p[1], p[2]);
+      if (o.kind[m] == K_SOLID) continue;
+      nb[s] = m;
+    }
+    for (int a = 0; a < 3; ++a) {
+      const double* u = o.uvel_prev.data() + long(a) * o.N;
+      if (nb[0] >= 0 && nb[1] >= 0) g[a][b] = 0.5 * (u[nb[0]] - u[nb[1]]);
+      else if (nb[0] >= 0) g[a][b] = u[nb[0]] - u[n];
+      else if (nb[1] >= 0) g[a][b] = u[n] - u[nb[1]];
+      else g[a][b] = 0.0;
+    }
+  }
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) S[a][b] = 0.5 * (g[a][b] + g[b][a]);
+}
+
 // One cell's update. f holds the gathered pre-collision populations (boundary substitutions done);
 // on return fs holds the post-collision populations, urep the reported velocity
 // u = j/rho + F/(2 rho) and rho_out the density.
@@ -492,6 +638,17 @@ void collide_cell(const Oracle& o, long n, T f[27], T gamma, const T ub[3], cons
     double tau = (nu0 + nut) / CS2 + 0.5;
     T uh[3];
     for (int a = 0; a < 3; ++a) uh[a] = ws.uB[a] + o.force[a] / rho;
+    if (o.model == 1) {
+      // HRR form: third-order equilibrium at u^B, f^(1) from A2 = -2 rho cs^2 tau S expanded
+      // recursively around u^B.
+      T A2[3][3], ub3[3];
+      for (int a = 0; a < 3; ++a) {
+        ub3[a] = T(ws.uB[a]);
+        for (int b = 0; b < 3; ++b) A2[a][b] = -2.0 * CS2 * tau * rho * S[a][b];
+      }
+      collide_hrr(L, rho, uh, ub3, T(tau), A2, fs);
+      return;
+    }
     for (int i = 0; i < L.Q; ++i) {
       T f1 = -(L.w[i] * rho * tau / CS2) * q_contract(L, i, S);
       fs[i] = feq(L, i, rho, uh) + (1.0 - 1.0 / tau) * f1;
@@ -512,6 +669,20 @@ void collide_cell(const Oracle& o, long n, T f[27], T gamma, const T ub[3], cons
   // through the exact-difference shift u_hat += F/rho.
   T uh[3];
   for (int a = 0; a < 3; ++a) uh[a] = gamma * u[a] + o.force[a] / rho;
+  if (o.model == 1) {
+    // HRR: A2 = sigma Pi^neq + (1 - sigma) Pi^FD with Pi^FD = -2 rho cs^2 tau S^FD (the
+    // Chapman-Enskog stress of the finite-difference strain; reading of the sign and of the missing
+    // weight in the printed f^(1,FD)), expanded around the homogenised velocity gamma u.
+    double Sfd[3][3];
+    strain_fd(o, n, Sfd);
+    T A2[3][3], uhom[3];
+    for (int a = 0; a < 3; ++a) {
+      uhom[a] = gamma * u[a];
+      for (int b = 0; b < 3; ++b) A2[a][b] = o.sigma * Pi[a][b] + (1.0 - o.sigma) * (-2.0 * CS2) * tau * rho * Sfd[a][b];
+    }
+    collide_hrr(L, rho, uh, uhom, tau, A2, fs);
+    return;
+  }
   for (int i = 0; i < L.Q; ++i) fs[i] = feq(L, i, rho, uh) + (1.0 - 1.0 / tau) * (f[i] - fe[i]);
 }
 
@@ -570,6 +741,8 @@ void init_refs(Oracle& o) {
     if (o.isref[n])
       for (int a = 0; a < 3; ++a) o.uref_prev[3 * n + a] = u[a * o.N + n];
   o.uref_cur = o.uref_prev;
+  o.uvel_prev = u;
+  o.uvel_cur = u;
 }
 
 // One time step: collide every non-solid cell of F into P, record the reference velocities, then
@@ -589,6 +762,7 @@ void step_once(Oracle& o) {
     for (int i = 0; i < L.Q; ++i) o.P[long(i) * o.N + n] = fs[i];
     if (o.isref[n])
       for (int a = 0; a < 3; ++a) o.uref_cur[3 * n + a] = urep[a];
+    for (int a = 0; a < 3; ++a) o.uvel_cur[long(a) * o.N + n] = urep[a];
   }
 #pragma omp parallel for schedule(static)
   for (long n = 0; n < o.N; ++n) {
@@ -602,6 +776,7 @@ void step_once(Oracle& o) {
   std::swap(o.F, o.Fn);
   store_round(o, o.F);
   o.uref_prev = o.uref_cur;
+  o.uvel_prev = o.uvel_cur;
   ++o.t;
 }
 
@@ -778,6 +953,67 @@ void orc_set_wall_model(void* h, int on, double kappa, double E) {
   o.wm = on != 0; o.kappa = kappa; o.E = E;
 }
 void orc_set_storage(void* h, int mode) { static_cast<Oracle*>(h)->storage = mode; }
+
+// Collision model: 0 BGK, 1 hybrid recursive regularised with hybridisation factor sigma in [0, 1].
+int orc_set_collision(void* h, int model, double sigma) {
+  Oracle& o = *static_cast<Oracle*>(h);
+  if ((model != 0 && model != 1) || !(sigma >= 0.0 && sigma <= 1.0)) { g_err = "bad collision model"; return 1; }
+  o.model = model;
+  o.sigma = sigma;
+  return 0;
+}
+int orc_get_collision(void* h, double* sigma) {
+  Oracle& o = *static_cast<Oracle*>(h);
+  *sigma = o.sigma;
+  return o.model;
+}
+
+// Third-order term of every population for the symmetric tensor a (27 values, a[(a*3+b)*3+c]).
+int orc_third_order(int q, const double* a27, double* out) {
+  if (q != 19 && q != 27) return 1;
+  Lat L = make_lattice(q);
+  double a[3][3][3];
+  for (int i = 0; i < 27; ++i) a[i / 9][(i / 3) % 3][i % 3] = a27[i];
+  for (int i = 0; i < q; ++i) out[i] = third_term(L, i, a);
+  return 0;
+}
+// Third-order equilibrium of every population.
+int orc_feq3(int q, double rho, const double* u, double* out) {
+  if (q != 19 && q != 27) return 1;
+  Lat L = make_lattice(q);
+  for (int i = 0; i < q; ++i) out[i] = feq3(L, i, rho, u);
+  return 0;
+}
+// One HRR update of a cell from its density, equilibrium velocity ueq, expansion velocity uh,
+// relaxation time and second-order coefficient A2 (9 values, row-major).
+int orc_collide_hrr(int q, double rho, const double* ueq, const double* uh, double tau, const double* A2, double* out) {
+  if (q != 19 && q != 27) return 1;
+  Lat L = make_lattice(q);
+  double A[3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) A[a][b] = A2[3 * a + b];
+  collide_hrr(L, rho, ueq, uh, tau, A, out);
+  return 0;
+}
+// Finite-difference strain of cell n from the stored velocity field (9 values, row-major).
+void orc_strain_fd(void* h, long long n, double* S9) {
+  Oracle& o = *static_cast<Oracle*>(h);
+  double S[3][3];
+  strain_fd(o, long(n), S);
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) S9[3 * a + b] = S[a][b];
+}
+// Velocity field of the last step (3N, component-major) as the HRR strain reads it; set_velocity_field
+// replaces it (tests of the finite differences).
+void orc_get_velocity_field(void* h, double* u) {
+  Oracle& o = *static_cast<Oracle*>(h);
+  std::memcpy(u, o.uvel_prev.data(), sizeof(double) * 3 * o.N);
+}
+void orc_set_velocity_field(void* h, const double* u) {
+  Oracle& o = *static_cast<Oracle*>(h);
+  o.uvel_prev.assign(u, u + 3 * o.N);
+  o.uvel_cur = o.uvel_prev;
+}
 
 // f_i = f^eq_i(rho, u); rho (N), u (3N, component-major). Then the reference buffer is filled with
 // the reported velocity of this state.
@@ -971,6 +1207,7 @@ void orc_vjp_step(void* h, const double* w, double* out_f, double* out_g, double
 int orc_objective_run(void* h, int T, int W, int xa, int xb, double* J) {
   Oracle& o = *static_cast<Oracle*>(h);
   if (T < 1 || W < 1 || W > T || xa < 0 || xa >= o.nx || xb < 0 || xb >= o.nx) { g_err = "bad objective args"; return 1; }
+  if (o.model != 0) { g_err = "the adjoint is defined for the BGK collision only"; return 1; }
   const Lat& L = o.L;
   o.dJdS_w.assign(o.N, 0.0);
   long na = 0, nb = 0;

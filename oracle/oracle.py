@@ -43,6 +43,14 @@ def lib():
             "orc_set_porosity": (None, [_p, _p]),
             "orc_set_wall_model": (None, [_p, _i, _d, _d]),
             "orc_set_storage": (None, [_p, _i]),
+            "orc_set_collision": (_i, [_p, _i, _d]),
+            "orc_get_collision": (_i, [_p, _p]),
+            "orc_third_order": (_i, [_i, _p, _p]),
+            "orc_feq3": (_i, [_i, _d, _p, _p]),
+            "orc_collide_hrr": (_i, [_i, _d, _p, _p, _d, _p, _p]),
+            "orc_strain_fd": (None, [_p, ctypes.c_longlong, _p]),
+            "orc_get_velocity_field": (None, [_p, _p]),
+            "orc_set_velocity_field": (None, [_p, _p]),
             "orc_init_equilibrium": (None, [_p, _p, _p]),
             "orc_set_populations": (None, [_p, _p]),
             "orc_get_populations": (None, [_p, _p]),
@@ -97,6 +105,35 @@ def lattice(q):
     if lib().orc_lattice(q, _ptr(c), _ptr(w), _ptr(opp), _ptr(W), ctypes.byref(den)):
         raise ValueError("lattice must be 19 or 27")
     return c, w, opp, W, den.value
+
+
+def third_order(q, a):
+    """Third-order Hermite term of every population for the symmetric 3x3x3 tensor a."""
+    a = _f64(np.asarray(a).reshape(27))
+    out = np.zeros(q)
+    if lib().orc_third_order(q, _ptr(a), _ptr(out)):
+        raise ValueError("lattice must be 19 or 27")
+    return out
+
+
+def feq3(q, rho, u):
+    """Third-order equilibrium f^eq_i(rho, u)."""
+    uu = _f64(np.asarray(u).reshape(3))
+    out = np.zeros(q)
+    if lib().orc_feq3(q, float(rho), _ptr(uu), _ptr(out)):
+        raise ValueError("lattice must be 19 or 27")
+    return out
+
+
+def collide_hrr(q, rho, ueq, uh, tau, A2):
+    """One HRR update from (rho, equilibrium velocity, expansion velocity, tau, A2)."""
+    ue = _f64(np.asarray(ueq).reshape(3))
+    uh = _f64(np.asarray(uh).reshape(3))
+    A = _f64(np.asarray(A2).reshape(9))
+    out = np.zeros(q)
+    if lib().orc_collide_hrr(q, float(rho), _ptr(ue), _ptr(uh), float(tau), _ptr(A), _ptr(out)):
+        raise ValueError("lattice must be 19 or 27")
+    return out
 
 
 def set_threads(n):
@@ -213,6 +250,32 @@ class Oracle:
     def set_storage(self, mode):
         lib().orc_set_storage(self.h, int(mode))
 
+    def set_collision(self, model, sigma=1.0):
+        """model 0: BGK; 1: hybrid recursive regularised with hybridisation factor sigma."""
+        self._chk(lib().orc_set_collision(self.h, int(model), float(sigma)))
+
+    def collision(self):
+        s = np.zeros(1)
+        return lib().orc_get_collision(self.h, _ptr(s)), s[0]
+
+    def strain_fd(self, n):
+        S = np.zeros(9)
+        lib().orc_strain_fd(self.h, int(n), _ptr(S))
+        return S.reshape(3, 3)
+
+    def velocity_field(self):
+        u = np.zeros(3 * self.N)
+        lib().orc_get_velocity_field(self.h, _ptr(u))
+        return u.reshape(3, self.N)
+
+    def set_velocity_field(self, u):
+        u = _f64(np.asarray(u).reshape(-1))
+        lib().orc_set_velocity_field(self.h, _ptr(u))
+
+    def _bgk_only(self):
+        if self.collision()[0] != 0:
+            raise RuntimeError("the adjoint is defined for the BGK collision only")
+
     def init_equilibrium(self, rho, u):
         r = _f64(np.asarray(rho).reshape(-1))
         uu = _f64(np.asarray(u).reshape(-1))
@@ -278,6 +341,7 @@ class Oracle:
         return uB, d[0]
 
     def jvp_step(self, vf, vg=None, vu=None):
+        self._bgk_only()
         vf = _f64(np.asarray(vf).reshape(-1))
         vg = _f64(None if vg is None else np.asarray(vg).reshape(-1))
         vu = _f64(None if vu is None else np.asarray(vu).reshape(-1))
@@ -286,6 +350,7 @@ class Oracle:
         return out.reshape(self.q, self.N)
 
     def vjp_step(self, w):
+        self._bgk_only()
         w = _f64(np.asarray(w).reshape(-1))
         of = np.zeros(self.q * self.N)
         og = np.zeros(self.N)

@@ -72,6 +72,8 @@ class Workload:
     E: float = 9.52
     rho0: Optional[np.ndarray] = None      # (N,)
     u0: Optional[np.ndarray] = None        # (3, N)
+    model: int = 0                         # collision: 0 BGK, 1 hybrid recursive regularised
+    sigma: float = 1.0                     # hybridisation factor of the HRR collision
     meta: dict = field(default_factory=dict)
 
     @property

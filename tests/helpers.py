@@ -25,6 +25,8 @@ def oracle_from(w, storage=0, cast32=False):
         o.set_porosity(_arr(w.gamma, cast32))
     o.set_wall_model(w.wall_model, w.kappa, w.E)
     o.set_storage(storage)
+    if getattr(w, "model", 0):
+        o.set_collision(w.model, w.sigma)
     o.init_equilibrium(_arr(w.rho0, cast32), _arr(w.u0, cast32))
     return o
 
