@@ -71,9 +71,9 @@ __device__ __forceinline__ void collide_fluid_vjp(const C* h, C gamma, const Arg
   sums<Q, C>(h, drho, jx, jy, jz);
   const C rho = C(1) + drho, ir = C(1) / rho;
   const C ux = jx * ir, uy = jy * ir, uz = jz * ir;
-  C tau = C(a.tau0);
+  C tau = a.tau0.get<C>();
   C pxx = 0, pyy = 0, pzz = 0, pxy = 0, pxz = 0, pyz = 0, pn = 0, sD = 0;
-  const bool smag = a.smag > 0.0;
+  const bool smag = a.use_smag != 0;
   if (smag) {
     C sxx = 0, syy = 0, szz = 0, sxy = 0, sxz = 0, syz = 0;
     sfor<0, Q>([&](auto I) {
@@ -89,12 +89,12 @@ __device__ __forceinline__ void collide_fluid_vjp(const C* h, C gamma, const Arg
     pxx = sxx - d3 - rho * ux * ux; pyy = syy - d3 - rho * uy * uy; pzz = szz - d3 - rho * uz * uz;
     pxy = sxy - rho * ux * uy; pxz = sxz - rho * ux * uz; pyz = syz - rho * uy * uz;
     pn = sqrt(pxx * pxx + pyy * pyy + pzz * pzz + C(2) * (pxy * pxy + pxz * pxz + pyz * pyz));
-    const C t0 = C(a.tau0);
-    sD = sqrt(t0 * t0 + C(a.smag) * pn * ir);
+    const C t0 = a.tau0.get<C>();
+    sD = sqrt(t0 * t0 + a.smag.get<C>() * pn * ir);
     tau = C(0.5) * (t0 + sD);
   }
   const C k = C(1) - C(1) / tau;
-  const C vx = gamma * ux + C(a.fx) * ir, vy = gamma * uy + C(a.fy) * ir, vz = gamma * uz + C(a.fz) * ir;
+  const C vx = gamma * ux + a.fx.get<C>() * ir, vy = gamma * uy + a.fy.get<C>() * ir, vz = gamma * uz + a.fz.get<C>() * ir;
 
   const WMoments<Q, C> m = wmoments<Q, C>(mu);
   C smh = C(0);
@@ -108,12 +108,12 @@ __device__ __forceinline__ void collide_fluid_vjp(const C* h, C gamma, const Arg
   // v = gamma u + F / rho
   gux += gamma * gvx; guy += gamma * gvy; guz += gamma * gvz;
   ggam += ux * gvx + uy * gvy + uz * gvz;
-  grho -= (C(a.fx) * gvx + C(a.fy) * gvy + C(a.fz) * gvz) * ir * ir;
+  grho -= (a.fx.get<C>() * gvx + a.fy.get<C>() * gvy + a.fz.get<C>() * gvz) * ir * ir;
   C gjx = 0, gjy = 0, gjz = 0;
   C gsxx = 0, gsyy = 0, gszz = 0, gsxy = 0, gsxz = 0, gsyz = 0;
   if (smag) {
     const C gtau = G / (tau * tau);
-    const C Ks = C(a.smag);
+    const C Ks = a.smag.get<C>();
     const C gpn = gtau * Ks / (C(4) * sD) * ir;
     grho -= gtau * Ks * pn / (C(4) * sD) * ir * ir;
     if (pn > C(0)) {

@@ -147,6 +147,7 @@ Args make_args(const lbm_ctx* c) {
   a.tau0 = c->tau0;
   a.nu0 = (c->tau0 - 0.5) / 3.0;
   a.smag = 18.0 * std::sqrt(2.0) * c->cs * c->cs;
+  a.use_smag = a.smag.d > 0.0;
   a.cs2smag = c->cs * c->cs;
   a.fx = c->force[0]; a.fy = c->force[1]; a.fz = c->force[2];
   a.status = static_cast<unsigned*>(c->status.p);

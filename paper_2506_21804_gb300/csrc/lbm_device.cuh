@@ -122,6 +122,23 @@ template <> struct Codec<__nv_bfloat16> {
 };
 
 // ---- kernel arguments (plain data, copied by value into the launch) ---------------------------------
+// A scalar parameter in both precisions, rounded to float once on the host: FP32 kernels read the
+// float copy, so no double-to-float conversion runs per thread (the FP64 pipe is narrow).
+struct Param {
+  double d;
+  float f;
+  template <class C>
+  __host__ __device__ __forceinline__ C get() const {
+    if constexpr (std::is_same<C, float>::value) return f;
+    else return C(d);
+  }
+  __host__ Param& operator=(double v) {
+    d = v;
+    f = float(v);
+    return *this;
+  }
+};
+
 struct Args {
   void* f;                 // population deviations, population p of cell m at f + p*stride + m
   long long stride;        // elements between population arrays
@@ -130,11 +147,12 @@ struct Args {
   int nx, ny, nz;
   long long nxy, N;
   int face[6];
-  double tau0;             // molecular relaxation time
-  double nu0;              // molecular viscosity (tau0 - 1/2)/3, formed in double precision
-  double smag;             // 18 sqrt(2) C_S^2
-  double cs2smag;          // C_S^2
-  double fx, fy, fz;       // body force
+  Param tau0;              // molecular relaxation time
+  Param nu0;               // molecular viscosity (tau0 - 1/2)/3, formed in double precision
+  Param smag;              // 18 sqrt(2) C_S^2
+  int use_smag;            // smag > 0
+  Param cs2smag;           // C_S^2
+  Param fx, fy, fz;        // body force
   unsigned* status;        // sticky device status bits
   // boundary list
   const long long* lcell;  // cell index per entry
@@ -147,8 +165,8 @@ struct Args {
   const void* ref_rd;      // C[3] per entry, reference velocities of the previous step
   void* ref_wr;            // C[3] per entry, written by reference cells this step
   const void* uin;         // C[3][ny*nz] inlet velocity
-  double rho_out;
-  double drho_out;         // rho_out - 1, formed in double precision
+  Param rho_out;
+  Param drho_out;          // rho_out - 1, formed in double precision
   int wm;                  // wall model on
   int fuse;                // 1: list cells flagged T_INLINE are updated by the interior kernel; the
                            //    boundary-list kernel then runs over the other entries only
@@ -163,7 +181,7 @@ struct Args {
   int kernel;              // interior kernel: 0 plain, 2 staged (bulk copies into shared memory) where the shape allows
   int idx32;               // 1: every population index q*stride fits in 32 bits (32-bit index arithmetic)
   int debug_stall;         // 1: the staged kernel also waits on a barrier nobody completes (tests the bounded wait)
-  double kappa, E;
+  Param kappa, E;
 };
 
 // ---- AA-pattern slot map ------------------------------------------------------------------------------
@@ -296,18 +314,18 @@ __device__ __forceinline__ void collide_fluid(C* h, C gamma, const Args& a, C& r
   const C rho = C(1) + drho, ir = rcp(rho);
   const C ux = jx * ir, uy = jy * ir, uz = jz * ir;
   const C usq = ux * ux + uy * uy + uz * uz;
-  C tau = C(a.tau0);
-  if (a.smag > 0.0) {
+  C tau = a.tau0.get<C>();
+  if (a.use_smag != 0) {
     // Pi^neq = sum c c h - drho/3 I - rho u u (second moment of the 2nd-order equilibrium).
     const C d3 = drho * C(1.0 / 3.0);
     const C pxx = sxx - d3 - rho * ux * ux, pyy = syy - d3 - rho * uy * uy, pzz = szz - d3 - rho * uz * uz;
     const C pxy = sxy - rho * ux * uy, pxz = sxz - rho * ux * uz, pyz = syz - rho * uy * uz;
     const C pn = sqrt(pxx * pxx + pyy * pyy + pzz * pzz + C(2) * (pxy * pxy + pxz * pxz + pyz * pyz));
-    const C t0 = C(a.tau0);
-    tau = C(0.5) * (t0 + sqrt(t0 * t0 + C(a.smag) * pn * ir));
+    const C t0 = a.tau0.get<C>();
+    tau = C(0.5) * (t0 + sqrt(t0 * t0 + a.smag.get<C>() * pn * ir));
   }
   const C k = C(1) - rcp(tau);
-  const C vx = gamma * ux + C(a.fx) * ir, vy = gamma * uy + C(a.fy) * ir, vz = gamma * uz + C(a.fz) * ir;
+  const C vx = gamma * ux + a.fx.get<C>() * ir, vy = gamma * uy + a.fy.get<C>() * ir, vz = gamma * uz + a.fz.get<C>() * ir;
   const C vsq = vx * vx + vy * vy + vz * vz;
   const C base = (C(1) - k) * drho - C(1.5) * rho * (vsq - k * usq);
   const C r45 = C(4.5) * rho, r3 = C(3) * rho;
@@ -322,9 +340,109 @@ __device__ __forceinline__ void collide_fluid(C* h, C gamma, const Args& a, C& r
   });
   rho_o = rho;
   const C hf = C(0.5) * ir;
-  urx = ux + C(a.fx) * hf;
-  ury = uy + C(a.fy) * hf;
-  urz = uz + C(a.fz) * hf;
+  urx = ux + a.fx.get<C>() * hf;
+  ury = uy + a.fy.get<C>() * hf;
+  urz = uz + a.fz.get<C>() * hf;
+}
+
+// ---- the same collision on two cells at once with packed FP32 instructions -------------------------------
+// Lane x of every float2 belongs to one cell, lane y to the other. The packed add, multiply and fused
+// multiply-add round each lane exactly as their scalar forms, so this is the FP32 collision above
+// with half the arithmetic instructions; reciprocals and square roots run per lane.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 bc2(float s) { return make_float2(s, s); }
+__device__ __forceinline__ float2 rcp2(float2 a) { return make_float2(rcp(a.x), rcp(a.y)); }
+__device__ __forceinline__ float2 sqrt2(float2 a) { return make_float2(sqrtf(a.x), sqrtf(a.y)); }
+__device__ __forceinline__ float2 abs2(float2 a) { return make_float2(fabsf(a.x), fabsf(a.y)); }
+// acc + S v for a compile-time sign S = +-1
+template <int S> __device__ __forceinline__ float2 acc2(float2 acc, float2 v) {
+  if constexpr (S > 0) return add2(acc, v);
+  else return sub2(acc, v);
+}
+// sigma_i (c_i . v) with sigma_i the sign of the first non-zero component of c_i
+template <int Q, int I> __device__ __forceinline__ float2 cdot2(float2 x, float2 y, float2 z) {
+  constexpr int cx = Lat<Q>::cx(I), cy = Lat<Q>::cy(I), cz = Lat<Q>::cz(I);
+  constexpr int sg = cx != 0 ? cx : (cy != 0 ? cy : cz);
+  constexpr int ax = sg * cx, ay = sg * cy, az = sg * cz;
+  if constexpr (ax != 0) {
+    float2 r = x;
+    if constexpr (ay != 0) r = acc2<ay>(r, y);
+    if constexpr (az != 0) r = acc2<az>(r, z);
+    return r;
+  } else if constexpr (ay != 0) {
+    float2 r = y;
+    if constexpr (az != 0) r = acc2<az>(r, z);
+    return r;
+  } else {
+    return z;
+  }
+}
+template <int Q, int I> __host__ __device__ constexpr int csign() {
+  return Lat<Q>::cx(I) != 0 ? Lat<Q>::cx(I) : (Lat<Q>::cy(I) != 0 ? Lat<Q>::cy(I) : Lat<Q>::cz(I));
+}
+
+// Returns false when either cell's density or velocity is not finite.
+template <int Q>
+__device__ __forceinline__ bool collide_fluid_x2(float2* h, float2 gamma, const Args& a) {
+  constexpr int H = Lat<Q>::H;
+  const float2 z2 = bc2(0.f);
+  float2 drho = h[0], jx = z2, jy = z2, jz = z2;
+  float2 sxx = z2, syy = z2, szz = z2, sxy = z2, sxz = z2, syz = z2;
+  sfor<1, H + 1>([&](auto I) {
+    constexpr int i = decltype(I)::value, cx = Lat<Q>::cx(i), cy = Lat<Q>::cy(i), cz = Lat<Q>::cz(i);
+    const float2 sp = add2(h[i], h[i + H]), dp = sub2(h[i], h[i + H]);
+    drho = add2(drho, sp);
+    if constexpr (cx != 0) { jx = acc2<cx>(jx, dp); sxx = add2(sxx, sp); }
+    if constexpr (cy != 0) { jy = acc2<cy>(jy, dp); syy = add2(syy, sp); }
+    if constexpr (cz != 0) { jz = acc2<cz>(jz, dp); szz = add2(szz, sp); }
+    if constexpr (cx * cy != 0) sxy = acc2<cx * cy>(sxy, sp);
+    if constexpr (cx * cz != 0) sxz = acc2<cx * cz>(sxz, sp);
+    if constexpr (cy * cz != 0) syz = acc2<cy * cz>(syz, sp);
+  });
+  const float2 one = bc2(1.f);
+  const float2 rho = add2(one, drho), ir = rcp2(rho);
+  const float2 ux = mul2(jx, ir), uy = mul2(jy, ir), uz = mul2(jz, ir);
+  const float2 usq = fma2(ux, ux, fma2(uy, uy, mul2(uz, uz)));
+  const float t0 = a.tau0.f;
+  float2 tau = bc2(t0);
+  if (a.use_smag != 0) {
+    const float2 d3 = mul2(drho, bc2(1.f / 3.f));
+    const float2 rux = mul2(rho, ux), ruy = mul2(rho, uy), ruz = mul2(rho, uz);
+    const float2 pxx = sub2(sxx, fma2(rux, ux, d3)), pyy = sub2(syy, fma2(ruy, uy, d3)), pzz = sub2(szz, fma2(ruz, uz, d3));
+    const float2 pxy = sub2(sxy, mul2(rux, uy)), pxz = sub2(sxz, mul2(rux, uz)), pyz = sub2(syz, mul2(ruy, uz));
+    const float2 off = fma2(pxy, pxy, fma2(pxz, pxz, mul2(pyz, pyz)));
+    const float2 pn = sqrt2(fma2(bc2(2.f), off, fma2(pxx, pxx, fma2(pyy, pyy, mul2(pzz, pzz)))));
+    tau = mul2(bc2(0.5f), add2(bc2(t0), sqrt2(fma2(bc2(a.smag.f), mul2(pn, ir), bc2(t0 * t0)))));
+  }
+  const float2 itau = rcp2(tau);
+  const float2 k = sub2(one, itau), nk = sub2(itau, one);
+  const float2 vx = fma2(gamma, ux, mul2(bc2(a.fx.f), ir));
+  const float2 vy = fma2(gamma, uy, mul2(bc2(a.fy.f), ir));
+  const float2 vz = fma2(gamma, uz, mul2(bc2(a.fz.f), ir));
+  const float2 vsq = fma2(vx, vx, fma2(vy, vy, mul2(vz, vz)));
+  const float2 base = sub2(mul2(itau, drho), mul2(mul2(bc2(1.5f), rho), fma2(nk, usq, vsq)));
+  const float2 r45 = mul2(bc2(4.5f), rho), r3 = mul2(bc2(3.f), rho);
+  h[0] = fma2(k, h[0], mul2(bc2(wgt<Q, float>(0)), base));
+  sfor<1, H + 1>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    const float2 cu = cdot2<Q, i>(ux, uy, uz), cv = cdot2<Q, i>(vx, vy, vz);
+    const float2 sym = fma2(r45, fma2(nk, mul2(cu, cu), mul2(cv, cv)), base);
+    const float2 anti = mul2(r3, fma2(nk, cu, cv));
+    const float2 w = bc2(wgt<Q, float>(i));
+    const float2 p = mul2(w, add2(sym, anti)), m = mul2(w, sub2(sym, anti));
+    if constexpr (csign<Q, i>() > 0) {
+      h[i] = fma2(k, h[i], p);
+      h[i + H] = fma2(k, h[i + H], m);
+    } else {
+      h[i] = fma2(k, h[i], m);
+      h[i + H] = fma2(k, h[i + H], p);
+    }
+  });
+  const float2 chk = add2(add2(abs2(rho), abs2(ux)), add2(abs2(uy), abs2(uz)));
+  return chk.x < 1e30f && chk.y < 1e30f;
 }
 
 // Regularised reconstruction: unknown populations (known(i) false) take the non-equilibrium part
@@ -455,8 +573,8 @@ __device__ __forceinline__ void wall_state(const Args& a, const C* nrm, C yw, co
     const C U = sqrt(utx * utx + uty * uty + utz * utz);
     if (U >= C(1e-12)) {
       tx = utx / U; ty = uty / U; tz = utz / U;
-      const C k = C(a.kappa), E = C(a.E);
-      const C nu = C(a.nu0);
+      const C k = a.kappa.get<C>(), E = a.E.get<C>();
+      const C nu = a.nu0.get<C>();
       const C upr = sp_solve_re<C>(U * (yw + C(1)) / nu, k, E);
       const C utau = U / upr;
       const C upw = sp_solve_y<C>(yw * utau / nu, k, E);
@@ -467,7 +585,7 @@ __device__ __forceinline__ void wall_state(const Args& a, const C* nrm, C yw, co
   }
   const C hd = C(0.5) * dudn;
   ws[0] = ubx; ws[1] = uby; ws[2] = ubz;
-  ws[3] = C(a.tau0) + C(3) * C(a.cs2smag) * fabs(dudn);
+  ws[3] = a.tau0.get<C>() + C(3) * a.cs2smag.get<C>() * fabs(dudn);
   ws[4] = hd * C(2) * tx * nx; ws[5] = hd * C(2) * ty * ny; ws[6] = hd * C(2) * tz * nz;
   ws[7] = hd * (tx * ny + nx * ty); ws[8] = hd * (tx * nz + nx * tz); ws[9] = hd * (ty * nz + ny * tz);
 }
@@ -481,12 +599,12 @@ __device__ __forceinline__ void collide_wall_state(C* h, const Args& a, const C*
   const C rho = C(1) + drho, ir = rcp(rho);
   rho_o = rho;
   const C hf = C(0.5) * ir;
-  urx = jx * ir + C(a.fx) * hf;
-  ury = jy * ir + C(a.fy) * hf;
-  urz = jz * ir + C(a.fz) * hf;
+  urx = jx * ir + a.fx.get<C>() * hf;
+  ury = jy * ir + a.fy.get<C>() * hf;
+  urz = jz * ir + a.fz.get<C>() * hf;
   const C tau = ws[3];
   const C sxx = ws[4], syy = ws[5], szz = ws[6], sxy = ws[7], sxz = ws[8], syz = ws[9];
-  const C vx = ws[0] + C(a.fx) * ir, vy = ws[1] + C(a.fy) * ir, vz = ws[2] + C(a.fz) * ir;
+  const C vx = ws[0] + a.fx.get<C>() * ir, vy = ws[1] + a.fy.get<C>() * ir, vz = ws[2] + a.fz.get<C>() * ir;
   const C vsq = vx * vx + vy * vy + vz * vz;
   const C g = -C(3) * rho * (tau - C(1));  // (1 - 1/tau) * (-rho tau / cs^2)
   sfor<0, Q>([&](auto I) {

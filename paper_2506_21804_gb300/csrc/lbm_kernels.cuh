@@ -54,6 +54,37 @@ struct Nbr32 {
   }
 };
 
+// Neighbour offsets of the cell pair (x0, x0 + 1), x0 even and nx even: only x0 - 1 and x0 + 2 can
+// wrap in x, so one x-delta per side serves both cells.
+struct Nbr32Pair {
+  unsigned n;  // index of x0
+  int dxm, dxp, dym, dyp, dzm, dzp;
+  __device__ __forceinline__ Nbr32Pair(const Args& a, int x0, int y, int z, long long n0) {
+    n = unsigned(n0);
+    const int nx = a.nx, nxy = int(a.nxy);
+    dxm = x0 == 0 ? nx - 1 : -1;
+    dxp = x0 + 1 == nx - 1 ? 1 - nx : 1;
+    dym = y == 0 ? (a.ny - 1) * nx : -nx;
+    dyp = y == a.ny - 1 ? (1 - a.ny) * nx : nx;
+    dzm = z == 0 ? (a.nz - 1) * nxy : -nxy;
+    dzp = z == a.nz - 1 ? (1 - a.nz) * nxy : nxy;
+  }
+  // index of population p at cell x0 + CELL displaced by (dx, dy, dz)
+  template <int CELL, int DX, int DY, int DZ>
+  __device__ __forceinline__ unsigned at(unsigned pbase) const {
+    unsigned r = pbase + n;
+    if constexpr (CELL == 0 && DX < 0) r += unsigned(dxm);
+    if constexpr (CELL == 0 && DX > 0) r += 1u;
+    if constexpr (CELL == 1 && DX == 0) r += 1u;
+    if constexpr (CELL == 1 && DX > 0) r += 1u + unsigned(dxp);
+    if constexpr (DY < 0) r += unsigned(dym);
+    if constexpr (DY > 0) r += unsigned(dyp);
+    if constexpr (DZ < 0) r += unsigned(dzm);
+    if constexpr (DZ > 0) r += unsigned(dzp);
+    return r;
+  }
+};
+
 // Gather the Q deviations of cell n. LOAD_LOCAL: h_i from slot (i, n) of src (natural layout);
 // LOAD_SLOTS: h_i from the AA slot of direction i (state after an even step).
 template <int Q, class S, int LOAD>
@@ -237,7 +268,7 @@ __device__ __forceinline__ void apply_bc(const Args& a, int kind, int y, int z, 
     const long long pl = (long long)a.ny * a.nz, p = y + (long long)a.ny * z;
     bc_inlet<Q, C>(h, ub[p], ub[pl + p], ub[2 * pl + p]);
   } else if (kind == K_OUTFLOW) {
-    bc_outlet<Q, C>(h, C(a.rho_out), C(a.drho_out));
+    bc_outlet<Q, C>(h, a.rho_out.get<C>(), a.drho_out.get<C>());
   }
 }
 
@@ -343,6 +374,7 @@ template <> struct Pair<__half> {
   static __device__ __forceinline__ float hif(V v) { return __high2float(v); }
   static __device__ __forceinline__ V with_lo(V v, float x) { return __halves2half2(__float2half_rn(x), __high2half(v)); }
   static __device__ __forceinline__ V with_hi(V v, float x) { return __halves2half2(__low2half(v), __float2half_rn(x)); }
+  static __device__ __forceinline__ V pack(float lo, float hi) { return __floats2half2_rn(lo, hi); }
 };
 template <> struct Pair<__nv_bfloat16> {
   using V = __nv_bfloat162;
@@ -355,16 +387,88 @@ template <> struct Pair<__nv_bfloat16> {
   static __device__ __forceinline__ float hif(V v) { return __high2float(v); }
   static __device__ __forceinline__ V with_lo(V v, float x) { return __halves2bfloat162(__float2bfloat16_rn(x), __high2bfloat16(v)); }
   static __device__ __forceinline__ V with_hi(V v, float x) { return __halves2bfloat162(__low2bfloat16(v), __float2bfloat16_rn(x)); }
+  static __device__ __forceinline__ V pack(float lo, float hi) { return __floats2bfloat162_rn(lo, hi); }
 };
 
 // Interior kernel for 16-bit storage (nx even, 32-bit indices): the thread owns cells x0 = 2j and
-// x0 + 1. When both are plain FLUID cells, directions without an x-component move both cells'
-// values with one 32-bit access and the others with two 16-bit accesses; the pair stays packed in
-// registers and the two cells are collided one after the other. Otherwise each cell takes the
+// x0 + 1. Directions without an x-component move both cells' values with one 32-bit access, the
+// others with two 16-bit accesses; the pair stays packed in 16-bit pair registers and the two cells
+// collide together in packed FP32 lanes. Pairs holding a cell that is not plain FLUID take the
 // per-cell path.
 template <int Q, class S, bool ODD>
-__global__ void __launch_bounds__(BULK_THREADS, (Q == 19 ? 8 : 4)) k_bulk2(const Args a) {
+__device__ __forceinline__ void pair_load(const Args& a, const S* f, int x0, int y, int z, typename Pair<S>::V* raw) {
   using P = Pair<S>;
+  const unsigned us = unsigned(a.stride);
+  const unsigned un = unsigned(x0 + y * a.nx) + unsigned(z) * unsigned(a.nxy);
+  if constexpr (!ODD) {
+    sfor<0, Q>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      raw[i] = P::ld(f + (unsigned(i) * us + un));
+    });
+  } else {
+    const Nbr32Pair nb(a, x0, y, z, un);
+    sfor<0, Q>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      constexpr int cx = -Lat<Q>::cx(i), cy = -Lat<Q>::cy(i), cz = -Lat<Q>::cz(i);
+      const unsigned pb = unsigned(opp<Q>(i)) * us;
+      if constexpr (cx == 0) raw[i] = P::ld(f + nb.at<0, 0, cy, cz>(pb));
+      else raw[i] = P::make(f[nb.at<0, cx, cy, cz>(pb)], f[nb.at<1, cx, cy, cz>(pb)]);
+    });
+  }
+}
+
+template <int Q, class S, bool ODD>
+__device__ __forceinline__ void pair_update(const Args& a, S* f, int x0, int y, int z, typename Pair<S>::V* raw) {
+  using P = Pair<S>;
+  const unsigned us = unsigned(a.stride);
+  const unsigned un = unsigned(x0 + y * a.nx) + unsigned(z) * unsigned(a.nxy);
+  bool ok;
+  {
+    float2 h[Q];
+    sfor<0, Q>([&](auto I) { h[I] = make_float2(P::lof(raw[I]), P::hif(raw[I])); });
+    const float2 gam = a.gamma ? make_float2(static_cast<const float*>(a.gamma)[un], static_cast<const float*>(a.gamma)[un + 1])
+                               : bc2(1.f);
+    ok = collide_fluid_x2<Q>(h, gam, a);
+    sfor<0, Q>([&](auto I) { raw[I] = P::pack(h[I].x, h[I].y); });
+  }
+  if (!ok) atomicOr(a.status, ST_NAN);
+  // Opaque copies of the coordinates: the store addresses are recomputed here rather than held live
+  // across the collision.
+  int x0c, yc, zc;
+  asm volatile("mov.b32 %0, %1;" : "=r"(x0c) : "r"(x0));
+  asm volatile("mov.b32 %0, %1;" : "=r"(yc) : "r"(y));
+  asm volatile("mov.b32 %0, %1;" : "=r"(zc) : "r"(z));
+  const unsigned un2 = unsigned(x0c + yc * a.nx) + unsigned(zc) * unsigned(a.nxy);
+  if constexpr (!ODD) {
+    sfor<0, Q>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      P::st(f + (unsigned(opp<Q>(i)) * us + un2), raw[i]);
+    });
+  } else {
+    const Nbr32Pair nb(a, x0c, yc, zc, un2);
+    sfor<0, Q>([&](auto I) {
+      constexpr int k = decltype(I)::value;  // f*_k goes to slot (k, x + c_k)
+      constexpr int cx = Lat<Q>::cx(k), cy = Lat<Q>::cy(k), cz = Lat<Q>::cz(k);
+      const unsigned pb = unsigned(k) * us;
+      if constexpr (cx == 0) {
+        P::st(f + nb.at<0, 0, cy, cz>(pb), raw[k]);
+      } else {
+        f[nb.at<0, cx, cy, cz>(pb)] = P::lo(raw[k]);
+        f[nb.at<1, cx, cy, cz>(pb)] = P::hi(raw[k]);
+      }
+    });
+  }
+}
+
+#ifndef LBM_BULK2_MINB_EVEN
+#define LBM_BULK2_MINB_EVEN 7
+#endif
+#ifndef LBM_BULK2_MINB_ODD
+#define LBM_BULK2_MINB_ODD 7
+#endif
+template <int Q, class S, bool ODD>
+__global__ void __launch_bounds__(BULK_THREADS, (Q == 19 ? (ODD ? LBM_BULK2_MINB_ODD : LBM_BULK2_MINB_EVEN) : 4))
+    k_bulk2(const Args a) {
   const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
@@ -372,68 +476,14 @@ __global__ void __launch_bounds__(BULK_THREADS, (Q == 19 ? 8 : 4)) k_bulk2(const
   const long long n0 = x0 + (long long)y * a.nx + (long long)z * a.nxy;
   S* f = static_cast<S*>(a.f);
   const unsigned short tt = *reinterpret_cast<const unsigned short*>(a.type + n0);
-  const uint8_t t0 = uint8_t(tt & 0xff), t1 = uint8_t(tt >> 8);
-  if (t0 | t1) {
-    bulk_cell<Q, S, ODD>(a, f, x0, y, z, n0, t0);
-    bulk_cell<Q, S, ODD>(a, f, x0 + 1, y, z, n0 + 1, t1);
+  if (tt) {
+    bulk_cell<Q, S, ODD>(a, f, x0, y, z, n0, uint8_t(tt & 0xff));
+    bulk_cell<Q, S, ODD>(a, f, x0 + 1, y, z, n0 + 1, uint8_t(tt >> 8));
     return;
   }
-  typename P::V raw[Q];
-  const unsigned us = unsigned(a.stride), un = unsigned(n0);
-  if constexpr (!ODD) {
-    sfor<0, Q>([&](auto I) {
-      constexpr int i = decltype(I)::value;
-      raw[i] = P::ld(f + (unsigned(i) * us + un));
-    });
-  } else {
-    const Nbr32 nb0(a, x0, y, z, n0), nb1(a, x0 + 1, y, z, n0 + 1);
-    sfor<0, Q>([&](auto I) {
-      constexpr int i = decltype(I)::value;
-      constexpr int cx = -Lat<Q>::cx(i), cy = -Lat<Q>::cy(i), cz = -Lat<Q>::cz(i);
-      const unsigned pb = unsigned(opp<Q>(i)) * us;
-      if constexpr (cx == 0) raw[i] = P::ld(f + nb0.at<0, cy, cz>(pb));
-      else raw[i] = P::make(f[nb0.at<cx, cy, cz>(pb)], f[nb1.at<cx, cy, cz>(pb)]);
-    });
-  }
-  bool ok = true;
-  {
-    float h[Q], r, ux, uy, uz;
-    sfor<0, Q>([&](auto I) { h[I] = P::lof(raw[I]); });
-    collide_fluid<Q, float>(h, gamma_at<float>(a, n0), a, r, ux, uy, uz);
-    ok = finite_all<float>(r, ux, uy, uz);
-    sfor<0, Q>([&](auto I) { raw[I] = P::with_lo(raw[I], h[I]); });
-  }
-  {
-    float h[Q], r, ux, uy, uz;
-    sfor<0, Q>([&](auto I) { h[I] = P::hif(raw[I]); });
-    collide_fluid<Q, float>(h, gamma_at<float>(a, n0 + 1), a, r, ux, uy, uz);
-    ok = ok && finite_all<float>(r, ux, uy, uz);
-    sfor<0, Q>([&](auto I) { raw[I] = P::with_hi(raw[I], h[I]); });
-  }
-  if (!ok) atomicOr(a.status, ST_NAN);
-  if constexpr (!ODD) {
-    // The store addresses equal the load addresses; an opaque copy of the cell index makes the
-    // compiler recompute them instead of holding 19 pointers live across the two collisions.
-    unsigned un2;
-    asm volatile("mov.u32 %0, %1;" : "=r"(un2) : "r"(un));
-    sfor<0, Q>([&](auto I) {
-      constexpr int i = decltype(I)::value;
-      P::st(f + (unsigned(opp<Q>(i)) * us + un2), raw[i]);
-    });
-  } else {
-    const Nbr32 nb0(a, x0, y, z, n0), nb1(a, x0 + 1, y, z, n0 + 1);
-    sfor<0, Q>([&](auto I) {
-      constexpr int k = decltype(I)::value;  // f*_k goes to slot (k, x + c_k)
-      constexpr int cx = Lat<Q>::cx(k), cy = Lat<Q>::cy(k), cz = Lat<Q>::cz(k);
-      const unsigned pb = unsigned(k) * us;
-      if constexpr (cx == 0) {
-        P::st(f + nb0.at<0, cy, cz>(pb), raw[k]);
-      } else {
-        f[nb0.at<cx, cy, cz>(pb)] = P::lo(raw[k]);
-        f[nb1.at<cx, cy, cz>(pb)] = P::hi(raw[k]);
-      }
-    });
-  }
+  typename Pair<S>::V raw[Q];
+  pair_load<Q, S, ODD>(a, f, x0, y, z, raw);
+  pair_update<Q, S, ODD>(a, f, x0, y, z, raw);
 }
 
 // Wall-model state of every WALL entry from the previous step's reference velocities (fused mode).
@@ -547,9 +597,9 @@ __device__ __forceinline__ void cell_macro(const Args& a, long long n, bool swap
   sums<Q, C>(h, drho, jx, jy, jz);
   rho = C(1) + drho;
   const C ir = C(1) / rho, hf = C(0.5) * ir;
-  u[0] = jx * ir + C(a.fx) * hf;
-  u[1] = jy * ir + C(a.fy) * hf;
-  u[2] = jz * ir + C(a.fz) * hf;
+  u[0] = jx * ir + a.fx.get<C>() * hf;
+  u[1] = jy * ir + a.fy.get<C>() * hf;
+  u[2] = jz * ir + a.fz.get<C>() * hf;
 }
 
 template <int Q, class S>
@@ -741,24 +791,27 @@ __device__ __forceinline__ void reverse_cell(const Args& a, const AdjArgs& d, in
       mu[opp<Q>(i)] = tmp[i];
     });
   }
-  C h[Q];
-  gather<Q, S, LOAD_LOCAL>(a, static_cast<const S*>(d.fst), x, y, z, n, false, h);
   C lam[Q], ggam = C(0), gub[3] = {C(0), C(0), C(0)};
   const C gam = gamma_at<C>(a, n);
   const bool bc = kind == K_INFLOW || kind == K_OUTFLOW;
   // boundary reconstruction forward (inlet/outlet lanes only), then the collision reverse for all
-  // lanes together, then the reconstruction reverse (inlet/outlet lanes only)
+  // lanes together, then the reconstruction reverse (inlet/outlet lanes only, which read the
+  // populations again rather than keep them live through the collision reverse)
   C hb[Q];
-  sfor<0, Q>([&](auto I) { hb[I] = h[I]; });
+  gather<Q, S, LOAD_LOCAL>(a, static_cast<const S*>(d.fst), x, y, z, n, false, hb);
   if (bc) apply_bc<Q, C>(a, kind, y, z, hb);
   C gh[Q];
   collide_fluid_vjp<Q, C>(hb, gam, a, mu, gh, ggam);
   if (kind == K_INFLOW) {
+    C h[Q];
+    gather<Q, S, LOAD_LOCAL>(a, static_cast<const S*>(d.fst), x, y, z, n, false, h);
     const C* ub = cptr<C>(a.uin);
     const long long pl = (long long)a.ny * a.nz, p = y + (long long)a.ny * z;
     bc_inlet_vjp<Q, C>(h, ub[p], ub[pl + p], ub[2 * pl + p], gh, lam, gub);
   } else if (kind == K_OUTFLOW) {
-    bc_outlet_vjp<Q, C>(h, C(a.rho_out), C(a.drho_out), gh, lam);
+    C h[Q];
+    gather<Q, S, LOAD_LOCAL>(a, static_cast<const S*>(d.fst), x, y, z, n, false, h);
+    bc_outlet_vjp<Q, C>(h, a.rho_out.get<C>(), a.drho_out.get<C>(), gh, lam);
   } else {
     sfor<0, Q>([&](auto I) { lam[I] = gh[I]; });
   }
@@ -780,8 +833,11 @@ __device__ __forceinline__ void reverse_cell(const Args& a, const AdjArgs& d, in
 
 // Reverse step over every cell (inlet/outlet cells included: their extra boundary-condition reverse
 // costs less as a divergent branch than as a separate, latency-bound pass over a sparse plane).
+#ifndef LBM_REVERSE_MINB
+#define LBM_REVERSE_MINB 8
+#endif
 template <int Q, class S>
-__global__ void __launch_bounds__(BULK_THREADS) k_reverse(const Args a, const AdjArgs d) {
+__global__ void __launch_bounds__(BULK_THREADS, LBM_REVERSE_MINB) k_reverse(const Args a, const AdjArgs d) {
   using C = typename Codec<S>::C;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
