@@ -249,6 +249,17 @@ def secondary(lbm, I, torch):
                                   "interior_kernel_gbs": bw}
         lat.close()
     del u32
+    # hybrid recursive regularised collision on the same channel: local stress only (sigma = 1) and
+    # blended with the finite-difference strain (sigma = 1/2, reads and writes the velocity field)
+    for sg in (1.0, 0.5):
+        lat = lbm.Lattice.from_workload(w, storage=lbm.F32)
+        lat.set_collision(lbm.HRR, sg)
+        g, ms = timed_glups(lat, 40, 3)
+        info = lat.info()
+        nb = info["N"] - info["n_solid"] - info["n_list"]
+        bw = (nb * (152 + (24 if sg < 1 else 0)) + info["N"]) / (ms[0] / 40 * 1e-3) / 1e9
+        out[f"channel_hrr_sigma{sg:g}_fp32"] = {"glups": g, "vs_bgk_fp32": g / g32, "interior_kernel_gbs": bw}
+        lat.close()
     # urban canopy, D3Q19 and D3Q27
     for q in (19, 27):
         wc = I.canopy(nx=512, ny=512, nz=256, q=q, seed=2506, dtype=np.float32)
@@ -278,6 +289,8 @@ def main():
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"],
                     help="population storage (the headline is f32; the others are for profiling)")
     ap.add_argument("--lattice", type=int, default=19, choices=[19, 27], help="velocity set (profiling)")
+    ap.add_argument("--collision", default="bgk", choices=["bgk", "hrr"], help="collision model (profiling)")
+    ap.add_argument("--sigma", type=float, default=1.0, help="HRR hybridisation factor")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -302,7 +315,7 @@ def main():
                           "unit": "GLUPS", "config": {"workload": f"duct {n}^3 D3Q19 FP32 porosity"}, "adjoint": res}))
         return
     headline = (args.workload == "channel" and args.size in (None, [256, 256, 256]) and args.storage == "f32"
-                and args.lattice == 19)
+                and args.lattice == 19 and args.collision == "bgk")
     storage = {"f32": lbm.F32, "f16": lbm.F16, "bf16": lbm.BF16}[args.storage]
     esize = 4 if args.storage == "f32" else 2
     if args.workload == "channel":
@@ -319,6 +332,10 @@ def main():
     lat.set_stream(stream)
     if args.kernel == "staged":
         lat.set_option(lbm.OPT_KERNEL, lbm.KERNEL_STAGED)
+    hrr = args.collision == "hrr"
+    if hrr:
+        lat.set_collision(lbm.HRR, args.sigma)
+        wname += f", HRR collision sigma={args.sigma}"
     info = lat.info()
     lat.step(args.warmup)
     lat.sync()
@@ -336,7 +353,8 @@ def main():
     t_ms = max_over_ranks(ms[2], world)
     value = world * w.N * args.steps / (t_ms * 1e-3) / 1e9
     n_bulk = info["N"] - info["n_solid"] - info["n_list"]
-    per_cell = 2 * w.q * esize
+    # HRR with sigma < 1 also reads the previous velocity field and writes its own (3 values each)
+    per_cell = 2 * w.q * esize + (2 * 3 * (8 if args.storage == "f64" else 4) if (hrr and args.sigma < 1) else 0)
     bytes_bulk = n_bulk * per_cell + info["N"] * 1
     bulk_ms = ms[0] / args.steps
     peak, peak_src = peaks()
@@ -370,7 +388,7 @@ def main():
         "config": {"workload": wname, "kernel": args.kernel, "cells": w.N, "parallelism": f"replicas x{world}",
                    "l2": "state of 2.6 GB > 129 MB L2 between steps, no flush needed",
                    "non_solid_cells": info["N"] - info["n_solid"], "boundary_list_cells": info["n_list"]},
-        "roofline": {"bound": "hbm", "kernel": ("k_bulk_tma" if (args.kernel == "staged" and w.nx % 128 == 0) else "k_bulk") + " (interior cells)", "achieved": achieved, "peak": peak,
+        "roofline": {"bound": "hbm", "kernel": ("k_bulk_hrr" if hrr else ("k_bulk_tma" if (args.kernel == "staged" and w.nx % 128 == 0) else "k_bulk")) + " (interior cells)", "achieved": achieved, "peak": peak,
                      "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "bytes_per_launch": bytes_bulk, "launch_ms": bulk_ms,
                      "share_of_step": ms[0] / ms[2]},

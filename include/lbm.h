@@ -68,6 +68,8 @@ enum { LBM_KIND_FLUID = 0, LBM_KIND_SOLID = 1, LBM_KIND_WALL = 2, LBM_KIND_INFLO
 enum { LBM_FACE_PERIODIC = 0, LBM_FACE_WALL = 1, LBM_FACE_SLIP = 2, LBM_FACE_OPEN = 3 };
 /* dtype codes of host/device array arguments of the *_ex calls. */
 enum { LBM_DTYPE_F32 = 1, LBM_DTYPE_F64 = 0 };
+/* Collision models (lbm_set_collision). */
+enum { LBM_BGK = 0, LBM_HRR = 1 };
 
 /* Create a lattice of nx*ny*nz cells with molecular relaxation time tau (> 1/2) and Smagorinsky
  * constant c_smag >= 0 (C_S of Eq. turbVisc; 0 gives plain BGK). Storage LBM_F32, all faces
@@ -99,6 +101,17 @@ int lbm_set_porosity_ex(lbm_ctx* ctx, const void* gamma, int dtype);
 /* Spalding wall function on WALL cells with von Karman constant kappa and wall constant E
  * (kappa <= 0 switches it off: WALL cells then collide like fluid cells with bounce-back). */
 int lbm_set_wall_model(lbm_ctx* ctx, double kappa, double E);
+/* Collision model (Sec. 2.2, Eq. hlbm). LBM_BGK (default): f^(1) = f - f^eq(rho, u), second-order
+ * equilibrium. LBM_HRR: the hybrid recursive regularised form: third-order Hermite equilibrium,
+ * f^(1) rebuilt from the second-order coefficient A2 = sigma Pi^neq + (1 - sigma) Pi^FD and its
+ * recursive third-order extension, Pi^FD = -2 rho cs^2 tau S^FD with S^FD the central-difference
+ * strain of the previous step's velocity field (one-sided next to solids and non-periodic faces);
+ * WALL cells with the wall model use sigma = 0 with the modelled strain. sigma in [0, 1]; 1 needs no
+ * velocity field. The HRR form keeps a velocity field of 3*N compute-type values (two copies,
+ * allocated here, released on LBM_BGK); it is rebuilt from the state before the first step after
+ * any state change and is part of lbm_save. The adjoint calls return LBM_ESTATE under LBM_HRR.
+ * Errors: LBM_EINVAL for an unknown model or sigma outside [0, 1]. */
+int lbm_set_collision(lbm_ctx* ctx, int model, double sigma);
 /* Equilibrium state f_i = f_i^eq(rho, u) (rho: N values, u: 3*N values); step counter to 0; the
  * wall-model reference buffer is filled with this state's velocity. */
 int lbm_init_equilibrium(lbm_ctx* ctx, const float* rho, const float* u);

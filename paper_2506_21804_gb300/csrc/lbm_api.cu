@@ -56,12 +56,13 @@ struct DevBuf {
 };
 
 constexpr int RED_BLOCKS = 1024;
-constexpr uint32_t SAVE_MAGIC = 0x4C424D31u;  // "LBM1"
+constexpr uint32_t SAVE_MAGIC = 0x4C424D32u;  // "LBM2"
 
 struct SaveHeader {
-  uint32_t magic, q, storage, pad;
+  uint32_t magic, q, storage, model;
   int64_t nx, ny, nz, n_list, t;
-  uint64_t fbytes, rbytes;
+  uint64_t fbytes, rbytes, ubytes;  // populations, one reference buffer, HRR velocity field (0: none)
+  double sigma;
 };
 }  // namespace
 
@@ -77,6 +78,9 @@ struct lbm_ctx {
   double kappa = 0.41, E = 9.52;
   int kernel = 0;       // LBM_OPT_KERNEL value
   int debug_stall = 0;  // LBM_OPT_DEBUG_STALL value
+  int model = LBM_BGK;  // collision model
+  double sigma = 1.0;   // HRR hybridisation factor
+  bool uvel_stale = true;  // the HRR velocity field must be rebuilt from the state before the next step
   int device = 0;
   cudaStream_t stream = 0;
   const Ops* ops = nullptr;
@@ -85,6 +89,7 @@ struct lbm_ctx {
   // device buffers
   DevBuf f, type, mask, wdist, gamma, uin, lcell, nsum, wref, lxyz, lcode, wnrm, wyw, ref0, ref1, status, red, redout, stage;
   DevBuf lidx, lsub, lwall, lbc, wst;
+  DevBuf uvel0, uvel1;  // HRR velocity fields (step t reads uvel[t & 1], writes the other)
   int n_sub = 0, n_wall = 0, n_bc = 0;
   bool has_gamma = false, has_wdist = false;
   int n_list = 0;
@@ -102,7 +107,7 @@ struct lbm_ctx {
   double adj_ms[3] = {0, 0, 0};
 
   ~lbm_ctx() {
-    DevBuf* all[] = {&lidx, &lsub, &lwall, &lbc, &wst, &f, &type, &mask, &wdist, &gamma, &uin, &lcell, &nsum, &wref, &lxyz, &lcode, &wnrm, &wyw, &ref0, &ref1, &status, &red,
+    DevBuf* all[] = {&uvel0, &uvel1, &lidx, &lsub, &lwall, &lbc, &wst, &f, &type, &mask, &wdist, &gamma, &uin, &lcell, &nsum, &wref, &lxyz, &lcode, &wnrm, &wyw, &ref0, &ref1, &status, &red,
                      &redout, &stage, &lamA, &lamB, &dgam, &duin, &plane};
     for (DevBuf* b : all) b->release();
     for (auto& b : ckpts) b.release();
@@ -179,6 +184,11 @@ Args make_args(const lbm_ctx* c) {
   a.wst = c->wst.p;
   a.idx32 = ((unsigned long long)c->q * (unsigned long long)c->stride < (1ull << 32) && c->N < (1ll << 31)) ? 1 : 0;
   a.debug_stall = c->debug_stall;
+  a.model = c->model;
+  a.hybrid = (c->model == LBM_HRR && c->sigma < 1.0) ? 1 : 0;
+  a.sigma = c->sigma;
+  a.uvel_rd = (c->t & 1) ? c->uvel1.p : c->uvel0.p;
+  a.uvel_wr = (c->t & 1) ? c->uvel0.p : c->uvel1.p;
   return a;
 }
 
@@ -369,7 +379,10 @@ int build_geometry(lbm_ctx* c) {
 
 // One time step: in fused mode the wall-model states of the WALL entries first, then the interior
 // kernel, then the boundary-list kernel. Events (optional) bracket the interior kernel.
+int fill_uvel(lbm_ctx* c);
+
 void launch_step(lbm_ctx* c, cudaEvent_t before_bulk = nullptr, cudaEvent_t after_bulk = nullptr) {
+  if (c->model == LBM_HRR && c->uvel_stale) fill_uvel(c);
   const Args a = make_args(c);
   const int odd = int(c->t & 1);
   if (a.fuse && a.wm) c->ops->wall_pass(a, c->stream);
@@ -382,6 +395,7 @@ void launch_step(lbm_ctx* c, cudaEvent_t before_bulk = nullptr, cudaEvent_t afte
 
 // State to rest (f = w), step counter 0, reference buffers from that state.
 int reset_state(lbm_ctx* c) {
+  c->uvel_stale = true;
   CK(cudaMemsetAsync(c->f.p, 0, (size_t)c->q * c->stride * c->ops->elem, c->stream));
   c->t = 0;
   c->adj_t0 = -1;
@@ -391,7 +405,22 @@ int reset_state(lbm_ctx* c) {
   return LBM_OK;
 }
 
+// HRR velocity field of the current state (reported velocity of every cell) into the buffer the
+// next step reads.
+int fill_uvel(lbm_ctx* c) {
+  const size_t bytes = 3 * (size_t)c->N * c->ops->celem;
+  CK(c->uvel0.ensure(bytes));
+  CK(c->uvel1.ensure(bytes));
+  Args a = make_args(c);
+  c->ops->moments(a, int(c->t & 1), nullptr, const_cast<void*>(a.uvel_rd),
+                  c->ops->celem == 8 ? LBM_DTYPE_F64 : LBM_DTYPE_F32, c->stream);
+  CK(cudaGetLastError());
+  c->uvel_stale = false;
+  return LBM_OK;
+}
+
 int fill_refs(lbm_ctx* c) {
+  c->uvel_stale = true;
   Args a = make_args(c);
   const int sw = int(c->t & 1);
   c->ops->ref_fill(a, sw, c->ref0.p, c->stream);
@@ -494,6 +523,7 @@ int lbm_set_precision(lbm_ctx* c, int storage) {
   if ((rc = upload_uin(c)) != LBM_OK) return rc;
   if (c->has_gamma && (rc = upload_compute(c, c->gamma, g.data(), LBM_DTYPE_F64, c->N)) != LBM_OK) return rc;
   c->wnrm.release(); c->wyw.release(); c->ref0.release(); c->ref1.release();
+  c->uvel0.release(); c->uvel1.release();
   if ((rc = build_geometry(c)) != LBM_OK) return rc;
   return reset_state(c);
 }
@@ -821,21 +851,30 @@ int lbm_save(lbm_ctx* c, void* buf, size_t* len) {
   if (!c || !len) return fail(LBM_EINVAL, "null argument");
   const size_t fb = (size_t)c->q * c->stride * c->ops->elem;
   const size_t rb = std::max<size_t>(1, (size_t)c->n_list) * 3 * c->ops->celem;
-  const size_t total = sizeof(SaveHeader) + fb + 2 * rb;
+  const size_t ub = c->model == LBM_HRR ? 3 * (size_t)c->N * c->ops->celem : 0;
+  const size_t total = sizeof(SaveHeader) + fb + 2 * rb + ub;
   if (!buf) {
     *len = total;
     return LBM_OK;
   }
   if (*len < total) return fail(LBM_EINVAL, "buffer holds %zu bytes, %zu needed", *len, total);
+  if (ub && c->uvel_stale) {
+    int rc = fill_uvel(c);
+    if (rc != LBM_OK) return rc;
+  }
   SaveHeader h{};
-  h.magic = SAVE_MAGIC; h.q = c->q; h.storage = c->storage;
+  h.magic = SAVE_MAGIC; h.q = c->q; h.storage = c->storage; h.model = c->model;
   h.nx = c->nx; h.ny = c->ny; h.nz = c->nz; h.n_list = c->n_list; h.t = c->t;
-  h.fbytes = fb; h.rbytes = rb;
+  h.fbytes = fb; h.rbytes = rb; h.ubytes = ub; h.sigma = c->sigma;
   char* p = static_cast<char*>(buf);
   std::memcpy(p, &h, sizeof(h));
   CK(cudaMemcpyAsync(p + sizeof(h), c->f.p, fb, cudaMemcpyDefault, c->stream));
   CK(cudaMemcpyAsync(p + sizeof(h) + fb, c->ref0.p, rb, cudaMemcpyDefault, c->stream));
   CK(cudaMemcpyAsync(p + sizeof(h) + fb + rb, c->ref1.p, rb, cudaMemcpyDefault, c->stream));
+  if (ub) {
+    const void* src = (c->t & 1) ? c->uvel1.p : c->uvel0.p;
+    CK(cudaMemcpyAsync(p + sizeof(h) + fb + 2 * rb, src, ub, cudaMemcpyDefault, c->stream));
+  }
   CK(cudaStreamSynchronize(c->stream));
   *len = total;
   return LBM_OK;
@@ -848,22 +887,47 @@ int lbm_load(lbm_ctx* c, const void* buf, size_t len) {
   std::memcpy(&h, buf, sizeof(h));
   const size_t fb = (size_t)c->q * c->stride * c->ops->elem;
   const size_t rb = std::max<size_t>(1, (size_t)c->n_list) * 3 * c->ops->celem;
+  const size_t ub = c->model == LBM_HRR ? 3 * (size_t)c->N * c->ops->celem : 0;
   if (h.magic != SAVE_MAGIC || int(h.q) != c->q || int(h.storage) != c->storage || h.nx != c->nx || h.ny != c->ny ||
-      h.nz != c->nz || h.n_list != c->n_list || h.fbytes != fb || h.rbytes != rb || len < sizeof(h) + fb + 2 * rb)
-    return fail(LBM_EINVAL, "checkpoint does not match this context (lattice, size, storage or geometry)");
+      h.nz != c->nz || h.n_list != c->n_list || h.fbytes != fb || h.rbytes != rb || int(h.model) != c->model ||
+      h.ubytes != ub || len < sizeof(h) + fb + 2 * rb + ub)
+    return fail(LBM_EINVAL, "checkpoint does not match this context (lattice, size, storage, geometry or collision model)");
   const char* p = static_cast<const char*>(buf);
   CK(cudaStreamSynchronize(c->stream));
   CK(cudaMemcpyAsync(c->f.p, p + sizeof(h), fb, cudaMemcpyDefault, c->stream));
   CK(cudaMemcpyAsync(c->ref0.p, p + sizeof(h) + fb, rb, cudaMemcpyDefault, c->stream));
   CK(cudaMemcpyAsync(c->ref1.p, p + sizeof(h) + fb + rb, rb, cudaMemcpyDefault, c->stream));
-  CK(cudaStreamSynchronize(c->stream));
   c->t = h.t;
+  if (ub) {
+    CK(c->uvel0.ensure(ub));
+    CK(c->uvel1.ensure(ub));
+    void* dst = (c->t & 1) ? c->uvel1.p : c->uvel0.p;
+    CK(cudaMemcpyAsync(dst, p + sizeof(h) + fb + 2 * rb, ub, cudaMemcpyDefault, c->stream));
+    c->uvel_stale = false;
+  }
+  CK(cudaStreamSynchronize(c->stream));
   c->adj_t0 = -1;
+  return LBM_OK;
+}
+
+// Collision model: LBM_BGK, or LBM_HRR with hybridisation factor sigma in [0, 1].
+int lbm_set_collision(lbm_ctx* c, int model, double sigma) {
+  if (!c) return fail(LBM_EINVAL, "null context");
+  if (model != LBM_BGK && model != LBM_HRR) return fail(LBM_EINVAL, "model must be LBM_BGK or LBM_HRR");
+  if (!(sigma >= 0.0 && sigma <= 1.0)) return fail(LBM_EINVAL, "sigma must lie in [0, 1]");
+  c->model = model;
+  c->sigma = sigma;
+  c->uvel_stale = true;
+  if (model == LBM_BGK) {
+    c->uvel0.release();
+    c->uvel1.release();
+  }
   return LBM_OK;
 }
 
 // ---- adjoint ---------------------------------------------------------------------------------------------
 static int adj_check(lbm_ctx* c, int xa, int xb, double* wa, double* wb, int W) {
+  if (c->model != LBM_BGK) return fail(LBM_ESTATE, "the adjoint is defined for the BGK collision only");
   if (c->wm) return fail(LBM_ESTATE, "the wall model is not differentiated; switch it off (kappa <= 0)");
   if (xa < 0 || xa >= c->nx || xb < 0 || xb >= c->nx || xa == xb) return fail(LBM_EINVAL, "objective planes out of range");
   long long na = 0, nb = 0;
@@ -1017,6 +1081,7 @@ int lbm_objective_backward(lbm_ctx* c, double* dJ_dgamma, double* dJ_duin) {
 int lbm_adjoint_step(lbm_ctx* c, const void* lam_in, void* lam_out, int dtype, double* dgamma, double* duin) {
   if (!c) return fail(LBM_EINVAL, "null context");
   if (!valid_dtype(dtype)) return fail(LBM_EINVAL, "dtype must be LBM_DTYPE_F32 or LBM_DTYPE_F64");
+  if (c->model != LBM_BGK) return fail(LBM_ESTATE, "the adjoint is defined for the BGK collision only");
   if (c->wm) return fail(LBM_ESTATE, "the wall model is not differentiated");
   if (c->t & 1) return fail(LBM_ESTATE, "the reverse step needs the state after an even number of steps");
   int rc;

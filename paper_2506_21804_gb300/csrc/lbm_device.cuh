@@ -182,6 +182,12 @@ struct Args {
   int idx32;               // 1: every population index q*stride fits in 32 bits (32-bit index arithmetic)
   int debug_stall;         // 1: the staged kernel also waits on a barrier nobody completes (tests the bounded wait)
   Param kappa, E;
+  // hybrid recursive regularised collision
+  int model;               // 0 BGK, 1 HRR
+  int hybrid;              // HRR with sigma < 1 (the finite-difference strain is needed)
+  Param sigma;             // hybridisation factor
+  const void* uvel_rd;     // C[3][N] velocity field of the previous step
+  void* uvel_wr;           // C[3][N] velocity field written by this step
 };
 
 // ---- AA-pattern slot map ------------------------------------------------------------------------------

@@ -70,6 +70,11 @@ struct Impl {
     return true;
   }
   static void step_bulk(const Args& a, int odd, cudaStream_t s) {
+    if (a.model != 0) {
+      if (odd) k_bulk_hrr<Q, S, true><<<bulk_grid(a), bulk_block(a), 0, s>>>(a);
+      else k_bulk_hrr<Q, S, false><<<bulk_grid(a), bulk_block(a), 0, s>>>(a);
+      return;
+    }
     const TmaLayout L = tma_layout(a);
     if (L.stages >= 2) {
       if (odd ? launch_tma<true>(a, L, s) : launch_tma<false>(a, L, s)) return;
@@ -93,6 +98,11 @@ struct Impl {
   static void step_list(const Args& a, int odd, cudaStream_t s) {
     const int nj = a.lsub ? a.n_sub : a.n_list;
     if (nj <= 0) return;
+    if (a.model != 0) {
+      if (odd) k_list<Q, S, true, true><<<blocks_for(nj, LIST_THREADS), LIST_THREADS, 0, s>>>(a);
+      else k_list<Q, S, false, true><<<blocks_for(nj, LIST_THREADS), LIST_THREADS, 0, s>>>(a);
+      return;
+    }
     if (odd) k_list<Q, S, true><<<blocks_for(nj, LIST_THREADS), LIST_THREADS, 0, s>>>(a);
     else k_list<Q, S, false><<<blocks_for(nj, LIST_THREADS), LIST_THREADS, 0, s>>>(a);
   }

@@ -3,6 +3,7 @@
 #pragma once
 
 #include "lbm_device.cuh"
+#include "lbm_hrr.cuh"
 #include "lbm_adjoint.cuh"
 #include "lbm_ops.h"
 
@@ -274,8 +275,8 @@ __device__ __forceinline__ void apply_bc(const Args& a, int kind, int y, int z, 
 
 // Collision of a cell of any non-solid kind (boundary reconstruction first, then fluid or wall
 // model). k = list entry for reference-velocity bookkeeping (-1: not a list cell).
-template <int Q, class C>
-__device__ __forceinline__ void collide_any(const Args& a, int kind, uint8_t t, int y, int z, long long n, int k, C* h) {
+template <int Q, class C, bool HRR = false>
+__device__ __forceinline__ void collide_any(const Args& a, int kind, uint8_t t, int x, int y, int z, long long n, int k, C* h) {
   apply_bc<Q, C>(a, kind, y, z, h);
   C rho, urx, ury, urz;
   if (kind == K_WALL && a.wm) {
@@ -283,7 +284,14 @@ __device__ __forceinline__ void collide_any(const Args& a, int kind, uint8_t t, 
     const int r = a.wref[k];
     const C* ur = r >= 0 ? cptr<C>(a.ref_rd) + 3 * (long long)r : nullptr;
     C z3[3] = {C(0), C(0), C(0)};
-    collide_wall<Q, C>(h, a, nr, cptr<C>(a.wyw)[k], r >= 0 ? ur : z3, r >= 0, rho, urx, ury, urz);
+    C ws[WALL_STATE];
+    wall_state<C>(a, nr, cptr<C>(a.wyw)[k], r >= 0 ? ur : z3, r >= 0, ws);
+    if constexpr (HRR) collide_wall_hrr<Q, C>(h, a, ws, rho, urx, ury, urz);
+    else collide_wall_state<Q, C>(h, a, ws, rho, urx, ury, urz);
+  } else if constexpr (HRR) {
+    C S[6] = {C(0), C(0), C(0), C(0), C(0), C(0)};
+    if (a.hybrid) strain_fd<C>(a, x, y, z, n, (t & T_NEAR) != 0, S);
+    collide_hrr<Q, C>(h, gamma_at<C>(a, n), a, S, rho, urx, ury, urz);
   } else {
     collide_fluid<Q, C>(h, gamma_at<C>(a, n), a, rho, urx, ury, urz);
   }
@@ -291,6 +299,7 @@ __device__ __forceinline__ void collide_any(const Args& a, int kind, uint8_t t, 
     C* w = cptr<C>(a.ref_wr) + 3 * (long long)k;
     w[0] = urx; w[1] = ury; w[2] = urz;
   }
+  if constexpr (HRR) record_velocity<C>(a, n, urx, ury, urz);
   if (!finite_all<C>(rho, urx, ury, urz)) atomicOr(a.status, ST_NAN);
 }
 
@@ -298,7 +307,7 @@ __device__ __forceinline__ void collide_any(const Args& a, int kind, uint8_t t, 
 // A list cell updated inside the interior kernel (fused mode): its entry gives the slot codes, the
 // precomputed wall-model state and the reference-buffer position. Inlet/outlet lanes add their
 // boundary reconstruction before the collision; the collision itself is shared with plain lanes.
-template <int Q, class S, bool ODD>
+template <int Q, class S, bool ODD, bool HRR = false>
 __device__ __forceinline__ void list_cell_inline(const Args& a, S* f, int x, int y, int z, long long n, uint8_t t) {
   using C = typename Codec<S>::C;
   const int k = a.lidx[n];
@@ -313,8 +322,19 @@ __device__ __forceinline__ void list_cell_inline(const Args& a, S* f, int x, int
   }
   if (kind == K_INFLOW || kind == K_OUTFLOW) apply_bc<Q, C>(a, kind, y, z, h);
   C rho, urx, ury, urz;
-  if (kind == K_WALL && a.wm) collide_wall_state<Q, C>(h, a, cptr<C>(a.wst) + (long long)WALL_STATE * k, rho, urx, ury, urz);
-  else collide_fluid<Q, C>(h, gamma_at<C>(a, n), a, rho, urx, ury, urz);
+  if constexpr (HRR) {
+    if (kind == K_WALL && a.wm) {
+      collide_wall_hrr<Q, C>(h, a, cptr<C>(a.wst) + (long long)WALL_STATE * k, rho, urx, ury, urz);
+    } else {
+      C S[6] = {C(0), C(0), C(0), C(0), C(0), C(0)};
+      if (a.hybrid) strain_fd<C>(a, x, y, z, n, (t & T_NEAR) != 0, S);
+      collide_hrr<Q, C>(h, gamma_at<C>(a, n), a, S, rho, urx, ury, urz);
+    }
+    record_velocity<C>(a, n, urx, ury, urz);
+  } else {
+    if (kind == K_WALL && a.wm) collide_wall_state<Q, C>(h, a, cptr<C>(a.wst) + (long long)WALL_STATE * k, rho, urx, ury, urz);
+    else collide_fluid<Q, C>(h, gamma_at<C>(a, n), a, rho, urx, ury, urz);
+  }
   if (t & T_REF) {
     C* w = cptr<C>(a.ref_wr) + 3 * (long long)k;
     w[0] = urx; w[1] = ury; w[2] = urz;
@@ -335,18 +355,25 @@ template <int Q, class S, bool ODD> constexpr int bulk_min_blocks() {
   return sizeof(S) == 8 ? 1 : (Q == 19 ? (ODD ? 8 : 10) : (ODD ? 6 : 8));
 }
 
-template <int Q, class S, bool ODD>
+template <int Q, class S, bool ODD, bool HRR = false>
 __device__ __forceinline__ void bulk_cell(const Args& a, S* f, int x, int y, int z, long long n, uint8_t t) {
   using C = typename Codec<S>::C;
   if (t & (T_LIST | T_KIND)) {
-    if ((t & T_INLINE) && a.fuse) list_cell_inline<Q, S, ODD>(a, f, x, y, z, n, t);
+    if ((t & T_INLINE) && a.fuse) list_cell_inline<Q, S, ODD, HRR>(a, f, x, y, z, n, t);
     return;
   }
   const bool near = (t & T_NEAR) != 0;
   C h[Q];
   gather<Q, S, ODD ? LOAD_SLOTS : LOAD_LOCAL>(a, f, x, y, z, n, near, h);
   C rho, urx, ury, urz;
-  collide_fluid<Q, C>(h, gamma_at<C>(a, n), a, rho, urx, ury, urz);
+  if constexpr (HRR) {
+    C S6[6] = {C(0), C(0), C(0), C(0), C(0), C(0)};
+    if (a.hybrid) strain_fd<C>(a, x, y, z, n, near, S6);
+    collide_hrr<Q, C>(h, gamma_at<C>(a, n), a, S6, rho, urx, ury, urz);
+    record_velocity<C>(a, n, urx, ury, urz);
+  } else {
+    collide_fluid<Q, C>(h, gamma_at<C>(a, n), a, rho, urx, ury, urz);
+  }
   if (!finite_all<C>(rho, urx, ury, urz)) atomicOr(a.status, ST_NAN);
   scatter<Q, S, ODD ? STORE_SLOTS : STORE_MIRROR>(a, f, x, y, z, n, near, h);
 }
@@ -358,6 +385,16 @@ __global__ void __launch_bounds__(BULK_THREADS, (bulk_min_blocks<Q, S, ODD>())) 
   if (x >= a.nx || y >= a.ny) return;
   const long long n = x + (long long)y * a.nx + (long long)z * a.nxy;
   bulk_cell<Q, S, ODD>(a, static_cast<S*>(a.f), x, y, z, n, a.type[n]);
+}
+// Interior kernel of the HRR collision (same cell set and slot handling as k_bulk).
+template <int Q, class S, bool ODD>
+__global__ void __launch_bounds__(BULK_THREADS) k_bulk_hrr(const Args a) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= a.nx || y >= a.ny) return;
+  const long long n = x + (long long)y * a.nx + (long long)z * a.nxy;
+  bulk_cell<Q, S, ODD, true>(a, static_cast<S*>(a.f), x, y, z, n, a.type[n]);
 }
 
 // ---- 16-bit storage, two cells per thread -------------------------------------------------------------
@@ -501,7 +538,7 @@ __global__ void k_wall_state(const Args a) {
 
 // Boundary-list kernel, one thread per list entry: every entry, or in fused mode the entries not
 // handled inline (Args::lsub: INFLOW/OUTFLOW entries and list cells in sparse x-groups).
-template <int Q, class S, bool ODD>
+template <int Q, class S, bool ODD, bool HRR = false>
 __global__ void __launch_bounds__(LIST_THREADS) k_list(const Args a) {
   using C = typename Codec<S>::C;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -517,11 +554,11 @@ __global__ void __launch_bounds__(LIST_THREADS) k_list(const Args a) {
   if constexpr (ODD) {
     const unsigned long long code = a.lcode[k];
     gather_coded<Q, S>(a, f, x, y, z, n, code, h);
-    collide_any<Q, C>(a, kind, t, y, z, n, k, h);
+    collide_any<Q, C, HRR>(a, kind, t, x, y, z, n, k, h);
     scatter_coded<Q, S>(a, f, x, y, z, n, code, h);
   } else {
     gather<Q, S, LOAD_LOCAL>(a, f, x, y, z, n, false, h);
-    collide_any<Q, C>(a, kind, t, y, z, n, k, h);
+    collide_any<Q, C, HRR>(a, kind, t, x, y, z, n, k, h);
     scatter<Q, S, STORE_MIRROR>(a, f, x, y, z, n, false, h);
   }
 }
@@ -608,13 +645,13 @@ __global__ void k_moments(const Args a, int swapped, void* rho, void* u, int dty
   const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (n >= a.N) return;
   if ((a.type[n] & T_KIND) == K_SOLID) {
-    store_out(rho, dtype, n, 0.0);
+    if (rho) store_out(rho, dtype, n, 0.0);
     for (int c = 0; c < 3; ++c) store_out(u, dtype, c * a.N + n, 0.0);
     return;
   }
   C r, uu[3];
   cell_macro<Q, S>(a, n, swapped != 0, r, uu);
-  store_out(rho, dtype, n, double(r));
+  if (rho) store_out(rho, dtype, n, double(r));
   for (int c = 0; c < 3; ++c) store_out(u, dtype, c * a.N + n, double(uu[c]));
 }
 

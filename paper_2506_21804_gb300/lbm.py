@@ -22,6 +22,7 @@ KIND_FLUID, KIND_SOLID, KIND_WALL, KIND_INFLOW, KIND_OUTFLOW = 0, 1, 2, 3, 4
 T_KIND, T_REF, T_NEAR, T_LIST = 7, 8, 16, 32
 OPT_KERNEL, OPT_DEBUG_STALL = 1, 2
 KERNEL_PLAIN, KERNEL_STAGED = 0, 2
+BGK, HRR = 0, 1
 STORAGE_NAMES = {"f64": F64, "f32": F32, "f16": F16, "bf16": BF16}
 
 _ERR_NAMES = {EINVAL: "LBM_EINVAL", ENOMEM: "LBM_ENOMEM", ECUDA: "LBM_ECUDA", ENAN: "LBM_ENAN",
@@ -44,6 +45,7 @@ SIGNATURES = {
     "lbm_destroy": (None, [_p]),
     "lbm_last_error": (ctypes.c_char_p, []),
     "lbm_set_precision": (_i, [_p, _i]),
+    "lbm_set_collision": (_i, [_p, _i, _d]),
     "lbm_set_periodic": (_i, [_p, _i, _i, _i]),
     "lbm_set_faces": (_i, [_p, _p]),
     "lbm_set_geometry": (_i, [_p, _p, _p]),
@@ -187,6 +189,11 @@ class Lattice:
     def set_wall_model(self, kappa=0.41, E=9.52):
         _check(lib().lbm_set_wall_model(self.h, float(kappa), float(E)))
 
+    def set_collision(self, model, sigma=1.0):
+        """BGK (model 0) or the hybrid recursive regularised collision (model 1, HRR) with
+        hybridisation factor sigma."""
+        _check(lib().lbm_set_collision(self.h, int(model), float(sigma)))
+
     def set_stream(self, stream):
         ptr = stream if isinstance(stream, int) else getattr(stream, "cuda_stream", 0)
         _check(lib().lbm_set_stream(self.h, ctypes.c_void_p(ptr)))
@@ -308,6 +315,8 @@ class Lattice:
             lat.set_porosity(np.asarray(w.gamma, np.float64 if storage == F64 else np.float32))
         if w.wall_model:
             lat.set_wall_model(w.kappa, w.E)
+        if getattr(w, "model", 0):
+            lat.set_collision(w.model, w.sigma)
         if init:
             dt = np.float64 if storage == F64 else np.float32
             lat.init_equilibrium(np.asarray(w.rho0, dt), np.asarray(w.u0, dt))

@@ -11,7 +11,7 @@ import pytest
 
 from oracle import oracle as O
 from paper_2506_21804_gb300 import inputs as I
-from tests.helpers import oracle_from, rel_l2
+from tests.helpers import oracle_from, rel_l2, small_cases, with_features
 
 pytestmark = pytest.mark.gpu
 
@@ -29,31 +29,6 @@ def _cuda():
 
 def gpu_from(w, storage):
     return lbm.Lattice.from_workload(w, storage=storage)
-
-
-def small_cases(q=19):
-    return [
-        I.random_box(9, 7, 6, seed=1, q=q, solid_frac=0.15, tau=0.62, cs=0.12, faces=(0, 0, 0, 0, 0, 0)),
-        I.random_box(10, 7, 5, seed=2, q=q, solid_frac=0.1, tau=0.55, cs=0.1, faces=(3, 3, 2, 2, 1, 2),
-                     inflow=True, outflow=True),
-        I.random_box(8, 6, 7, seed=3, q=q, solid_frac=0.2, tau=0.8, cs=0.0, faces=(2, 2, 2, 2, 2, 2)),
-        I.random_box(33, 5, 4, seed=4, q=q, solid_frac=0.05, tau=0.7, cs=0.15, faces=(1, 1, 2, 2, 0, 0)),
-        I.canopy(nx=40, ny=24, nz=20, q=q, n_buildings=6, seed=2506, domain=(200, 24, 60), crop=(64, 0, 0),
-                 dtype=np.float64),
-        I.channel(nx=16, ny=14, nz=6, q=q, noise=0.05, seed=5, dtype=np.float64),
-        I.duct(n=10, q=q, u_in=0.03, tau=0.7, sigma=2.0, cs=0.1, dtype=np.float64),
-    ]
-
-
-def with_features(w):
-    """Switch on force, porosity and the wall model where the case has room for them."""
-    rng = np.random.default_rng(w.nx * 7 + w.ny)
-    if w.gamma is None and w.name.startswith("random"):
-        w.gamma = 0.7 + 0.3 * rng.random(w.N)
-    if w.name.startswith("random") and w.faces[0] != 3:
-        w.force = (2e-6, -1e-6, 5e-7)
-    w.wall_model = True
-    return w
 
 
 # ---- integer work: bit-exact ------------------------------------------------------------------------------
