@@ -156,6 +156,11 @@ struct Oracle {
   std::vector<double> F, P, Fn;
   std::vector<double> uref_prev, uref_cur;
   std::vector<double> uvel_prev, uvel_cur;  // 3N component-major: velocity field of the last step (HRR)
+  // vortex-method inlet (Sec. 2.2.2); off when vm_n == 0
+  int vm_n = 0;
+  double vm_sigma = 4.0, vm_I = 0.1;
+  uint64_t vm_seed = 0;
+  std::vector<double> uin_cur;  // inlet velocity of the current (last) step, 3 * ny * nz
   long t = 0;
   // adjoint bookkeeping
   std::vector<std::vector<double>> hist;  // stored pre-collision states S_0..S_{T-1}
@@ -701,7 +706,8 @@ void inlet_velocity(const Oracle& o, long n, double ub[3]) {
   int x, y, z;
   coords(o, n, x, y, z);
   long p = long(y) + long(o.ny) * z, pl = long(o.ny) * o.nz;
-  for (int a = 0; a < 3; ++a) ub[a] = o.uin.empty() ? 0.0 : o.uin[a * pl + p];
+  const std::vector<double>& src = o.vm_n > 0 ? o.uin_cur : o.uin;
+  for (int a = 0; a < 3; ++a) ub[a] = src.empty() ? 0.0 : src[a * pl + p];
 }
 
 double gamma_at(const Oracle& o, long n) { return o.gamma.empty() ? 1.0 : o.gamma[n]; }
@@ -733,7 +739,10 @@ void moments_of(const Oracle& o, const std::vector<double>& A, double* rho, doub
   }
 }
 
+void vm_reset(Oracle& o);
+
 void init_refs(Oracle& o) {
+  vm_reset(o);
   std::vector<double> rho(o.N), u(3 * o.N);
   moments_of(o, o.F, rho.data(), u.data());
   o.uref_prev.assign(3 * o.N, 0.0);
@@ -745,10 +754,118 @@ void init_refs(Oracle& o) {
   o.uvel_cur = u;
 }
 
+// ---- Vortex-method turbulent inlet (Sec. 2.2.2) ------------------------------------------------
+// Counter-based random numbers: the SplitMix64 output function (Steele, Lea, Flood 2014) applied to
+// seed + (1 + counter) * 0x9E3779B97F4A7C15, the top 53 bits scaled to [0, 1). Counter of vortex i,
+// component c (0: y, 1: z, 2: sign) at step t: (t * n + i) * 4 + c.
+uint64_t splitmix64_out(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+double vm_uniform(uint64_t seed, uint64_t counter) {
+  const uint64_t r = splitmix64_out(seed + (counter + 1) * 0x9E3779B97F4A7C15ull);
+  return double(r >> 11) * (1.0 / 9007199254740992.0);
+}
+
+struct Vortex { double y, z, gamma; };
+
+// Seed points of step t: positions uniform on the inlet plane [-1/2, ny - 1/2) x [-1/2, nz - 1/2)
+// (cell centres at integer coordinates), signs +-1, circulation from the turbulent kinetic energy
+// k_i = 3/2 (|u_mean(p_i)| I)^2 at the cell containing p_i:
+//   Gamma_i = 4 s_i sqrt(pi k_i A / ((6 ln 3 - 9 ln 2) n)),  A = number of INFLOW cells.
+std::vector<Vortex> vm_vortices(const Oracle& o, long t) {
+  std::vector<Vortex> v(o.vm_n);
+  long area = 0;
+  for (long n = 0; n < o.N; ++n) area += o.kind[n] == K_INFLOW;
+  const long pl = long(o.ny) * o.nz;
+  for (int i = 0; i < o.vm_n; ++i) {
+    const uint64_t base = (uint64_t(t) * uint64_t(o.vm_n) + uint64_t(i)) * 4ull;
+    const double y = -0.5 + o.ny * vm_uniform(o.vm_seed, base + 0);
+    const double z = -0.5 + o.nz * vm_uniform(o.vm_seed, base + 1);
+    const double sg = vm_uniform(o.vm_seed, base + 2) < 0.5 ? 1.0 : -1.0;
+    int iy = int(std::floor(y + 0.5)), iz = int(std::floor(z + 0.5));
+    iy = std::min(std::max(iy, 0), o.ny - 1);
+    iz = std::min(std::max(iz, 0), o.nz - 1);
+    const long p = iy + long(o.ny) * iz;
+    double um2 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+      const double ua = o.uin.empty() ? 0.0 : o.uin[a * pl + p];
+      um2 += ua * ua;
+    }
+    const double k = 1.5 * um2 * o.vm_I * o.vm_I;
+    const double gam = 4.0 * sg * std::sqrt(M_PI * k * double(area) / ((6.0 * std::log(3.0) - 9.0 * std::log(2.0)) * o.vm_n));
+    v[i] = {y, z, gam};
+  }
+  return v;
+}
+
+// In-plane velocity induced at plane position (y, z) by the vortices, inflow direction d = +x:
+//   u_v = (1/2pi) sum_i Gamma_i ((p_i - x) x d) (1 - e^{-a}) e^{-a} / |p_i - x|^2,  a = |p_i - x|^2/(2 sigma^2)
+// (reading: the vortex profile whose energy integral gives the constant 6 ln 3 - 9 ln 2 of Gamma;
+// the printed kernel has lost the sign of the exponent and the second factor). With r = p_i - x in
+// the plane, r x e_x = (0, r_z, -r_y).
+void vm_field(const std::vector<Vortex>& v, double sigma, double y, double z, double& uy, double& uz) {
+  uy = 0.0;
+  uz = 0.0;
+  for (const Vortex& q : v) {
+    const double ry = q.y - y, rz = q.z - z;
+    const double r2 = ry * ry + rz * rz;
+    if (r2 == 0.0) continue;
+    const double e = std::exp(-r2 / (2.0 * sigma * sigma));
+    const double f = q.gamma * (1.0 - e) * e / (2.0 * M_PI * r2);
+    uy += f * rz;
+    uz -= f * ry;
+  }
+}
+
+// Inlet velocity of step t: u = u_mean + u_v + u'_x e_x with the streamwise fluctuation of the
+// linear kinematic (Langevin) model, u'_x = -(u_v . grad U)/|grad U|, U the streamwise component of
+// the previous step's inlet velocity (reading of the printed cross product as this projection);
+// grad U by central differences over the plane positions, one-sided at the plane edges; u'_x = 0
+// where grad U = 0.
+void vm_update(Oracle& o, long t) {
+  const std::vector<Vortex> v = vm_vortices(o, t);
+  const long pl = long(o.ny) * o.nz;
+  std::vector<double> next(3 * pl, 0.0);
+  for (int z = 0; z < o.nz; ++z)
+    for (int y = 0; y < o.ny; ++y) {
+      const long p = y + long(o.ny) * z;
+      double uy, uz;
+      vm_field(v, o.vm_sigma, double(y), double(z), uy, uz);
+      auto U = [&](int yy, int zz) { return o.uin_cur[yy + long(o.ny) * zz]; };
+      double gy = 0.0, gz = 0.0;
+      if (o.ny > 1) {
+        if (y == 0) gy = U(1, z) - U(0, z);
+        else if (y == o.ny - 1) gy = U(y, z) - U(y - 1, z);
+        else gy = 0.5 * (U(y + 1, z) - U(y - 1, z));
+      }
+      if (o.nz > 1) {
+        if (z == 0) gz = U(y, 1) - U(y, 0);
+        else if (z == o.nz - 1) gz = U(y, z) - U(y, z - 1);
+        else gz = 0.5 * (U(y, z + 1) - U(y, z - 1));
+      }
+      const double gn = std::sqrt(gy * gy + gz * gz);
+      const double ux = gn > 0.0 ? -(uy * gy + uz * gz) / gn : 0.0;
+      const double um[3] = {o.uin.empty() ? 0.0 : o.uin[p], o.uin.empty() ? 0.0 : o.uin[pl + p],
+                            o.uin.empty() ? 0.0 : o.uin[2 * pl + p]};
+      next[p] = um[0] + ux;
+      next[pl + p] = um[1] + uy;
+      next[2 * pl + p] = um[2] + uz;
+    }
+  o.uin_cur = next;
+}
+
+void vm_reset(Oracle& o) {
+  o.uin_cur = o.uin;
+  if (o.uin_cur.empty()) o.uin_cur.assign(3L * o.ny * o.nz, 0.0);
+}
+
 // One time step: collide every non-solid cell of F into P, record the reference velocities, then
 // pull-stream P into F through the source map.
 void step_once(Oracle& o) {
   const Lat& L = o.L;
+  if (o.vm_n > 0) vm_update(o, o.t);
 #pragma omp parallel for schedule(static)
   for (long n = 0; n < o.N; ++n) {
     if (o.kind[n] == K_SOLID) {
@@ -942,7 +1059,37 @@ void orc_set_force(void* h, double fx, double fy, double fz) {
 void orc_set_inflow(void* h, const double* uin) {
   Oracle& o = *static_cast<Oracle*>(h);
   o.uin.assign(uin, uin + 3L * o.ny * o.nz);
+  vm_reset(o);
 }
+
+// Vortex-method inlet: n vortices per step (0: off), vortex size sigma (cells), turbulence intensity
+// I, random seed. The inlet field restarts from the mean profile.
+int orc_set_vortex_inlet(void* h, int n, double sigma, double I, unsigned long long seed) {
+  Oracle& o = *static_cast<Oracle*>(h);
+  if (n < 0 || !(sigma > 0.0) || !(I >= 0.0)) { g_err = "bad vortex inlet parameters"; return 1; }
+  o.vm_n = n; o.vm_sigma = sigma; o.vm_I = I; o.vm_seed = seed;
+  vm_reset(o);
+  return 0;
+}
+// Vortices of step t (3 values each: y, z, Gamma).
+void orc_vm_vortices(void* h, long long t, double* out) {
+  Oracle& o = *static_cast<Oracle*>(h);
+  std::vector<Vortex> v = vm_vortices(o, long(t));
+  for (size_t i = 0; i < v.size(); ++i) { out[3 * i] = v[i].y; out[3 * i + 1] = v[i].z; out[3 * i + 2] = v[i].gamma; }
+}
+// In-plane velocity of the given vortices (3 values each) at plane position (y, z).
+void orc_vm_field(int n, const double* vort, double sigma, double y, double z, double* out2) {
+  std::vector<Vortex> v(n);
+  for (int i = 0; i < n; ++i) v[i] = {vort[3 * i], vort[3 * i + 1], vort[3 * i + 2]};
+  vm_field(v, sigma, y, z, out2[0], out2[1]);
+}
+// Inlet velocity of the last step (3 * ny * nz, component-major).
+void orc_inflow_field(void* h, double* out) {
+  Oracle& o = *static_cast<Oracle*>(h);
+  std::memcpy(out, o.uin_cur.data(), sizeof(double) * o.uin_cur.size());
+}
+unsigned long long orc_splitmix64(unsigned long long z) { return splitmix64_out(z); }
+double orc_vm_uniform(unsigned long long seed, unsigned long long counter) { return vm_uniform(seed, counter); }
 void orc_set_outflow(void* h, double rho) { static_cast<Oracle*>(h)->rho_out = rho; }
 void orc_set_porosity(void* h, const double* g) {
   Oracle& o = *static_cast<Oracle*>(h);
@@ -1208,6 +1355,7 @@ int orc_objective_run(void* h, int T, int W, int xa, int xb, double* J) {
   Oracle& o = *static_cast<Oracle*>(h);
   if (T < 1 || W < 1 || W > T || xa < 0 || xa >= o.nx || xb < 0 || xb >= o.nx) { g_err = "bad objective args"; return 1; }
   if (o.model != 0) { g_err = "the adjoint is defined for the BGK collision only"; return 1; }
+  if (o.vm_n != 0) { g_err = "the adjoint is defined for a steady inlet only"; return 1; }
   const Lat& L = o.L;
   o.dJdS_w.assign(o.N, 0.0);
   long na = 0, nb = 0;

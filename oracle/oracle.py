@@ -51,6 +51,12 @@ def lib():
             "orc_strain_fd": (None, [_p, ctypes.c_longlong, _p]),
             "orc_get_velocity_field": (None, [_p, _p]),
             "orc_set_velocity_field": (None, [_p, _p]),
+            "orc_set_vortex_inlet": (_i, [_p, _i, _d, _d, ctypes.c_ulonglong]),
+            "orc_vm_vortices": (None, [_p, ctypes.c_longlong, _p]),
+            "orc_vm_field": (None, [_i, _p, _d, _d, _d, _p]),
+            "orc_inflow_field": (None, [_p, _p]),
+            "orc_splitmix64": (ctypes.c_ulonglong, [ctypes.c_ulonglong]),
+            "orc_vm_uniform": (_d, [ctypes.c_ulonglong, ctypes.c_ulonglong]),
             "orc_init_equilibrium": (None, [_p, _p, _p]),
             "orc_set_populations": (None, [_p, _p]),
             "orc_get_populations": (None, [_p, _p]),
@@ -133,6 +139,22 @@ def collide_hrr(q, rho, ueq, uh, tau, A2):
     out = np.zeros(q)
     if lib().orc_collide_hrr(q, float(rho), _ptr(ue), _ptr(uh), float(tau), _ptr(A), _ptr(out)):
         raise ValueError("lattice must be 19 or 27")
+    return out
+
+
+def splitmix64(z):
+    return lib().orc_splitmix64(int(z) & 0xFFFFFFFFFFFFFFFF)
+
+
+def vm_uniform(seed, counter):
+    return lib().orc_vm_uniform(int(seed), int(counter))
+
+
+def vm_field(vortices, sigma, y, z):
+    """In-plane velocity (u_y, u_z) of vortices (rows y, z, Gamma) at plane position (y, z)."""
+    v = _f64(np.asarray(vortices).reshape(-1))
+    out = np.zeros(2)
+    lib().orc_vm_field(len(v) // 3, _ptr(v), float(sigma), float(y), float(z), _ptr(out))
     return out
 
 
@@ -271,6 +293,23 @@ class Oracle:
     def set_velocity_field(self, u):
         u = _f64(np.asarray(u).reshape(-1))
         lib().orc_set_velocity_field(self.h, _ptr(u))
+
+    def set_vortex_inlet(self, n, sigma=4.0, intensity=0.1, seed=0):
+        """Vortex-method inlet with n vortices per step (0: off)."""
+        self._chk(lib().orc_set_vortex_inlet(self.h, int(n), float(sigma), float(intensity), int(seed)))
+        self.vm_n = int(n)
+
+    def vortices(self, t):
+        """Vortices of step t, rows (y, z, Gamma)."""
+        n = getattr(self, "vm_n", 0)
+        out = np.zeros(3 * max(n, 1))
+        lib().orc_vm_vortices(self.h, int(t), _ptr(out))
+        return out.reshape(-1, 3)[:n]
+
+    def inflow_field(self):
+        out = np.zeros(3 * self.ny * self.nz)
+        lib().orc_inflow_field(self.h, _ptr(out))
+        return out.reshape(3, self.ny * self.nz)
 
     def _bgk_only(self):
         if self.collision()[0] != 0:
