@@ -1095,6 +1095,33 @@ void orc_set_porosity(void* h, const double* g) {
   Oracle& o = *static_cast<Oracle*>(h);
   if (g) o.gamma.assign(g, g + o.N); else o.gamma.clear();
 }
+
+// Forchheimer permeability (Sec. 2.1): K = mu Q / (A (dP/L - rho Q^2 / (K_beta A^2))); K_beta = inf
+// drops the inertial term (Darcy). Returns NaN when the bracket is not positive.
+double orc_forchheimer_k(double mu, double Q, double A, double L, double dP, double rho, double Kbeta) {
+  const double inertial = std::isinf(Kbeta) ? 0.0 : rho / Kbeta * Q * Q / (A * A);
+  const double br = dP / L - inertial;
+  if (!(br > 0.0)) return NAN;
+  return mu * Q / (A * br);
+}
+
+// Porosity from the permeability K of every cell (lattice units, K = dx^2-scaled; +inf = fluid):
+// the lattice porosity of Eq. lattice_porosity, d = 1 - dx^2 nu tau / K with dx = 1, nu = (tau - 1/2)/3
+// the molecular viscosity and tau the molecular relaxation time, read as the fluid fraction
+// gamma = d (gamma = 1 for K = inf) clamped to [0, 1].
+void orc_set_permeability(void* h, const double* K) {
+  Oracle& o = *static_cast<Oracle*>(h);
+  const double nu = CS2 * (o.tau0 - 0.5);
+  o.gamma.assign(o.N, 1.0);
+  for (long n = 0; n < o.N; ++n) {
+    double g = std::isinf(K[n]) ? 1.0 : 1.0 - nu * o.tau0 / K[n];
+    o.gamma[n] = std::min(1.0, std::max(0.0, g));
+  }
+}
+void orc_get_porosity(void* h, double* g) {
+  Oracle& o = *static_cast<Oracle*>(h);
+  for (long n = 0; n < o.N; ++n) g[n] = o.gamma.empty() ? 1.0 : o.gamma[n];
+}
 void orc_set_wall_model(void* h, int on, double kappa, double E) {
   Oracle& o = *static_cast<Oracle*>(h);
   o.wm = on != 0; o.kappa = kappa; o.E = E;

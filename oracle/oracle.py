@@ -52,6 +52,9 @@ def lib():
             "orc_get_velocity_field": (None, [_p, _p]),
             "orc_set_velocity_field": (None, [_p, _p]),
             "orc_set_vortex_inlet": (_i, [_p, _i, _d, _d, ctypes.c_ulonglong]),
+            "orc_forchheimer_k": (_d, [_d, _d, _d, _d, _d, _d, _d]),
+            "orc_set_permeability": (None, [_p, _p]),
+            "orc_get_porosity": (None, [_p, _p]),
             "orc_vm_vortices": (None, [_p, ctypes.c_longlong, _p]),
             "orc_vm_field": (None, [_i, _p, _d, _d, _d, _p]),
             "orc_inflow_field": (None, [_p, _p]),
@@ -140,6 +143,10 @@ def collide_hrr(q, rho, ueq, uh, tau, A2):
     if lib().orc_collide_hrr(q, float(rho), _ptr(ue), _ptr(uh), float(tau), _ptr(A), _ptr(out)):
         raise ValueError("lattice must be 19 or 27")
     return out
+
+
+def forchheimer_k(mu, Q, A, L, dP, rho, Kbeta=float("inf")):
+    return lib().orc_forchheimer_k(mu, Q, A, L, dP, rho, Kbeta)
 
 
 def splitmix64(z):
@@ -265,6 +272,16 @@ class Oracle:
     def set_porosity(self, gamma):
         g = _f64(None if gamma is None else np.asarray(gamma).reshape(-1))
         lib().orc_set_porosity(self.h, _ptr(g))
+
+    def set_permeability(self, K):
+        """Porosity from the per-cell permeability K (lattice units; inf = fluid)."""
+        k = _f64(np.asarray(K).reshape(-1))
+        lib().orc_set_permeability(self.h, _ptr(k))
+
+    def porosity(self):
+        g = np.zeros(self.N)
+        lib().orc_get_porosity(self.h, _ptr(g))
+        return g
 
     def set_wall_model(self, on=True, kappa=0.41, E=9.52):
         lib().orc_set_wall_model(self.h, int(on), kappa, E)
