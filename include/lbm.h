@@ -93,11 +93,33 @@ int lbm_set_force(lbm_ctx* ctx, double fx, double fy, double fz);
 /* Inlet velocity of INFLOW cells, 3*ny*nz values (inward normal +x). */
 int lbm_set_inflow(lbm_ctx* ctx, const float* u_in);
 int lbm_set_inflow_ex(lbm_ctx* ctx, const void* u_in, int dtype);
+/* Vortex-method turbulent inlet (Sec. 2.2.2). Before every step, n seed points are drawn uniformly
+ * on the inlet plane (counter-based SplitMix64 random numbers keyed by seed and the step counter,
+ * so a run is reproducible step by step); vortex i has circulation
+ * Gamma_i = 4 s_i sqrt(pi k_i A / ((6 ln 3 - 9 ln 2) n)), k_i = 3/2 (|u_mean(p_i)| intensity)^2,
+ * A = number of INFLOW cells, random sign s_i; the inlet velocity of the step is the mean profile of
+ * lbm_set_inflow plus the in-plane vortex field (profile (1 - e^-a) e^-a / r^2, a = r^2/(2 sigma^2))
+ * plus the streamwise fluctuation -(u_v . grad U)/|grad U| with U the streamwise inlet velocity of
+ * the previous step. n = 0 switches it off. The inlet field restarts from the mean profile on
+ * lbm_set_inflow, lbm_set_vortex_inlet and every state (re)initialisation, and is part of lbm_save.
+ * The adjoint calls return LBM_ESTATE while it is on. Errors: LBM_EINVAL for n outside [0, 2^20],
+ * sigma <= 0 or intensity < 0. Device memory: 2 * 3 * ny * nz + 3 * n compute-type values. */
+int lbm_set_vortex_inlet(lbm_ctx* ctx, int n, double sigma, double intensity, unsigned long long seed);
 /* Outlet density of OUTFLOW cells (inward normal -x). */
 int lbm_set_outflow(lbm_ctx* ctx, double rho_out);
 /* Per-cell porosity gamma (N values in [0,1], 1 = fluid); NULL removes it. */
 int lbm_set_porosity(lbm_ctx* ctx, const float* gamma);
 int lbm_set_porosity_ex(lbm_ctx* ctx, const void* gamma, int dtype);
+/* Porosity from a per-cell permeability K (N values, lattice units K/dx^2; +inf = fluid): the
+ * lattice porosity of Eq. lattice_porosity, gamma = 1 - nu tau / K with nu = (tau - 1/2)/3 and tau
+ * the molecular relaxation time, read as the fluid fraction and clamped to [0, 1]; replaces any
+ * porosity set before. Errors: LBM_EINVAL for a bad pointer or dtype. */
+int lbm_set_permeability(lbm_ctx* ctx, const float* K);
+int lbm_set_permeability_ex(lbm_ctx* ctx, const void* K, int dtype);
+/* Forchheimer permeability of a sample (Sec. 2.1): K = mu Q / (A (dP/L - rho Q^2 / (K_beta A^2))),
+ * K_beta = +inf for Darcy's law. Any consistent units; NaN when the bracket is not positive or
+ * A, L <= 0. No context, no device work. */
+double lbm_forchheimer_permeability(double mu, double Q, double A, double L, double dP, double rho, double K_beta);
 /* Spalding wall function on WALL cells with von Karman constant kappa and wall constant E
  * (kappa <= 0 switches it off: WALL cells then collide like fluid cells with bounce-back). */
 int lbm_set_wall_model(lbm_ctx* ctx, double kappa, double E);

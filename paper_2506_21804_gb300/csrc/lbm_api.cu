@@ -14,6 +14,8 @@
 #include "lbm_adjoint.cuh"
 #include "lbm_device.cuh"
 #include "lbm_ops.h"
+#include "lbm_vortex.h"
+#include "lbm_porous.h"
 
 using namespace lbm;
 
@@ -63,6 +65,7 @@ struct SaveHeader {
   int64_t nx, ny, nz, n_list, t;
   uint64_t fbytes, rbytes, ubytes;  // populations, one reference buffer, HRR velocity field (0: none)
   double sigma;
+  uint64_t vbytes;                  // vortex-inlet field of the last step (0: none)
 };
 }  // namespace
 
@@ -81,6 +84,11 @@ struct lbm_ctx {
   int model = LBM_BGK;  // collision model
   double sigma = 1.0;   // HRR hybridisation factor
   bool uvel_stale = true;  // the HRR velocity field must be rebuilt from the state before the next step
+  // vortex-method inlet (off when vm_n == 0)
+  int vm_n = 0;
+  double vm_sigma = 4.0, vm_I = 0.1;
+  unsigned long long vm_seed = 0;
+  int vm_which = 0;  // 0: the current inlet field is uin_a
   int device = 0;
   cudaStream_t stream = 0;
   const Ops* ops = nullptr;
@@ -90,12 +98,14 @@ struct lbm_ctx {
   DevBuf f, type, mask, wdist, gamma, uin, lcell, nsum, wref, lxyz, lcode, wnrm, wyw, ref0, ref1, status, red, redout, stage;
   DevBuf lidx, lsub, lwall, lbc, wst;
   DevBuf uvel0, uvel1;  // HRR velocity fields (step t reads uvel[t & 1], writes the other)
+  DevBuf uin_a, uin_b, vort;  // vortex inlet: current/previous inlet fields, vortex list
   int n_sub = 0, n_wall = 0, n_bc = 0;
   bool has_gamma = false, has_wdist = false;
   int n_list = 0;
   long long counts[8] = {0};  // wall, ref, inflow, outflow, solid
   std::vector<double> uin_host;
-  std::vector<uint8_t> type_host;
+  std::vector<uint8_t> type_host;  // host copy of the type bytes, valid when type_host_valid
+  bool type_host_valid = false;
   unsigned* status_h = nullptr;
   double* red_h = nullptr;
   // adjoint state
@@ -107,7 +117,7 @@ struct lbm_ctx {
   double adj_ms[3] = {0, 0, 0};
 
   ~lbm_ctx() {
-    DevBuf* all[] = {&uvel0, &uvel1, &lidx, &lsub, &lwall, &lbc, &wst, &f, &type, &mask, &wdist, &gamma, &uin, &lcell, &nsum, &wref, &lxyz, &lcode, &wnrm, &wyw, &ref0, &ref1, &status, &red,
+    DevBuf* all[] = {&uin_a, &uin_b, &vort, &uvel0, &uvel1, &lidx, &lsub, &lwall, &lbc, &wst, &f, &type, &mask, &wdist, &gamma, &uin, &lcell, &nsum, &wref, &lxyz, &lcode, &wnrm, &wyw, &ref0, &ref1, &status, &red,
                      &redout, &stage, &lamA, &lamB, &dgam, &duin, &plane};
     for (DevBuf* b : all) b->release();
     for (auto& b : ckpts) b.release();
@@ -166,7 +176,7 @@ Args make_args(const lbm_ctx* c) {
   // step t reads the reference velocities written in step t-1 and writes its own
   a.ref_rd = (c->t & 1) ? c->ref0.p : c->ref1.p;
   a.ref_wr = (c->t & 1) ? c->ref1.p : c->ref0.p;
-  a.uin = c->uin.p;
+  a.uin = c->vm_n > 0 ? (c->vm_which == 0 ? c->uin_a.p : c->uin_b.p) : c->uin.p;
   a.rho_out = c->rho_out;
   a.drho_out = c->rho_out - 1.0;
   a.wm = c->wm ? 1 : 0;
@@ -321,68 +331,98 @@ int build_geometry(lbm_ctx* c) {
     // Inline (fused-mode) choice: INFLOW/OUTFLOW cells are always updated by the interior kernel
     // (their extra work is a short reconstruction before the shared collision); WALL and reference
     // cells when their 32-cell x-group holds at least INLINE_MIN list cells. Isolated WALL and
-    // reference cells stay with the boundary-list kernel.
+    // reference cells stay with the boundary-list kernel. Then the sub-lists of the boundary list.
     constexpr int INLINE_MIN = 8;
-    std::vector<long long> cells(c->n_list);
-    std::vector<uint8_t> tl(c->N);
-    if (c->n_list) CK(cudaMemcpyAsync(cells.data(), c->lcell.p, c->n_list * sizeof(long long), cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(tl.data(), c->type.p, c->N, cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    for (long long row = 0; row < (long long)c->ny * c->nz; ++row) {
-      const long long base = row * c->nx;
-      for (int g0 = 0; g0 < c->nx; g0 += 32) {
-        const int g1 = std::min(c->nx, g0 + 32);
-        int cnt = 0;
-        for (int x = g0; x < g1; ++x) cnt += (tl[base + x] & T_LIST) != 0;
-        for (int x = g0; x < g1; ++x) {
-          uint8_t& t = tl[base + x];
-          const int kind = t & T_KIND;
-          if (!(t & T_LIST)) continue;
-          if (kind == K_INFLOW || kind == K_OUTFLOW || cnt >= INLINE_MIN) t |= T_INLINE;
-        }
+    uint8_t* type = static_cast<uint8_t*>(c->type.p);
+    const long long* lcell = static_cast<const long long*>(c->lcell.p);
+    geo_inline_mark(g, type, INLINE_MIN, s);
+    const int sb = std::max(1, geo_sub_blocks(c->n_list));
+    DevBuf sc;
+    CK(sc.ensure((size_t)sb * 3 * sizeof(int)));
+    std::vector<int> hs(3 * (size_t)sb, 0);
+    if (c->n_list) {
+      geo_sub_count(type, lcell, c->n_list, static_cast<int*>(sc.p), s);
+      CK(cudaMemcpyAsync(hs.data(), sc.p, hs.size() * sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+    }
+    int tot[3] = {0, 0, 0};
+    for (int b = 0; b < sb; ++b)
+      for (int k = 0; k < 3; ++k) {
+        const int v = hs[3 * b + k];
+        hs[3 * b + k] = tot[k];
+        tot[k] += v;
       }
+    c->n_sub = tot[0]; c->n_wall = tot[1]; c->n_bc = tot[2];
+    CK(c->lsub.ensure(std::max<size_t>(1, (size_t)tot[0]) * sizeof(int)));
+    CK(c->lwall.ensure(std::max<size_t>(1, (size_t)tot[1]) * sizeof(int)));
+    CK(c->lbc.ensure(std::max<size_t>(1, (size_t)tot[2]) * sizeof(int)));
+    if (c->n_list) {
+      CK(cudaMemcpyAsync(sc.p, hs.data(), hs.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+      geo_sub_write(type, lcell, c->n_list, static_cast<const int*>(sc.p), static_cast<int*>(c->lsub.p),
+                    static_cast<int*>(c->lwall.p), static_cast<int*>(c->lbc.p), s);
     }
-    CK(cudaMemcpyAsync(c->type.p, tl.data(), c->N, cudaMemcpyHostToDevice, s));
-    std::vector<int> sub, wall, bc;
-    for (int k = 0; k < c->n_list; ++k) {
-      const uint8_t t = tl[cells[k]];
-      if (!(t & T_INLINE)) sub.push_back(k);
-      else if ((t & T_KIND) == K_WALL) wall.push_back(k);
-      if ((t & T_KIND) == K_INFLOW || (t & T_KIND) == K_OUTFLOW) bc.push_back(k);
-    }
-    c->n_bc = int(bc.size());
-    CK(c->lbc.ensure(std::max<size_t>(1, bc.size()) * sizeof(int)));
-    if (!bc.empty()) CK(cudaMemcpyAsync(c->lbc.p, bc.data(), bc.size() * sizeof(int), cudaMemcpyHostToDevice, s));
-    c->n_sub = int(sub.size());
-    c->n_wall = int(wall.size());
-    CK(c->lsub.ensure(std::max<size_t>(1, sub.size()) * sizeof(int)));
-    CK(c->lwall.ensure(std::max<size_t>(1, wall.size()) * sizeof(int)));
-    if (!sub.empty()) CK(cudaMemcpyAsync(c->lsub.p, sub.data(), sub.size() * sizeof(int), cudaMemcpyHostToDevice, s));
-    if (!wall.empty()) CK(cudaMemcpyAsync(c->lwall.p, wall.data(), wall.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    // cell-kind counters
+    DevBuf kc;
+    CK(kc.ensure(5 * sizeof(unsigned long long)));
+    geo_count_kinds(type, c->N, static_cast<unsigned long long*>(kc.p), s);
+    unsigned long long hk[5];
+    CK(cudaMemcpyAsync(hk, kc.p, sizeof(hk), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    CK(cudaGetLastError());
+    for (int i = 0; i < 5; ++i) c->counts[i] = (long long)hk[i];
+    sc.release();
+    kc.release();
   }
-  // host copy of the type bytes and counters
-  c->type_host.resize(c->N);
-  CK(cudaMemcpyAsync(c->type_host.data(), c->type.p, c->N, cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
   counts.release();
-  long long nw = 0, nr = 0, ni = 0, no = 0, ns = 0;
-  for (long long n = 0; n < c->N; ++n) {
-    const uint8_t t = c->type_host[n];
-    const int k = t & T_KIND;
-    nw += k == K_WALL; ni += k == K_INFLOW; no += k == K_OUTFLOW; ns += k == K_SOLID;
-    nr += (t & T_REF) != 0;
-  }
-  c->counts[0] = nw; c->counts[1] = nr; c->counts[2] = ni; c->counts[3] = no; c->counts[4] = ns;
+  c->type_host_valid = false;
   return LBM_OK;
+}
+
+// Host copy of the type bytes (fetched on first use after a geometry change).
+const std::vector<uint8_t>& host_types(lbm_ctx* c) {
+  if (!c->type_host_valid) {
+    c->type_host.resize(c->N);
+    cudaMemcpyAsync(c->type_host.data(), c->type.p, c->N, cudaMemcpyDeviceToHost, c->stream);
+    cudaStreamSynchronize(c->stream);
+    c->type_host_valid = true;
+  }
+  return c->type_host;
 }
 
 // One time step: in fused mode the wall-model states of the WALL entries first, then the interior
 // kernel, then the boundary-list kernel. Events (optional) bracket the interior kernel.
 int fill_uvel(lbm_ctx* c);
 
+// Vortex inlet: the inlet field restarts from the mean profile.
+int vm_reset(lbm_ctx* c) {
+  if (c->vm_n <= 0) return LBM_OK;
+  const size_t pb = 3 * (size_t)c->ny * c->nz * c->ops->celem;
+  CK(c->uin_a.ensure(pb));
+  CK(c->uin_b.ensure(pb));
+  CK(c->vort.ensure(3 * (size_t)c->vm_n * c->ops->celem));
+  CK(cudaMemcpyAsync(c->uin_a.p, c->uin.p, pb, cudaMemcpyDeviceToDevice, c->stream));
+  c->vm_which = 0;
+  return LBM_OK;
+}
+
+// Vortex inlet: the inlet field of step t from the vortices of step t and the previous field.
+void vm_step(lbm_ctx* c) {
+  VmArgs v{};
+  v.ny = c->ny; v.nz = c->nz; v.n = c->vm_n;
+  v.sigma = c->vm_sigma; v.I = c->vm_I; v.seed = c->vm_seed; v.t = c->t;
+  v.area = c->counts[2];
+  v.gden = 6.0 * std::log(3.0) - 9.0 * std::log(2.0);
+  v.mean = c->uin.p;
+  v.prev = c->vm_which == 0 ? c->uin_a.p : c->uin_b.p;
+  v.cur = c->vm_which == 0 ? c->uin_b.p : c->uin_a.p;
+  v.vort = c->vort.p;
+  vm_update(v, c->ops->celem, c->stream);
+  c->vm_which ^= 1;
+}
+
 void launch_step(lbm_ctx* c, cudaEvent_t before_bulk = nullptr, cudaEvent_t after_bulk = nullptr) {
   if (c->model == LBM_HRR && c->uvel_stale) fill_uvel(c);
+  if (c->vm_n > 0) vm_step(c);
   const Args a = make_args(c);
   const int odd = int(c->t & 1);
   if (a.fuse && a.wm) c->ops->wall_pass(a, c->stream);
@@ -396,6 +436,7 @@ void launch_step(lbm_ctx* c, cudaEvent_t before_bulk = nullptr, cudaEvent_t afte
 // State to rest (f = w), step counter 0, reference buffers from that state.
 int reset_state(lbm_ctx* c) {
   c->uvel_stale = true;
+  if (vm_reset(c) != LBM_OK) return LBM_ECUDA;
   CK(cudaMemsetAsync(c->f.p, 0, (size_t)c->q * c->stride * c->ops->elem, c->stream));
   c->t = 0;
   c->adj_t0 = -1;
@@ -421,6 +462,7 @@ int fill_uvel(lbm_ctx* c) {
 
 int fill_refs(lbm_ctx* c) {
   c->uvel_stale = true;
+  if (vm_reset(c) != LBM_OK) return LBM_ECUDA;
   Args a = make_args(c);
   const int sw = int(c->t & 1);
   c->ops->ref_fill(a, sw, c->ref0.p, c->stream);
@@ -524,6 +566,7 @@ int lbm_set_precision(lbm_ctx* c, int storage) {
   if (c->has_gamma && (rc = upload_compute(c, c->gamma, g.data(), LBM_DTYPE_F64, c->N)) != LBM_OK) return rc;
   c->wnrm.release(); c->wyw.release(); c->ref0.release(); c->ref1.release();
   c->uvel0.release(); c->uvel1.release();
+  c->uin_a.release(); c->uin_b.release(); c->vort.release();
   if ((rc = build_geometry(c)) != LBM_OK) return rc;
   return reset_state(c);
 }
@@ -600,7 +643,8 @@ int lbm_set_inflow_ex(lbm_ctx* c, const void* u_in, int dtype) {
     if (!std::isfinite(v) || (i < (size_t)c->ny * c->nz && v >= 1.0)) return fail(LBM_EINVAL, "u_in[%zu] = %g invalid", i, v);
     c->uin_host[i] = v;
   }
-  return upload_uin(c);
+  if ((rc = upload_uin(c)) != LBM_OK) return rc;
+  return vm_reset(c);
 }
 int lbm_set_inflow(lbm_ctx* c, const float* u_in) { return lbm_set_inflow_ex(c, u_in, LBM_DTYPE_F32); }
 
@@ -626,6 +670,25 @@ int lbm_set_porosity_ex(lbm_ctx* c, const void* gamma, int dtype) {
   return LBM_OK;
 }
 int lbm_set_porosity(lbm_ctx* c, const float* gamma) { return lbm_set_porosity_ex(c, gamma, LBM_DTYPE_F32); }
+
+int lbm_set_permeability_ex(lbm_ctx* c, const void* K, int dtype) {
+  if (!c) return fail(LBM_EINVAL, "null context");
+  if (!valid_dtype(dtype)) return fail(LBM_EINVAL, "dtype must be LBM_DTYPE_F32 or LBM_DTYPE_F64");
+  int rc;
+  if ((rc = check_ptr(c, K, "K")) != LBM_OK) return rc;
+  const size_t bytes = (size_t)c->N * dsize(dtype);
+  CK(cudaStreamSynchronize(c->stream));
+  CK(c->stage.ensure(bytes));
+  CK(cudaMemcpyAsync(c->stage.p, K, bytes, cudaMemcpyDefault, c->stream));
+  CK(c->gamma.ensure((size_t)c->N * c->ops->celem));
+  const double nu = (c->tau0 - 0.5) / 3.0;
+  porous_gamma(c->stage.p, dtype, c->gamma.p, c->ops->celem, c->N, nu * c->tau0, c->stream);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(c->stream));
+  c->has_gamma = true;
+  return LBM_OK;
+}
+int lbm_set_permeability(lbm_ctx* c, const float* K) { return lbm_set_permeability_ex(c, K, LBM_DTYPE_F32); }
 
 int lbm_set_wall_model(lbm_ctx* c, double kappa, double E) {
   if (!c) return fail(LBM_EINVAL, "null context");
@@ -820,7 +883,8 @@ int lbm_debug_dump(lbm_ctx* c, int which, int64_t* out, size_t count) {
   }
   if (count < need) return fail(LBM_EINVAL, "output holds %zu values, %zu needed", count, need);
   if (which == 0) {
-    for (long long n = 0; n < c->N; ++n) out[n] = c->type_host[n];
+    const std::vector<uint8_t>& th = host_types(c);
+    for (long long n = 0; n < c->N; ++n) out[n] = th[n];
     return LBM_OK;
   }
   if (which == 1) {
@@ -852,7 +916,8 @@ int lbm_save(lbm_ctx* c, void* buf, size_t* len) {
   const size_t fb = (size_t)c->q * c->stride * c->ops->elem;
   const size_t rb = std::max<size_t>(1, (size_t)c->n_list) * 3 * c->ops->celem;
   const size_t ub = c->model == LBM_HRR ? 3 * (size_t)c->N * c->ops->celem : 0;
-  const size_t total = sizeof(SaveHeader) + fb + 2 * rb + ub;
+  const size_t vb = c->vm_n > 0 ? 3 * (size_t)c->ny * c->nz * c->ops->celem : 0;
+  const size_t total = sizeof(SaveHeader) + fb + 2 * rb + ub + vb;
   if (!buf) {
     *len = total;
     return LBM_OK;
@@ -865,7 +930,7 @@ int lbm_save(lbm_ctx* c, void* buf, size_t* len) {
   SaveHeader h{};
   h.magic = SAVE_MAGIC; h.q = c->q; h.storage = c->storage; h.model = c->model;
   h.nx = c->nx; h.ny = c->ny; h.nz = c->nz; h.n_list = c->n_list; h.t = c->t;
-  h.fbytes = fb; h.rbytes = rb; h.ubytes = ub; h.sigma = c->sigma;
+  h.fbytes = fb; h.rbytes = rb; h.ubytes = ub; h.sigma = c->sigma; h.vbytes = vb;
   char* p = static_cast<char*>(buf);
   std::memcpy(p, &h, sizeof(h));
   CK(cudaMemcpyAsync(p + sizeof(h), c->f.p, fb, cudaMemcpyDefault, c->stream));
@@ -874,6 +939,10 @@ int lbm_save(lbm_ctx* c, void* buf, size_t* len) {
   if (ub) {
     const void* src = (c->t & 1) ? c->uvel1.p : c->uvel0.p;
     CK(cudaMemcpyAsync(p + sizeof(h) + fb + 2 * rb, src, ub, cudaMemcpyDefault, c->stream));
+  }
+  if (vb) {
+    const void* src = c->vm_which == 0 ? c->uin_a.p : c->uin_b.p;
+    CK(cudaMemcpyAsync(p + sizeof(h) + fb + 2 * rb + ub, src, vb, cudaMemcpyDefault, c->stream));
   }
   CK(cudaStreamSynchronize(c->stream));
   *len = total;
@@ -888,9 +957,10 @@ int lbm_load(lbm_ctx* c, const void* buf, size_t len) {
   const size_t fb = (size_t)c->q * c->stride * c->ops->elem;
   const size_t rb = std::max<size_t>(1, (size_t)c->n_list) * 3 * c->ops->celem;
   const size_t ub = c->model == LBM_HRR ? 3 * (size_t)c->N * c->ops->celem : 0;
+  const size_t vb = c->vm_n > 0 ? 3 * (size_t)c->ny * c->nz * c->ops->celem : 0;
   if (h.magic != SAVE_MAGIC || int(h.q) != c->q || int(h.storage) != c->storage || h.nx != c->nx || h.ny != c->ny ||
       h.nz != c->nz || h.n_list != c->n_list || h.fbytes != fb || h.rbytes != rb || int(h.model) != c->model ||
-      h.ubytes != ub || len < sizeof(h) + fb + 2 * rb + ub)
+      h.ubytes != ub || h.vbytes != vb || len < sizeof(h) + fb + 2 * rb + ub + vb)
     return fail(LBM_EINVAL, "checkpoint does not match this context (lattice, size, storage, geometry or collision model)");
   const char* p = static_cast<const char*>(buf);
   CK(cudaStreamSynchronize(c->stream));
@@ -905,8 +975,31 @@ int lbm_load(lbm_ctx* c, const void* buf, size_t len) {
     CK(cudaMemcpyAsync(dst, p + sizeof(h) + fb + 2 * rb, ub, cudaMemcpyDefault, c->stream));
     c->uvel_stale = false;
   }
+  if (vb) {
+    int rc = vm_reset(c);
+    if (rc != LBM_OK) return rc;
+    CK(cudaMemcpyAsync(c->uin_a.p, p + sizeof(h) + fb + 2 * rb + ub, vb, cudaMemcpyDefault, c->stream));
+  }
   CK(cudaStreamSynchronize(c->stream));
   c->adj_t0 = -1;
+  return LBM_OK;
+}
+
+// Vortex-method inlet: n vortices per step (0 switches it off), vortex size sigma (cells), turbulence
+// intensity, random-number seed.
+int lbm_set_vortex_inlet(lbm_ctx* c, int n, double sigma, double intensity, unsigned long long seed) {
+  if (!c) return fail(LBM_EINVAL, "null context");
+  if (n < 0 || n > (1 << 20)) return fail(LBM_EINVAL, "n must lie in [0, 2^20]");
+  if (!(sigma > 0.0) || !std::isfinite(sigma)) return fail(LBM_EINVAL, "sigma must be > 0");
+  if (!(intensity >= 0.0) || !std::isfinite(intensity)) return fail(LBM_EINVAL, "intensity must be >= 0");
+  c->vm_n = n; c->vm_sigma = sigma; c->vm_I = intensity; c->vm_seed = seed;
+  if (n == 0) {
+    c->uin_a.release(); c->uin_b.release(); c->vort.release();
+    return LBM_OK;
+  }
+  int rc = vm_reset(c);
+  if (rc != LBM_OK) return rc;
+  CK(cudaStreamSynchronize(c->stream));
   return LBM_OK;
 }
 
@@ -928,13 +1021,15 @@ int lbm_set_collision(lbm_ctx* c, int model, double sigma) {
 // ---- adjoint ---------------------------------------------------------------------------------------------
 static int adj_check(lbm_ctx* c, int xa, int xb, double* wa, double* wb, int W) {
   if (c->model != LBM_BGK) return fail(LBM_ESTATE, "the adjoint is defined for the BGK collision only");
+  if (c->vm_n > 0) return fail(LBM_ESTATE, "the adjoint is defined for a steady inlet only");
   if (c->wm) return fail(LBM_ESTATE, "the wall model is not differentiated; switch it off (kappa <= 0)");
   if (xa < 0 || xa >= c->nx || xb < 0 || xb >= c->nx || xa == xb) return fail(LBM_EINVAL, "objective planes out of range");
   long long na = 0, nb = 0;
+  const std::vector<uint8_t>& th = host_types(c);
   for (long long n = 0; n < c->N; ++n) {
     const int x = int(n % c->nx);
     if (x != xa && x != xb) continue;
-    const int k = c->type_host[n] & T_KIND;
+    const int k = th[n] & T_KIND;
     if (k == K_SOLID) continue;
     if (k == K_INFLOW || k == K_OUTFLOW) return fail(LBM_EINVAL, "objective plane x=%d holds boundary cells", x);
     (x == xa ? na : nb)++;
@@ -1082,6 +1177,7 @@ int lbm_adjoint_step(lbm_ctx* c, const void* lam_in, void* lam_out, int dtype, d
   if (!c) return fail(LBM_EINVAL, "null context");
   if (!valid_dtype(dtype)) return fail(LBM_EINVAL, "dtype must be LBM_DTYPE_F32 or LBM_DTYPE_F64");
   if (c->model != LBM_BGK) return fail(LBM_ESTATE, "the adjoint is defined for the BGK collision only");
+  if (c->vm_n > 0) return fail(LBM_ESTATE, "the adjoint is defined for a steady inlet only");
   if (c->wm) return fail(LBM_ESTATE, "the wall model is not differentiated");
   if (c->t & 1) return fail(LBM_ESTATE, "the reverse step needs the state after an even number of steps");
   int rc;

@@ -221,6 +221,112 @@ __global__ void k_source_map(const Args a, int64_t* sdir, int64_t* scell) {
   });
 }
 
+// Inline (fused-mode) choice per 32-cell x-group of a row: INFLOW/OUTFLOW cells always; WALL and
+// reference cells when the group holds at least inline_min list cells. One thread per group.
+__global__ void k_inline_mark(const GeoArgs g, uint8_t* type, int inline_min) {
+  const int groups = (g.nx + 31) / 32;
+  const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (j >= (long long)groups * g.ny * g.nz) return;
+  const long long row = j / groups;
+  const int g0 = int(j - row * groups) * 32;
+  const int g1 = g0 + 32 < g.nx ? g0 + 32 : g.nx;
+  uint8_t* t = type + row * g.nx;
+  int cnt = 0;
+  for (int x = g0; x < g1; ++x) cnt += (t[x] & T_LIST) != 0;
+  for (int x = g0; x < g1; ++x) {
+    const uint8_t v = t[x];
+    if (!(v & T_LIST)) continue;
+    const int kind = v & T_KIND;
+    if (kind == K_INFLOW || kind == K_OUTFLOW || cnt >= inline_min) t[x] = uint8_t(v | T_INLINE);
+  }
+}
+
+// Sub-lists of the boundary list, in list order: 0 entries not updated inline, 1 inline WALL
+// entries, 2 INFLOW/OUTFLOW entries. Two passes like the list itself: per-block counts, then
+// writes at exclusive offsets (entries ranked inside a warp by ballot).
+__device__ __forceinline__ void sub_flags(const uint8_t* type, const long long* lcell, int k, int n_list, bool f[3]) {
+  f[0] = f[1] = f[2] = false;
+  if (k >= n_list) return;
+  const uint8_t t = type[lcell[k]];
+  const int kind = t & T_KIND;
+  f[0] = !(t & T_INLINE);
+  f[1] = (t & T_INLINE) && kind == K_WALL;
+  f[2] = kind == K_INFLOW || kind == K_OUTFLOW;
+}
+
+constexpr int SUB_THREADS = 256;
+
+__global__ void __launch_bounds__(SUB_THREADS) k_sub_count(const uint8_t* type, const long long* lcell, int n_list, int* counts) {
+  __shared__ int wc[SUB_THREADS / 32][3];
+  const int k = blockIdx.x * SUB_THREADS + threadIdx.x;
+  bool f[3];
+  sub_flags(type, lcell, k, n_list, f);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int c = 0; c < 3; ++c) {
+    const unsigned b = __ballot_sync(0xffffffffu, f[c]);
+    if (lane == 0) wc[w][c] = __popc(b);
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    int sum = 0;
+    for (int i = 0; i < SUB_THREADS / 32; ++i) sum += wc[i][threadIdx.x];
+    counts[3 * blockIdx.x + threadIdx.x] = sum;
+  }
+}
+
+__global__ void __launch_bounds__(SUB_THREADS) k_sub_write(const uint8_t* type, const long long* lcell, int n_list,
+                                                           const int* offsets, int* lsub, int* lwall, int* lbc) {
+  __shared__ int wo[SUB_THREADS / 32][3];
+  const int k = blockIdx.x * SUB_THREADS + threadIdx.x;
+  bool f[3];
+  sub_flags(type, lcell, k, n_list, f);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  unsigned b[3];
+  for (int c = 0; c < 3; ++c) {
+    b[c] = __ballot_sync(0xffffffffu, f[c]);
+    if (lane == 0) wo[w][c] = __popc(b[c]);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int c = 0; c < 3; ++c) {
+      int run = offsets[3 * blockIdx.x + c];
+      for (int i = 0; i < SUB_THREADS / 32; ++i) {
+        const int v = wo[i][c];
+        wo[i][c] = run;
+        run += v;
+      }
+    }
+  }
+  __syncthreads();
+  int* dst[3] = {lsub, lwall, lbc};
+  for (int c = 0; c < 3; ++c)
+    if (f[c]) dst[c][wo[w][c] + __popc(b[c] & ((1u << lane) - 1u))] = k;
+}
+
+// Counts of WALL, reference, INFLOW, OUTFLOW and SOLID cells.
+__global__ void k_count_kinds(const uint8_t* type, long long N, unsigned long long* out) {
+  __shared__ unsigned long long sc[5];
+  if (threadIdx.x < 5) sc[threadIdx.x] = 0;
+  __syncthreads();
+  unsigned long long c[5] = {0, 0, 0, 0, 0};
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N; n += (long long)gridDim.x * blockDim.x) {
+    const uint8_t t = type[n];
+    const int k = t & T_KIND;
+    c[0] += k == K_WALL;
+    c[1] += (t & T_REF) != 0;
+    c[2] += k == K_INFLOW;
+    c[3] += k == K_OUTFLOW;
+    c[4] += k == K_SOLID;
+  }
+  for (int i = 0; i < 5; ++i) {
+    unsigned long long v = c[i];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&sc[i], v);
+  }
+  __syncthreads();
+  if (threadIdx.x < 5) atomicAdd(&out[threadIdx.x], sc[threadIdx.x]);
+}
+
 __global__ void k_list_index(const long long* lcell, int n_list, int* lidx) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k < n_list) lidx[lcell[k]] = k;
@@ -273,6 +379,31 @@ void geo_source_map(const GeoArgs& g, const uint8_t* type, int64_t* sdir, int64_
   for (int f = 0; f < 6; ++f) a.face[f] = g.face[f];
   if (g.q == 19) k_source_map<19><<<nblocks(g.N, 128), 128, 0, s>>>(a, sdir, scell);
   else k_source_map<27><<<nblocks(g.N, 128), 128, 0, s>>>(a, sdir, scell);
+}
+
+void geo_inline_mark(const GeoArgs& g, uint8_t* type, int inline_min, cudaStream_t s) {
+  const long long groups = (long long)((g.nx + 31) / 32) * g.ny * g.nz;
+  k_inline_mark<<<nblocks(groups, 256), 256, 0, s>>>(g, type, inline_min);
+}
+
+int geo_sub_blocks(int n_list) { return int(nblocks(n_list, SUB_THREADS)); }
+
+void geo_sub_count(const uint8_t* type, const long long* lcell, int n_list, int* counts, cudaStream_t s) {
+  if (n_list <= 0) return;
+  k_sub_count<<<nblocks(n_list, SUB_THREADS), SUB_THREADS, 0, s>>>(type, lcell, n_list, counts);
+}
+
+void geo_sub_write(const uint8_t* type, const long long* lcell, int n_list, const int* offsets, int* lsub, int* lwall,
+                   int* lbc, cudaStream_t s) {
+  if (n_list <= 0) return;
+  k_sub_write<<<nblocks(n_list, SUB_THREADS), SUB_THREADS, 0, s>>>(type, lcell, n_list, offsets, lsub, lwall, lbc);
+}
+
+void geo_count_kinds(const uint8_t* type, long long N, unsigned long long* out, cudaStream_t s) {
+  cudaMemsetAsync(out, 0, 5 * sizeof(unsigned long long), s);
+  long long blocks = nblocks(N, 256);
+  if (blocks > 4 * 1216) blocks = 4 * 1216;
+  k_count_kinds<<<unsigned(blocks), 256, 0, s>>>(type, N, out);
 }
 
 void geo_list_index(const long long* lcell, int n_list, int* lidx, cudaStream_t s) {

@@ -59,6 +59,15 @@ void geo_list_meta(const GeoArgs&, const uint8_t* type, const long long* lcell, 
                    int* lxyz, unsigned long long* lcode, cudaStream_t);
 // list position of every cell (-1 off the list)
 void geo_list_index(const long long* lcell, int n_list, int* lidx, cudaStream_t);
+// inline (fused-mode) flags per 32-cell x-group; sub-lists of the boundary list (3 per-block counts,
+// then writes at offsets: not-inline, inline WALL, INFLOW/OUTFLOW); counts of WALL, reference,
+// INFLOW, OUTFLOW and SOLID cells
+void geo_inline_mark(const GeoArgs&, uint8_t* type, int inline_min, cudaStream_t);
+int geo_sub_blocks(int n_list);
+void geo_sub_count(const uint8_t* type, const long long* lcell, int n_list, int* counts, cudaStream_t);
+void geo_sub_write(const uint8_t* type, const long long* lcell, int n_list, const int* offsets, int* lsub, int* lwall,
+                   int* lbc, cudaStream_t);
+void geo_count_kinds(const uint8_t* type, long long N, unsigned long long* out, cudaStream_t);
 // source map (debug): for each (i, n): source population and cell, -1 for solid cells
 void geo_source_map(const GeoArgs&, const uint8_t* type, int64_t* src_dir, int64_t* src_cell, cudaStream_t);
 // FP64 final reduction of nblk partials (4 doubles each) into out[4], fixed order

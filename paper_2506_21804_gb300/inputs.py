@@ -74,6 +74,7 @@ class Workload:
     u0: Optional[np.ndarray] = None        # (3, N)
     model: int = 0                         # collision: 0 BGK, 1 hybrid recursive regularised
     sigma: float = 1.0                     # hybridisation factor of the HRR collision
+    vortex: Optional[tuple] = None         # vortex-method inlet (n, sigma, intensity, seed) or None
     meta: dict = field(default_factory=dict)
 
     @property

@@ -46,6 +46,10 @@ SIGNATURES = {
     "lbm_last_error": (ctypes.c_char_p, []),
     "lbm_set_precision": (_i, [_p, _i]),
     "lbm_set_collision": (_i, [_p, _i, _d]),
+    "lbm_set_vortex_inlet": (_i, [_p, _i, _d, _d, ctypes.c_ulonglong]),
+    "lbm_set_permeability": (_i, [_p, _p]),
+    "lbm_set_permeability_ex": (_i, [_p, _p, _i]),
+    "lbm_forchheimer_permeability": (_d, [_d, _d, _d, _d, _d, _d, _d]),
     "lbm_set_periodic": (_i, [_p, _i, _i, _i]),
     "lbm_set_faces": (_i, [_p, _p]),
     "lbm_set_geometry": (_i, [_p, _p, _p]),
@@ -129,6 +133,12 @@ class _Arr:
             self.nbytes = a.nbytes
 
 
+def forchheimer_permeability(mu, Q, A, L, dP, rho, K_beta=float("inf")):
+    """Forchheimer permeability of a sample (K_beta = inf: Darcy's law)."""
+    return lib().lbm_forchheimer_permeability(float(mu), float(Q), float(A), float(L), float(dP), float(rho),
+                                              float(K_beta))
+
+
 class Lattice:
     """One lattice on the current CUDA device (owns its device memory through liblbm)."""
 
@@ -186,8 +196,17 @@ class Lattice:
         a = _Arr(gamma)
         _check(lib().lbm_set_porosity_ex(self.h, a.ptr, a.code))
 
+    def set_permeability(self, K):
+        """Porosity from the per-cell permeability K (lattice units; inf = fluid)."""
+        a = _Arr(K)
+        _check(lib().lbm_set_permeability_ex(self.h, a.ptr, a.code))
+
     def set_wall_model(self, kappa=0.41, E=9.52):
         _check(lib().lbm_set_wall_model(self.h, float(kappa), float(E)))
+
+    def set_vortex_inlet(self, n, sigma=4.0, intensity=0.1, seed=0):
+        """Vortex-method inlet with n vortices per step (0: off)."""
+        _check(lib().lbm_set_vortex_inlet(self.h, int(n), float(sigma), float(intensity), int(seed)))
 
     def set_collision(self, model, sigma=1.0):
         """BGK (model 0) or the hybrid recursive regularised collision (model 1, HRR) with
@@ -317,6 +336,8 @@ class Lattice:
             lat.set_wall_model(w.kappa, w.E)
         if getattr(w, "model", 0):
             lat.set_collision(w.model, w.sigma)
+        if getattr(w, "vortex", None):
+            lat.set_vortex_inlet(*w.vortex)
         if init:
             dt = np.float64 if storage == F64 else np.float32
             lat.init_equilibrium(np.asarray(w.rho0, dt), np.asarray(w.u0, dt))

@@ -28,6 +28,8 @@ def oracle_from(w, storage=0, cast32=False):
     o.set_storage(storage)
     if getattr(w, "model", 0):
         o.set_collision(w.model, w.sigma)
+    if getattr(w, "vortex", None):
+        o.set_vortex_inlet(*w.vortex)
     o.init_equilibrium(_arr(w.rho0, cast32), _arr(w.u0, cast32))
     return o
 
