@@ -390,16 +390,18 @@ template <int Q, int I> __host__ __device__ constexpr int csign() {
   return Lat<Q>::cx(I) != 0 ? Lat<Q>::cx(I) : (Lat<Q>::cy(I) != 0 ? Lat<Q>::cy(I) : Lat<Q>::cz(I));
 }
 
-// Returns false when either cell's density or velocity is not finite.
-template <int Q>
-__device__ __forceinline__ bool collide_fluid_x2(float2* h, float2 gamma, const Args& a) {
+// Returns false when either cell's density or velocity is not finite. get(i) yields population i of
+// both cells (read twice: for the moments and for the relaxation), put(i, v) stores its new value.
+template <int Q, class Get, class Put>
+__device__ __forceinline__ bool collide_fluid_x2(Get&& get, Put&& put, float2 gamma, const Args& a) {
   constexpr int H = Lat<Q>::H;
   const float2 z2 = bc2(0.f);
-  float2 drho = h[0], jx = z2, jy = z2, jz = z2;
+  float2 drho = get(0), jx = z2, jy = z2, jz = z2;
   float2 sxx = z2, syy = z2, szz = z2, sxy = z2, sxz = z2, syz = z2;
   sfor<1, H + 1>([&](auto I) {
     constexpr int i = decltype(I)::value, cx = Lat<Q>::cx(i), cy = Lat<Q>::cy(i), cz = Lat<Q>::cz(i);
-    const float2 sp = add2(h[i], h[i + H]), dp = sub2(h[i], h[i + H]);
+    const float2 hi = get(i), ho = get(i + H);
+    const float2 sp = add2(hi, ho), dp = sub2(hi, ho);
     drho = add2(drho, sp);
     if constexpr (cx != 0) { jx = acc2<cx>(jx, dp); sxx = add2(sxx, sp); }
     if constexpr (cy != 0) { jy = acc2<cy>(jy, dp); syy = add2(syy, sp); }
@@ -431,7 +433,7 @@ __device__ __forceinline__ bool collide_fluid_x2(float2* h, float2 gamma, const 
   const float2 vsq = fma2(vx, vx, fma2(vy, vy, mul2(vz, vz)));
   const float2 base = sub2(mul2(itau, drho), mul2(mul2(bc2(1.5f), rho), fma2(nk, usq, vsq)));
   const float2 r45 = mul2(bc2(4.5f), rho), r3 = mul2(bc2(3.f), rho);
-  h[0] = fma2(k, h[0], mul2(bc2(wgt<Q, float>(0)), base));
+  put(0, fma2(k, get(0), mul2(bc2(wgt<Q, float>(0)), base)));
   sfor<1, H + 1>([&](auto I) {
     constexpr int i = decltype(I)::value;
     const float2 cu = cdot2<Q, i>(ux, uy, uz), cv = cdot2<Q, i>(vx, vy, vz);
@@ -440,11 +442,11 @@ __device__ __forceinline__ bool collide_fluid_x2(float2* h, float2 gamma, const 
     const float2 w = bc2(wgt<Q, float>(i));
     const float2 p = mul2(w, add2(sym, anti)), m = mul2(w, sub2(sym, anti));
     if constexpr (csign<Q, i>() > 0) {
-      h[i] = fma2(k, h[i], p);
-      h[i + H] = fma2(k, h[i + H], m);
+      put(i, fma2(k, get(i), p));
+      put(i + H, fma2(k, get(i + H), m));
     } else {
-      h[i] = fma2(k, h[i], m);
-      h[i + H] = fma2(k, h[i + H], p);
+      put(i, fma2(k, get(i), m));
+      put(i + H, fma2(k, get(i + H), p));
     }
   });
   const float2 chk = add2(add2(abs2(rho), abs2(ux)), add2(abs2(uy), abs2(uz)));

@@ -460,12 +460,12 @@ __device__ __forceinline__ void pair_update(const Args& a, S* f, int x0, int y, 
   const unsigned us = unsigned(a.stride);
   const unsigned un = unsigned(x0 + y * a.nx) + unsigned(z) * unsigned(a.nxy);
   bool ok;
+  const float2 gam = a.gamma ? make_float2(static_cast<const float*>(a.gamma)[un], static_cast<const float*>(a.gamma)[un + 1])
+                             : bc2(1.f);
   {
     float2 h[Q];
     sfor<0, Q>([&](auto I) { h[I] = make_float2(P::lof(raw[I]), P::hif(raw[I])); });
-    const float2 gam = a.gamma ? make_float2(static_cast<const float*>(a.gamma)[un], static_cast<const float*>(a.gamma)[un + 1])
-                               : bc2(1.f);
-    ok = collide_fluid_x2<Q>(h, gam, a);
+    ok = collide_fluid_x2<Q>([&](int i) { return h[i]; }, [&](int i, float2 v) { h[i] = v; }, gam, a);
     sfor<0, Q>([&](auto I) { raw[I] = P::pack(h[I].x, h[I].y); });
   }
   if (!ok) atomicOr(a.status, ST_NAN);
