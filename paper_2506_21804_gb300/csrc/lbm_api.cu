@@ -98,7 +98,7 @@ struct lbm_ctx {
   DevBuf f, type, mask, wdist, gamma, uin, lcell, nsum, wref, lxyz, lcode, wnrm, wyw, ref0, ref1, status, red, redout, stage;
   DevBuf lidx, lsub, lwall, lbc, wst;
   DevBuf uvel0, uvel1;  // HRR velocity fields (step t reads uvel[t & 1], writes the other)
-  DevBuf uin_a, uin_b, vort;  // vortex inlet: current/previous inlet fields, vortex list
+  DevBuf uin_a, uin_b, vort, vpart;  // vortex inlet: current/previous inlet fields, vortex list, partial fields
   int n_sub = 0, n_wall = 0, n_bc = 0;
   bool has_gamma = false, has_wdist = false;
   int n_list = 0;
@@ -117,7 +117,7 @@ struct lbm_ctx {
   double adj_ms[3] = {0, 0, 0};
 
   ~lbm_ctx() {
-    DevBuf* all[] = {&uin_a, &uin_b, &vort, &uvel0, &uvel1, &lidx, &lsub, &lwall, &lbc, &wst, &f, &type, &mask, &wdist, &gamma, &uin, &lcell, &nsum, &wref, &lxyz, &lcode, &wnrm, &wyw, &ref0, &ref1, &status, &red,
+    DevBuf* all[] = {&uin_a, &uin_b, &vort, &vpart, &uvel0, &uvel1, &lidx, &lsub, &lwall, &lbc, &wst, &f, &type, &mask, &wdist, &gamma, &uin, &lcell, &nsum, &wref, &lxyz, &lcode, &wnrm, &wyw, &ref0, &ref1, &status, &red,
                      &redout, &stage, &lamA, &lamB, &dgam, &duin, &plane};
     for (DevBuf* b : all) b->release();
     for (auto& b : ckpts) b.release();
@@ -400,6 +400,7 @@ int vm_reset(lbm_ctx* c) {
   CK(c->uin_a.ensure(pb));
   CK(c->uin_b.ensure(pb));
   CK(c->vort.ensure(3 * (size_t)c->vm_n * c->ops->celem));
+  CK(c->vpart.ensure(2 * (size_t)((c->vm_n + VM_CHUNK - 1) / VM_CHUNK) * c->ny * c->nz * c->ops->celem));
   CK(cudaMemcpyAsync(c->uin_a.p, c->uin.p, pb, cudaMemcpyDeviceToDevice, c->stream));
   c->vm_which = 0;
   return LBM_OK;
@@ -416,6 +417,7 @@ void vm_step(lbm_ctx* c) {
   v.prev = c->vm_which == 0 ? c->uin_a.p : c->uin_b.p;
   v.cur = c->vm_which == 0 ? c->uin_b.p : c->uin_a.p;
   v.vort = c->vort.p;
+  v.part = c->vpart.p;
   vm_update(v, c->ops->celem, c->stream);
   c->vm_which ^= 1;
 }
@@ -566,7 +568,7 @@ int lbm_set_precision(lbm_ctx* c, int storage) {
   if (c->has_gamma && (rc = upload_compute(c, c->gamma, g.data(), LBM_DTYPE_F64, c->N)) != LBM_OK) return rc;
   c->wnrm.release(); c->wyw.release(); c->ref0.release(); c->ref1.release();
   c->uvel0.release(); c->uvel1.release();
-  c->uin_a.release(); c->uin_b.release(); c->vort.release();
+  c->uin_a.release(); c->uin_b.release(); c->vort.release(); c->vpart.release();
   if ((rc = build_geometry(c)) != LBM_OK) return rc;
   return reset_state(c);
 }
@@ -994,7 +996,7 @@ int lbm_set_vortex_inlet(lbm_ctx* c, int n, double sigma, double intensity, unsi
   if (!(intensity >= 0.0) || !std::isfinite(intensity)) return fail(LBM_EINVAL, "intensity must be >= 0");
   c->vm_n = n; c->vm_sigma = sigma; c->vm_I = intensity; c->vm_seed = seed;
   if (n == 0) {
-    c->uin_a.release(); c->uin_b.release(); c->vort.release();
+    c->uin_a.release(); c->uin_b.release(); c->vort.release(); c->vpart.release();
     return LBM_OK;
   }
   int rc = vm_reset(c);

@@ -16,7 +16,8 @@
 // seed + (1 + counter) * 0x9E3779B97F4A7C15, top 53 bits scaled to [0, 1); counter of vortex i,
 // component c (0: y, 1: z, 2: sign) at step t: (t n + i) 4 + c. Positions and circulations are
 // formed in double precision with explicitly rounded operations (no contraction), the plane field
-// in the compute type.
+// in the compute type: partial sums over chunks of VM_CHUNK vortices (one CTA row per chunk), then
+// their sum in chunk order (deterministic).
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -67,38 +68,52 @@ __global__ void k_vm_gen(const VmArgs v) {
 template <class C> __device__ __forceinline__ C vexp(C x) { return exp(x); }
 template <> __device__ __forceinline__ float vexp<float>(float x) { return expf(x); }
 
-constexpr int VM_TILE = 256;
+constexpr int VM_THREADS = 256;
 
+// Partial in-plane field of vortex chunk blockIdx.y (VM_CHUNK vortices) at every plane position.
 template <class C>
-__global__ void __launch_bounds__(VM_TILE) k_vm_plane(const VmArgs v) {
-  __shared__ C sv[3 * VM_TILE];
+__global__ void __launch_bounds__(VM_THREADS) k_vm_partial(const VmArgs v) {
+  __shared__ C sv[3 * VM_CHUNK];
   const long long pl = (long long)v.ny * v.nz;
+  const int c0 = blockIdx.y * VM_CHUNK;
+  const int m = v.n - c0 < VM_CHUNK ? v.n - c0 : VM_CHUNK;
+  const C* vort = static_cast<const C*>(v.vort);
+  for (int j = threadIdx.x; j < 3 * m; j += blockDim.x) sv[j] = vort[3 * c0 + j];
+  __syncthreads();
   const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const bool live = p < pl;
-  const int y = live ? int(p % v.ny) : 0, z = live ? int(p / v.ny) : 0;
-  const C yc = C(y), zc = C(z);
+  if (p >= pl) return;
+  const C yc = C(int(p % v.ny)), zc = C(int(p / v.ny));
   const C inv2s2 = C(1) / (C(2) * C(v.sigma) * C(v.sigma));
   const C inv2pi = C(1.0 / (2.0 * M_PI));
-  const C* vort = static_cast<const C*>(v.vort);
   C uy = C(0), uz = C(0);
-  for (int b = 0; b < v.n; b += VM_TILE) {
-    const int m = v.n - b < VM_TILE ? v.n - b : VM_TILE;
-    __syncthreads();
-    for (int j = threadIdx.x; j < 3 * m; j += blockDim.x) sv[j] = vort[3 * b + j];
-    __syncthreads();
-    if (live) {
-      for (int j = 0; j < m; ++j) {
-        const C ry = sv[3 * j] - yc, rz = sv[3 * j + 1] - zc;
-        const C r2 = ry * ry + rz * rz;
-        if (r2 == C(0)) continue;
-        const C e = vexp(-r2 * inv2s2);
-        const C f = sv[3 * j + 2] * (C(1) - e) * e * inv2pi / r2;
-        uy += f * rz;
-        uz -= f * ry;
-      }
-    }
+  for (int j = 0; j < m; ++j) {
+    const C ry = sv[3 * j] - yc, rz = sv[3 * j + 1] - zc;
+    const C r2 = ry * ry + rz * rz;
+    if (r2 == C(0)) continue;
+    const C e = vexp(-r2 * inv2s2);
+    const C f = sv[3 * j + 2] * (C(1) - e) * e * inv2pi / r2;
+    uy += f * rz;
+    uz -= f * ry;
   }
-  if (!live) return;
+  C* part = static_cast<C*>(v.part);
+  part[(2 * (long long)blockIdx.y) * pl + p] = uy;
+  part[(2 * (long long)blockIdx.y + 1) * pl + p] = uz;
+}
+
+// Sum of the chunk partials in chunk order, streamwise fluctuation, inlet field of the step.
+template <class C>
+__global__ void __launch_bounds__(VM_THREADS) k_vm_finish(const VmArgs v) {
+  const long long pl = (long long)v.ny * v.nz;
+  const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (p >= pl) return;
+  const int y = int(p % v.ny), z = int(p / v.ny);
+  const C* part = static_cast<const C*>(v.part);
+  const int nch = (v.n + VM_CHUNK - 1) / VM_CHUNK;
+  C uy = C(0), uz = C(0);
+  for (int c = 0; c < nch; ++c) {
+    uy += part[(2 * (long long)c) * pl + p];
+    uz += part[(2 * (long long)c + 1) * pl + p];
+  }
   const C* U = static_cast<const C*>(v.prev);  // streamwise component first
   auto at = [&](int yy, int zz) { return U[yy + (long long)v.ny * zz]; };
   C gy = C(0), gz = C(0);
@@ -126,13 +141,16 @@ __global__ void __launch_bounds__(VM_TILE) k_vm_plane(const VmArgs v) {
 void vm_update(const VmArgs& v, int celem, cudaStream_t s) {
   if (v.n <= 0) return;
   const long long pl = (long long)v.ny * v.nz;
-  const unsigned gb = unsigned((v.n + 127) / 128), gp = unsigned((pl + VM_TILE - 1) / VM_TILE);
+  const unsigned gb = unsigned((v.n + 127) / 128), gp = unsigned((pl + VM_THREADS - 1) / VM_THREADS);
+  const dim3 gpart(gp, unsigned((v.n + VM_CHUNK - 1) / VM_CHUNK));
   if (celem == 8) {
     k_vm_gen<double><<<gb, 128, 0, s>>>(v);
-    k_vm_plane<double><<<gp, VM_TILE, 0, s>>>(v);
+    k_vm_partial<double><<<gpart, VM_THREADS, 0, s>>>(v);
+    k_vm_finish<double><<<gp, VM_THREADS, 0, s>>>(v);
   } else {
     k_vm_gen<float><<<gb, 128, 0, s>>>(v);
-    k_vm_plane<float><<<gp, VM_TILE, 0, s>>>(v);
+    k_vm_partial<float><<<gpart, VM_THREADS, 0, s>>>(v);
+    k_vm_finish<float><<<gp, VM_THREADS, 0, s>>>(v);
   }
 }
 

@@ -19,9 +19,13 @@ struct VmArgs {
   const void* prev;    // compute type [3][ny*nz]: inlet field of the previous step
   void* cur;           // compute type [3][ny*nz]: inlet field of this step (written)
   void* vort;          // compute type [3*n]: y, z, Gamma of this step's vortices (written)
+  void* part;          // compute type [2*ceil(n/VM_CHUNK)][ny*nz]: per-chunk partial fields (scratch)
 };
 
-// Two launches on stream s: the vortices of step t, then the inlet field. celem = 4 or 8.
+constexpr int VM_CHUNK = 32;  // vortices per partial sum
+
+// Three launches on stream s: the vortices of step t, the per-chunk partial fields, the inlet field.
+// celem = 4 or 8.
 void vm_update(const VmArgs& v, int celem, cudaStream_t s);
 
 }  // namespace lbm
