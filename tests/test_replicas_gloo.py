@@ -43,7 +43,7 @@ def _worker(rank, world, port, out):
 
 def test_two_rank_replica_logic():
     world, port = 2, _free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.start_processes(_worker, args=(world, port, out), nprocs=world, join=True, start_method="spawn")
         res = dict(out)
