@@ -8,15 +8,17 @@ from tests.helpers import oracle_from
 from tests.test_gpu_parity import _crop_oracle
 
 
-@pytest.mark.parametrize("which", ["channel", "canopy"])
+@pytest.mark.parametrize("which", ["channel", "canopy", "channel_hrr", "canopy_hrr"])
 def test_crop_reproduces_full_domain(which):
-    if which == "channel":
+    if which.startswith("channel"):
         w = I.channel(nx=24, ny=22, nz=20, seed=3, dtype=np.float64)
-        steps, R = 4, 7
+        steps, R = (4, 7) if which == "channel" else (3, 7)
     else:
         w = I.canopy(nx=48, ny=30, nz=24, n_buildings=8, seed=2506, domain=(200, 30, 64), crop=(64, 0, 0),
                      dtype=np.float64)
-        steps, R = 2, 5
+        steps, R = (2, 5) if which == "canopy" else (2, 6)
+    if which.endswith("hrr"):
+        w.model, w.sigma = 1, 0.5
     full = oracle_from(w)
     full.step(steps)
     rf, uf = full.moments()
