@@ -197,6 +197,13 @@ def run_reference(args):
 
 
 # ---- GPU arm ---------------------------------------------------------------------------------------------------
+def interior_kernel_name(args, nx, hrr):
+    sixteen = args.storage in ("f16", "bf16")
+    if hrr:
+        return "k_bulk_hrr"
+    if args.kernel == "staged" and nx % 128 == 0:
+        return "k_bulk_tma"
+    return "k_bulk2" if (sixteen and nx % 2 == 0) else "k_bulk"
 def timed_glups(lat, steps, warmup):
     lat.step(warmup)
     lat.sync()
@@ -408,7 +415,7 @@ def main():
         "config": {"workload": wname, "kernel": args.kernel, "cells": w.N, "parallelism": f"replicas x{world}",
                    "l2": "state of 2.6 GB > 129 MB L2 between steps, no flush needed",
                    "non_solid_cells": info["N"] - info["n_solid"], "boundary_list_cells": info["n_list"]},
-        "roofline": {"bound": "hbm", "kernel": ("k_bulk_hrr" if hrr else ("k_bulk_tma" if (args.kernel == "staged" and w.nx % 128 == 0) else "k_bulk")) + " (interior cells)", "achieved": achieved, "peak": peak,
+        "roofline": {"bound": "hbm", "kernel": interior_kernel_name(args, w.nx, hrr) + " (interior cells)", "achieved": achieved, "peak": peak,
                      "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "bytes_per_launch": bytes_bulk, "launch_ms": bulk_ms,
                      "share_of_step": ms[0] / ms[2]},
