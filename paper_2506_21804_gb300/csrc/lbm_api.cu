@@ -99,6 +99,7 @@ struct lbm_ctx {
   DevBuf lidx, lsub, lwall, lbc, wst;
   DevBuf uvel0, uvel1;  // HRR velocity fields (step t reads uvel[t & 1], writes the other)
   DevBuf uin_a, uin_b, vort, vpart;  // vortex inlet: current/previous inlet fields, vortex list, partial fields
+  DevBuf geo_counts, geo_sub, geo_kinds;  // geometry set-up scratch (per-block counts, kind counters)
   int n_sub = 0, n_wall = 0, n_bc = 0;
   bool has_gamma = false, has_wdist = false;
   int n_list = 0;
@@ -117,7 +118,7 @@ struct lbm_ctx {
   double adj_ms[3] = {0, 0, 0};
 
   ~lbm_ctx() {
-    DevBuf* all[] = {&uin_a, &uin_b, &vort, &vpart, &uvel0, &uvel1, &lidx, &lsub, &lwall, &lbc, &wst, &f, &type, &mask, &wdist, &gamma, &uin, &lcell, &nsum, &wref, &lxyz, &lcode, &wnrm, &wyw, &ref0, &ref1, &status, &red,
+    DevBuf* all[] = {&geo_counts, &geo_sub, &geo_kinds, &uin_a, &uin_b, &vort, &vpart, &uvel0, &uvel1, &lidx, &lsub, &lwall, &lbc, &wst, &f, &type, &mask, &wdist, &gamma, &uin, &lcell, &nsum, &wref, &lxyz, &lcode, &wnrm, &wyw, &ref0, &ref1, &status, &red,
                      &redout, &stage, &lamA, &lamB, &dgam, &duin, &plane};
     for (DevBuf* b : all) b->release();
     for (auto& b : ckpts) b.release();
@@ -278,7 +279,7 @@ int build_geometry(lbm_ctx* c) {
   geo_classify(g, static_cast<const uint8_t*>(c->mask.p), static_cast<uint8_t*>(c->type.p), static_cast<unsigned*>(c->status.p), s);
   geo_mark_ref(g, static_cast<uint8_t*>(c->type.p), s);
   const int nb = geo_count_blocks(g);
-  DevBuf counts;
+  DevBuf& counts = c->geo_counts;  // kept between calls: a geometry change allocates nothing new
   CK(counts.ensure((size_t)nb * sizeof(int)));
   geo_list_count(g, static_cast<uint8_t*>(c->type.p), static_cast<int*>(counts.p), s);
   std::vector<int> hc(nb);
@@ -286,7 +287,6 @@ int build_geometry(lbm_ctx* c) {
   CK(cudaMemcpyAsync(c->status_h, c->status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   if (*c->status_h & ST_BADMASK) {
-    counts.release();
     return fail(LBM_EINVAL, "mask holds codes other than 0 (fluid), 1 (solid), 3 (inflow), 4 (outflow)");
   }
   long long total = 0;
@@ -296,7 +296,6 @@ int build_geometry(lbm_ctx* c) {
     total += v;
   }
   if (total > 0x7fffffffLL) {
-    counts.release();
     return fail(LBM_EINVAL, "boundary list too long (%lld entries)", total);
   }
   c->n_list = int(total);
@@ -337,7 +336,7 @@ int build_geometry(lbm_ctx* c) {
     const long long* lcell = static_cast<const long long*>(c->lcell.p);
     geo_inline_mark(g, type, INLINE_MIN, s);
     const int sb = std::max(1, geo_sub_blocks(c->n_list));
-    DevBuf sc;
+    DevBuf& sc = c->geo_sub;
     CK(sc.ensure((size_t)sb * 3 * sizeof(int)));
     std::vector<int> hs(3 * (size_t)sb, 0);
     if (c->n_list) {
@@ -362,7 +361,7 @@ int build_geometry(lbm_ctx* c) {
                     static_cast<int*>(c->lwall.p), static_cast<int*>(c->lbc.p), s);
     }
     // cell-kind counters
-    DevBuf kc;
+    DevBuf& kc = c->geo_kinds;
     CK(kc.ensure(5 * sizeof(unsigned long long)));
     geo_count_kinds(type, c->N, static_cast<unsigned long long*>(kc.p), s);
     unsigned long long hk[5];
@@ -370,10 +369,7 @@ int build_geometry(lbm_ctx* c) {
     CK(cudaStreamSynchronize(s));
     CK(cudaGetLastError());
     for (int i = 0; i < 5; ++i) c->counts[i] = (long long)hk[i];
-    sc.release();
-    kc.release();
   }
-  counts.release();
   c->type_host_valid = false;
   return LBM_OK;
 }

@@ -241,8 +241,8 @@ __global__ void k_inline_mark(const GeoArgs g, uint8_t* type, int inline_min) {
   }
 }
 
-// Sub-lists of the boundary list, in list order: 0 entries not updated inline, 1 inline WALL
-// entries, 2 INFLOW/OUTFLOW entries. Two passes like the list itself: per-block counts, then
+// Sub-lists of the boundary list, in list order: 0 entries not updated inline, 1 WALL entries (the
+// wall-model state pass), 2 INFLOW/OUTFLOW entries. Two passes like the list itself: per-block counts, then
 // writes at exclusive offsets (entries ranked inside a warp by ballot).
 __device__ __forceinline__ void sub_flags(const uint8_t* type, const long long* lcell, int k, int n_list, bool f[3]) {
   f[0] = f[1] = f[2] = false;
@@ -250,7 +250,7 @@ __device__ __forceinline__ void sub_flags(const uint8_t* type, const long long* 
   const uint8_t t = type[lcell[k]];
   const int kind = t & T_KIND;
   f[0] = !(t & T_INLINE);
-  f[1] = (t & T_INLINE) && kind == K_WALL;
+  f[1] = kind == K_WALL;
   f[2] = kind == K_INFLOW || kind == K_OUTFLOW;
 }
 

@@ -280,12 +280,17 @@ __device__ __forceinline__ void collide_any(const Args& a, int kind, uint8_t t, 
   apply_bc<Q, C>(a, kind, y, z, h);
   C rho, urx, ury, urz;
   if (kind == K_WALL && a.wm) {
-    const C* nr = cptr<C>(a.wnrm) + 3 * (long long)k;
-    const int r = a.wref[k];
-    const C* ur = r >= 0 ? cptr<C>(a.ref_rd) + 3 * (long long)r : nullptr;
-    C z3[3] = {C(0), C(0), C(0)};
-    C ws[WALL_STATE];
-    wall_state<C>(a, nr, cptr<C>(a.wyw)[k], r >= 0 ? ur : z3, r >= 0, ws);
+    // fused mode: the wall-model state pass has already solved every WALL entry of this step
+    C ws_own[WALL_STATE];
+    const C* ws = cptr<C>(a.wst) + (long long)WALL_STATE * k;
+    if (!a.fuse) {
+      const C* nr = cptr<C>(a.wnrm) + 3 * (long long)k;
+      const int r = a.wref[k];
+      const C* ur = r >= 0 ? cptr<C>(a.ref_rd) + 3 * (long long)r : nullptr;
+      C z3[3] = {C(0), C(0), C(0)};
+      wall_state<C>(a, nr, cptr<C>(a.wyw)[k], r >= 0 ? ur : z3, r >= 0, ws_own);
+      ws = ws_own;
+    }
     if constexpr (HRR) collide_wall_hrr<Q, C>(h, a, ws, rho, urx, ury, urz);
     else collide_wall_state<Q, C>(h, a, ws, rho, urx, ury, urz);
   } else if constexpr (HRR) {

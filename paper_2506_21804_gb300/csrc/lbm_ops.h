@@ -60,7 +60,7 @@ void geo_list_meta(const GeoArgs&, const uint8_t* type, const long long* lcell, 
 // list position of every cell (-1 off the list)
 void geo_list_index(const long long* lcell, int n_list, int* lidx, cudaStream_t);
 // inline (fused-mode) flags per 32-cell x-group; sub-lists of the boundary list (3 per-block counts,
-// then writes at offsets: not-inline, inline WALL, INFLOW/OUTFLOW); counts of WALL, reference,
+// then writes at offsets: not-inline, WALL, INFLOW/OUTFLOW); counts of WALL, reference,
 // INFLOW, OUTFLOW and SOLID cells
 void geo_inline_mark(const GeoArgs&, uint8_t* type, int inline_min, cudaStream_t);
 int geo_sub_blocks(int n_list);

@@ -149,6 +149,7 @@ class Lattice:
         if not h:
             raise LBMError(EINVAL, lib().lbm_last_error().decode())
         self.h = h
+        self.storage = F32
         if storage != F32:
             self.set_precision(storage)
 
@@ -166,6 +167,7 @@ class Lattice:
     # ---- configuration -------------------------------------------------------------------------------
     def set_precision(self, storage):
         _check(lib().lbm_set_precision(self.h, int(storage)))
+        self.storage = int(storage)
 
     def set_periodic(self, px, py, pz):
         _check(lib().lbm_set_periodic(self.h, int(px), int(py), int(pz)))

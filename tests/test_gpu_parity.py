@@ -145,6 +145,22 @@ def test_16bit_taylor_green_error(storage, bound):
     assert rel_l2(ug, uo) < bound
 
 
+@pytest.mark.parametrize("storage,bound", [(lbm.F16, 0.01), (lbm.BF16, 0.05)])
+def test_16bit_channel_mean_profile_vs_fp32(storage, bound):
+    """Turbulent-channel configuration (wall function, Smagorinsky, body force) on 128x130x32:
+    the streamwise mean-velocity profile <u_x>(y) of 16-bit storage against FP32 after 300 steps,
+    within 1 % (FP16) and 5 % (BF16) of the profile's maximum."""
+    w = I.channel(nx=128, ny=130, nz=32, seed=550, dtype=np.float32)
+    prof = []
+    for st in (lbm.F32, storage):
+        g = gpu_from(w, st)
+        g.step(300)
+        _, u = g.moments(np.float32)
+        prof.append(u[0].reshape(w.nz, w.ny, w.nx).mean(axis=(0, 2)))
+    ref, got = prof
+    assert np.abs(got - ref).max() < bound * np.abs(ref).max()
+
+
 def test_16bit_matches_oracle_storage_emulation_one_step():
     """One step of FP16 storage equals the oracle's FP16-rounded storage to within a few units in
     the last place of the stored deviation: FP32 (GPU) and FP64 (oracle) arithmetic can round the
