@@ -293,8 +293,13 @@ def secondary(lbm, I, torch):
         lat = lbm.Lattice.from_workload(wc, storage=lbm.F32)
         g, ms = timed_glups(lat, 20, 2)
         info = lat.info()
+        # wall-model traffic beyond the populations: normal + distance (16 B) per WALL cell, the
+        # reference velocity written and read (2 x 12 B) per reference cell, per cell of the grid
+        wm_bytes = (info["n_wall"] * 16 + info["n_ref"] * 24) / info["N"]
         out[f"canopy512x512x256_d3q{q}_fp32"] = {"glups": g, "boundary_list_fraction": info["n_list"] / info["N"],
-                                                 "interior_ms": ms[0] / 20, "list_ms": ms[1] / 20}
+                                                 "interior_ms": ms[0] / 20, "list_ms": ms[1] / 20,
+                                                 "wall_model_bytes_per_cell": wm_bytes,
+                                                 "glups_non_solid": g * (info["N"] - info["n_solid"]) / info["N"]}
         lat.close()
     # the paper's full model on the canopy: HRR collision (sigma = 1/2) and the vortex-method inlet
     wc = I.canopy(nx=512, ny=512, nz=256, q=19, seed=2506, dtype=np.float32)
@@ -445,6 +450,7 @@ def main():
         "step_roofline": {"bytes_per_step": step_bytes, "achieved_gbs": step_bytes / (t_ms / args.steps * 1e-3) / 1e9,
                           "frac": step_bytes / (t_ms / args.steps * 1e-3) / 1e9 / peak},
         "e2e": e2e,
+        "glups_non_solid": world * (info["N"] - info["n_solid"]) * args.steps / (t_ms * 1e-3) / 1e9,
         "gpu_launches": 2 * args.steps,
         "clocks": clocks,
     }
