@@ -110,7 +110,8 @@ int lbm_set_outflow(lbm_ctx* ctx, double rho_out);
 /* Per-cell porosity gamma (N values in [0,1], 1 = fluid); NULL removes it. */
 int lbm_set_porosity(lbm_ctx* ctx, const float* gamma);
 int lbm_set_porosity_ex(lbm_ctx* ctx, const void* gamma, int dtype);
-/* Porosity from a per-cell permeability K (N values, lattice units K/dx^2; +inf = fluid): the
+/* Porosity from a per-cell permeability K (N values, lattice units K/dx^2; +inf = fluid; K <= 0 or
+ * NaN = impermeable): the
  * lattice porosity of Eq. lattice_porosity, gamma = 1 - nu tau / K with nu = (tau - 1/2)/3 and tau
  * the molecular relaxation time, read as the fluid fraction and clamped to [0, 1]; replaces any
  * porosity set before. Errors: LBM_EINVAL for a bad pointer or dtype. */

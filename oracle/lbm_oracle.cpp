@@ -1108,13 +1108,14 @@ double orc_forchheimer_k(double mu, double Q, double A, double L, double dP, dou
 // Porosity from the permeability K of every cell (lattice units, K = dx^2-scaled; +inf = fluid):
 // the lattice porosity of Eq. lattice_porosity, d = 1 - dx^2 nu tau / K with dx = 1, nu = (tau - 1/2)/3
 // the molecular viscosity and tau the molecular relaxation time, read as the fluid fraction
-// gamma = d (gamma = 1 for K = inf) clamped to [0, 1].
+// gamma = d (gamma = 1 for K = inf, 0 for K <= 0 or NaN) clamped to [0, 1].
 void orc_set_permeability(void* h, const double* K) {
   Oracle& o = *static_cast<Oracle*>(h);
   const double nu = CS2 * (o.tau0 - 0.5);
   o.gamma.assign(o.N, 1.0);
   for (long n = 0; n < o.N; ++n) {
-    double g = std::isinf(K[n]) ? 1.0 : 1.0 - nu * o.tau0 / K[n];
+    // K = +inf: fluid; K <= 0 or NaN carries no permeability and is read as impermeable
+    double g = (std::isinf(K[n]) && K[n] > 0.0) ? 1.0 : (K[n] > 0.0 ? 1.0 - nu * o.tau0 / K[n] : 0.0);
     o.gamma[n] = std::min(1.0, std::max(0.0, g));
   }
 }

@@ -1088,6 +1088,8 @@ int lbm_objective_forward(lbm_ctx* c, int T, int W, int xa, int xb, int ckpt, do
 int lbm_objective_backward(lbm_ctx* c, double* dJ_dgamma, double* dJ_duin) {
   if (!c) return fail(LBM_EINVAL, "null context");
   if (c->adj_t0 != c->t) return fail(LBM_ESTATE, "no forward run to differentiate (run lbm_objective_forward first)");
+  if (c->model != LBM_BGK) return fail(LBM_ESTATE, "the adjoint is defined for the BGK collision only");
+  if (c->vm_n > 0) return fail(LBM_ESTATE, "the adjoint is defined for a steady inlet only");
   if (c->wm) return fail(LBM_ESTATE, "the wall model is not differentiated");
   const int T = c->adj_T, W = c->adj_W, ck = c->adj_ck;
   const int nck = (T + ck - 1) / ck;

@@ -10,14 +10,15 @@
 namespace lbm {
 namespace {
 
-// gamma = clamp(1 - nu tau / K, 0, 1) (lattice units, dx = 1; K = +inf gives 1). K of dtype KT,
-// gamma in the compute type C.
+// gamma = clamp(1 - nu tau / K, 0, 1) (lattice units, dx = 1; K = +inf gives 1, K <= 0 or NaN gives 0).
+// K of dtype KT, gamma in the compute type C.
 template <class KT, class C>
 __global__ void k_perm_gamma(const KT* K, C* gamma, long long n, double nu_tau) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= n) return;
   const double k = double(K[i]);
-  double g = isinf(k) ? 1.0 : 1.0 - nu_tau / k;
+  // K = +inf: fluid; K <= 0 or NaN (no valid permeability): impermeable
+  double g = isinf(k) && k > 0.0 ? 1.0 : (k > 0.0 ? 1.0 - nu_tau / k : 0.0);
   g = g < 0.0 ? 0.0 : (g > 1.0 ? 1.0 : g);
   gamma[i] = C(g);
 }

@@ -129,6 +129,7 @@ def test_permeability_field_matches_oracle_fp64():
     rng = np.random.default_rng(5)
     K = nu_tau / (1e-3 + rng.random(w.N))       # gamma spans [0, 1) with clamping below nu tau
     K[rng.random(w.N) < 0.3] = np.inf
+    K[:3] = (-1.0, 0.0, np.nan)                 # no valid permeability: impermeable on both sides
     w.gamma = None
     o = oracle_from(w)
     o.set_permeability(K)

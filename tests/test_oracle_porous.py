@@ -28,9 +28,12 @@ def test_porosity_from_permeability_limits():
     K[:8] = nu * tau            # at the threshold: solid-like
     K[8:16] = 0.5 * nu * tau    # below it: clamped
     K[16:24] = 10 * nu * tau    # gamma = 0.9
+    K[24] = -1.0                # invalid permeabilities are impermeable
+    K[25] = np.nan
     o.set_permeability(K)
     g = o.porosity()
-    assert np.all(g[:16] == 0.0)
+    assert np.all(g[:16] == 0.0) and g[24] == 0.0 and g[25] == 0.0
+    g[24:26] = 1.0
     assert np.allclose(g[16:24], 0.9, atol=1e-15)
     assert np.all(g[24:] == 1.0)
 
