@@ -21,6 +21,10 @@
 //     part (Sec. 2.2.1);
 //   * a regularised local velocity inlet (Sec. 2.2.2, last paragraph) and a fixed local pressure
 //     outlet and full-slip outer faces (Sec. 3.2);
+//   * the hybrid recursive regularised collision of Sec. 2.2 (third-order Hermite equilibrium,
+//     recursive third-order f^(1), finite-difference strain) as the alternative collision model;
+//   * the vortex-method turbulent inlet of Sec. 2.2.2 and the porous-medium inputs of Sec. 2.1
+//     (Forchheimer permeability, Eq. lattice_porosity);
 //   * the GLUPs definition of Sec. 3.1 is not computed here (it is a timing quantity).
 // Readings where the paper is silent or garbled are stated next to the code that takes them.
 //

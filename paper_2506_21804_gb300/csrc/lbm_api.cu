@@ -331,7 +331,10 @@ int build_geometry(lbm_ctx* c) {
     // (their extra work is a short reconstruction before the shared collision); WALL and reference
     // cells when their 32-cell x-group holds at least INLINE_MIN list cells. Isolated WALL and
     // reference cells stay with the boundary-list kernel. Then the sub-lists of the boundary list.
-    constexpr int INLINE_MIN = 8;
+#ifndef LBM_INLINE_MIN
+#define LBM_INLINE_MIN 8
+#endif
+    constexpr int INLINE_MIN = LBM_INLINE_MIN;
     uint8_t* type = static_cast<uint8_t*>(c->type.p);
     const long long* lcell = static_cast<const long long*>(c->lcell.p);
     geo_inline_mark(g, type, INLINE_MIN, s);
