@@ -200,7 +200,7 @@ def run_reference(args):
 def interior_kernel_name(args, nx, hrr):
     sixteen = args.storage in ("f16", "bf16")
     if hrr:
-        return "k_bulk_hrr"
+        return "k_bulk2<HRR>" if (sixteen and nx % 2 == 0) else "k_bulk_hrr"
     if args.kernel == "staged" and nx % 128 == 0:
         return "k_bulk_tma"
     return "k_bulk2" if (sixteen and nx % 2 == 0) else "k_bulk"

@@ -184,6 +184,135 @@ __device__ __forceinline__ void collide_wall_hrr(C* h, const Args& a, const C* w
                   ws[0], ws[1], ws[2], C(1) - rcp(tau), A);
 }
 
+// ---- the HRR update of two cells at once with packed FP32 instructions (16-bit paired kernel) --------
+// r + M v for a compile-time small integer M, packed lanes
+template <int M> __device__ __forceinline__ float2 accm2(float2 r, float2 v) {
+  if constexpr (M == 0) return r;
+  else if constexpr (M == 1) return add2(r, v);
+  else if constexpr (M == -1) return sub2(r, v);
+  else return fma2(bc2(float(M)), v, r);
+}
+
+// hrr_relax for two cells (lane x, lane y); same formulas, each lane rounded as the scalar form.
+template <int Q>
+__device__ __forceinline__ void hrr_relax_x2(float2* h, float2 drho, float2 rho, float2 uex, float2 uey, float2 uez,
+                                             float2 uhx, float2 uhy, float2 uhz, float2 k, const float2* A) {
+  constexpr int H = Lat<Q>::H;
+  const float2 Axx = A[0], Ayy = A[1], Azz = A[2], Axy = A[3], Axz = A[4], Ayz = A[5];
+  const float2 usq = fma2(uex, uex, fma2(uey, uey, mul2(uez, uez)));
+  const float2 c15 = bc2(1.5f), two = bc2(2.f);
+  const float2 base = sub2(sub2(drho, mul2(mul2(c15, rho), usq)), mul2(mul2(c15, k), add2(add2(Axx, Ayy), Azz)));
+  const float2 r45 = mul2(bc2(4.5f), rho), r3 = mul2(bc2(3.f), rho), k45 = mul2(bc2(4.5f), k);
+  const float2 rxx = mul2(mul2(rho, uex), uex), ryy = mul2(mul2(rho, uey), uey), rzz = mul2(mul2(rho, uez), uez);
+  const float2 a_xxy = fma2(rxx, uey, mul2(k, fma2(mul2(two, uhx), Axy, mul2(uhy, Axx))));
+  const float2 a_zzy = fma2(rzz, uey, mul2(k, fma2(mul2(two, uhz), Ayz, mul2(uhy, Azz))));
+  const float2 a_xxz = fma2(rxx, uez, mul2(k, fma2(mul2(two, uhx), Axz, mul2(uhz, Axx))));
+  const float2 a_yyz = fma2(ryy, uez, mul2(k, fma2(mul2(two, uhy), Ayz, mul2(uhz, Ayy))));
+  const float2 a_yyx = fma2(ryy, uex, mul2(k, fma2(mul2(two, uhy), Axy, mul2(uhx, Ayy))));
+  const float2 a_zzx = fma2(rzz, uex, mul2(k, fma2(mul2(two, uhz), Axz, mul2(uhx, Azz))));
+  float2 bp[6], bxyz = bc2(0.f);
+  if constexpr (Q == 19) {
+    const float2 c3 = bc2(3.f);
+    bp[0] = mul2(c3, fma2(two, a_xxy, a_zzy));
+    bp[1] = mul2(c3, fma2(two, a_zzy, a_xxy));
+    bp[2] = mul2(c3, fma2(two, a_xxz, a_yyz));
+    bp[3] = mul2(c3, fma2(two, a_yyz, a_xxz));
+    bp[4] = mul2(c3, fma2(two, a_yyx, a_zzx));
+    bp[5] = mul2(c3, fma2(two, a_zzx, a_yyx));
+  } else {
+    const float2 c45 = bc2(4.5f);
+    bp[0] = mul2(c45, a_xxy);
+    bp[1] = mul2(c45, a_zzy);
+    bp[2] = mul2(c45, a_xxz);
+    bp[3] = mul2(c45, a_yyz);
+    bp[4] = mul2(c45, a_yyx);
+    bp[5] = mul2(c45, a_zzx);
+    const float2 a_xyz = fma2(mul2(mul2(rho, uex), uey), uez, mul2(k, fma2(uhx, Ayz, fma2(uhy, Axz, mul2(uhz, Axy)))));
+    bxyz = mul2(bc2(27.f), a_xyz);
+  }
+  h[0] = mul2(bc2(wgt<Q, float>(0)), base);
+  sfor<1, H + 1>([&](auto I) {
+    constexpr int i = decltype(I)::value, cx = Lat<Q>::cx(i), cy = Lat<Q>::cy(i), cz = Lat<Q>::cz(i);
+    static_assert(csign<Q, i>() > 0, "the first half of the velocity set has a positive leading component");
+    const float2 cu = cdot2<Q, i>(uex, uey, uez);
+    float2 cac = bc2(0.f);
+    if constexpr (cx != 0) cac = add2(cac, Axx);
+    if constexpr (cy != 0) cac = add2(cac, Ayy);
+    if constexpr (cz != 0) cac = add2(cac, Azz);
+    if constexpr (cx * cy != 0) cac = accm2<2 * cx * cy>(cac, Axy);
+    if constexpr (cx * cz != 0) cac = accm2<2 * cx * cz>(cac, Axz);
+    if constexpr (cy * cz != 0) cac = accm2<2 * cy * cz>(cac, Ayz);
+    const float2 sym = fma2(k45, cac, fma2(r45, mul2(cu, cu), base));
+    float2 t3 = mul2(r3, cu);
+    t3 = accm2<h3_m<Q, i, 0>()>(t3, bp[0]);
+    t3 = accm2<h3_m<Q, i, 1>()>(t3, bp[1]);
+    t3 = accm2<h3_m<Q, i, 2>()>(t3, bp[2]);
+    t3 = accm2<h3_m<Q, i, 3>()>(t3, bp[3]);
+    t3 = accm2<h3_m<Q, i, 4>()>(t3, bp[4]);
+    t3 = accm2<h3_m<Q, i, 5>()>(t3, bp[5]);
+    if constexpr (Q == 27) t3 = accm2<cx * cy * cz>(t3, bxyz);
+    const float2 w = bc2(wgt<Q, float>(i));
+    h[i] = mul2(w, add2(sym, t3));
+    h[i + H] = mul2(w, sub2(sym, t3));
+  });
+}
+
+// collide_hrr for two cells; S holds the six strain components of both cells (unused when sigma =
+// 1). Returns false when either cell's density or velocity is not finite; ur* = reported velocity.
+template <int Q>
+__device__ __forceinline__ bool collide_hrr_x2(float2* h, float2 gamma, const Args& a, const float2* S, float2& urx,
+                                               float2& ury, float2& urz) {
+  constexpr int H = Lat<Q>::H;
+  const float2 z2 = bc2(0.f);
+  float2 drho = h[0], jx = z2, jy = z2, jz = z2;
+  float2 sxx = z2, syy = z2, szz = z2, sxy = z2, sxz = z2, syz = z2;
+  sfor<1, H + 1>([&](auto I) {
+    constexpr int i = decltype(I)::value, cx = Lat<Q>::cx(i), cy = Lat<Q>::cy(i), cz = Lat<Q>::cz(i);
+    const float2 sp = add2(h[i], h[i + H]), dp = sub2(h[i], h[i + H]);
+    drho = add2(drho, sp);
+    if constexpr (cx != 0) { jx = acc2<cx>(jx, dp); sxx = add2(sxx, sp); }
+    if constexpr (cy != 0) { jy = acc2<cy>(jy, dp); syy = add2(syy, sp); }
+    if constexpr (cz != 0) { jz = acc2<cz>(jz, dp); szz = add2(szz, sp); }
+    if constexpr (cx * cy != 0) sxy = acc2<cx * cy>(sxy, sp);
+    if constexpr (cx * cz != 0) sxz = acc2<cx * cz>(sxz, sp);
+    if constexpr (cy * cz != 0) syz = acc2<cy * cz>(syz, sp);
+  });
+  const float2 one = bc2(1.f);
+  const float2 rho = add2(one, drho), ir = rcp2(rho);
+  const float2 ux = mul2(jx, ir), uy = mul2(jy, ir), uz = mul2(jz, ir);
+  const float2 d3 = mul2(drho, bc2(1.f / 3.f));
+  const float2 rux = mul2(rho, ux), ruy = mul2(rho, uy), ruz = mul2(rho, uz);
+  float2 A[6];
+  A[0] = sub2(sxx, fma2(rux, ux, d3));
+  A[1] = sub2(syy, fma2(ruy, uy, d3));
+  A[2] = sub2(szz, fma2(ruz, uz, d3));
+  A[3] = sub2(sxy, mul2(rux, uy));
+  A[4] = sub2(sxz, mul2(rux, uz));
+  A[5] = sub2(syz, mul2(ruy, uz));
+  const float t0 = a.tau0.f;
+  float2 tau = bc2(t0);
+  if (a.use_smag != 0) {
+    const float2 off = fma2(A[3], A[3], fma2(A[4], A[4], mul2(A[5], A[5])));
+    const float2 pn = sqrt2(fma2(bc2(2.f), off, fma2(A[0], A[0], fma2(A[1], A[1], mul2(A[2], A[2])))));
+    tau = mul2(bc2(0.5f), add2(bc2(t0), sqrt2(fma2(bc2(a.smag.f), mul2(pn, ir), bc2(t0 * t0)))));
+  }
+  if (a.hybrid != 0) {
+    const float2 sg = bc2(a.sigma.f);
+    const float2 fd = mul2(sub2(one, sg), mul2(bc2(-2.f / 3.f), mul2(rho, tau)));
+    sfor<0, 6>([&](auto I) { A[I] = fma2(sg, A[I], mul2(fd, S[I])); });
+  }
+  const float2 k = sub2(one, rcp2(tau));
+  const float2 uhx = mul2(gamma, ux), uhy = mul2(gamma, uy), uhz = mul2(gamma, uz);
+  hrr_relax_x2<Q>(h, drho, rho, fma2(bc2(a.fx.f), ir, uhx), fma2(bc2(a.fy.f), ir, uhy), fma2(bc2(a.fz.f), ir, uhz), uhx,
+                  uhy, uhz, k, A);
+  const float2 hf = mul2(bc2(0.5f), ir);
+  urx = fma2(bc2(a.fx.f), hf, ux);
+  ury = fma2(bc2(a.fy.f), hf, uy);
+  urz = fma2(bc2(a.fz.f), hf, uz);
+  const float2 chk = add2(add2(abs2(rho), abs2(urx)), add2(abs2(ury), abs2(urz)));
+  return chk.x < 1e30f && chk.y < 1e30f;
+}
+
 // Finite-difference strain (xx, yy, zz, xy, xz, yz) of cell (x, y, z) from the previous step's
 // velocity field (3 component arrays of N). A neighbour x +- e_b is usable when it lies inside the
 // domain after periodic wrap and is not SOLID: central difference with both, one-sided with one,

@@ -71,6 +71,16 @@ struct Impl {
   }
   static void step_bulk(const Args& a, int odd, cudaStream_t s) {
     if (a.model != 0) {
+      if constexpr (sizeof(S) == 2) {
+        if (a.idx32 && a.nx % 2 == 0 && a.N % 2 == 0) {
+          const int bx = (a.nx / 2) >= 64 ? 64 : (((a.nx / 2) + 31) / 32) * 32;
+          const dim3 b(bx, BULK_THREADS / bx, 1);
+          const dim3 g((a.nx / 2 + b.x - 1) / b.x, (a.ny + b.y - 1) / b.y, a.nz);
+          if (odd) k_bulk2<Q, S, true, true><<<g, b, 0, s>>>(a);
+          else k_bulk2<Q, S, false, true><<<g, b, 0, s>>>(a);
+          return;
+        }
+      }
       if (odd) k_bulk_hrr<Q, S, true><<<bulk_grid(a), bulk_block(a), 0, s>>>(a);
       else k_bulk_hrr<Q, S, false><<<bulk_grid(a), bulk_block(a), 0, s>>>(a);
       return;

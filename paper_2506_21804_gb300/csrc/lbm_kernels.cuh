@@ -294,9 +294,9 @@ __device__ __forceinline__ void collide_any(const Args& a, int kind, uint8_t t, 
     if constexpr (HRR) collide_wall_hrr<Q, C>(h, a, ws, rho, urx, ury, urz);
     else collide_wall_state<Q, C>(h, a, ws, rho, urx, ury, urz);
   } else if constexpr (HRR) {
-    C S[6] = {C(0), C(0), C(0), C(0), C(0), C(0)};
-    if (a.hybrid) strain_fd<C>(a, x, y, z, n, (t & T_NEAR) != 0, S);
-    collide_hrr<Q, C>(h, gamma_at<C>(a, n), a, S, rho, urx, ury, urz);
+    C Sfd[6] = {C(0), C(0), C(0), C(0), C(0), C(0)};
+    if (a.hybrid) strain_fd<C>(a, x, y, z, n, (t & T_NEAR) != 0, Sfd);
+    collide_hrr<Q, C>(h, gamma_at<C>(a, n), a, Sfd, rho, urx, ury, urz);
   } else {
     collide_fluid<Q, C>(h, gamma_at<C>(a, n), a, rho, urx, ury, urz);
   }
@@ -331,9 +331,9 @@ __device__ __forceinline__ void list_cell_inline(const Args& a, S* f, int x, int
     if (kind == K_WALL && a.wm) {
       collide_wall_hrr<Q, C>(h, a, cptr<C>(a.wst) + (long long)WALL_STATE * k, rho, urx, ury, urz);
     } else {
-      C S[6] = {C(0), C(0), C(0), C(0), C(0), C(0)};
-      if (a.hybrid) strain_fd<C>(a, x, y, z, n, (t & T_NEAR) != 0, S);
-      collide_hrr<Q, C>(h, gamma_at<C>(a, n), a, S, rho, urx, ury, urz);
+      C Sfd[6] = {C(0), C(0), C(0), C(0), C(0), C(0)};
+      if (a.hybrid) strain_fd<C>(a, x, y, z, n, (t & T_NEAR) != 0, Sfd);
+      collide_hrr<Q, C>(h, gamma_at<C>(a, n), a, Sfd, rho, urx, ury, urz);
     }
     record_velocity<C>(a, n, urx, ury, urz);
   } else {
@@ -459,7 +459,7 @@ __device__ __forceinline__ void pair_load(const Args& a, const S* f, int x0, int
   }
 }
 
-template <int Q, class S, bool ODD>
+template <int Q, class S, bool ODD, bool HRR = false>
 __device__ __forceinline__ void pair_update(const Args& a, S* f, int x0, int y, int z, typename Pair<S>::V* raw) {
   using P = Pair<S>;
   const unsigned us = unsigned(a.stride);
@@ -467,7 +467,27 @@ __device__ __forceinline__ void pair_update(const Args& a, S* f, int x0, int y, 
   bool ok;
   const float2 gam = a.gamma ? make_float2(static_cast<const float*>(a.gamma)[un], static_cast<const float*>(a.gamma)[un + 1])
                              : bc2(1.f);
-  {
+  if constexpr (HRR) {
+    // both cells are plain (not NEAR): all six neighbours of each are usable for the strain
+    float2 S2[6];
+    if (a.hybrid) {
+      float s0[6], s1[6];
+      strain_fd<float>(a, x0, y, z, un, false, s0);
+      strain_fd<float>(a, x0 + 1, y, z, un + 1, false, s1);
+      sfor<0, 6>([&](auto I) { S2[I] = make_float2(s0[I], s1[I]); });
+    } else {
+      sfor<0, 6>([&](auto I) { S2[I] = bc2(0.f); });
+    }
+    float2 h[Q], ux, uy, uz;
+    sfor<0, Q>([&](auto I) { h[I] = make_float2(P::lof(raw[I]), P::hif(raw[I])); });
+    ok = collide_hrr_x2<Q>(h, gam, a, S2, ux, uy, uz);
+    sfor<0, Q>([&](auto I) { raw[I] = P::pack(h[I].x, h[I].y); });
+    float2* w = static_cast<float2*>(a.uvel_wr);  // N even, x0 even: pairs are 8-byte aligned
+    const long long N2 = a.N / 2, p2 = un / 2;
+    w[p2] = ux;
+    w[N2 + p2] = uy;
+    w[2 * N2 + p2] = uz;
+  } else {
     float2 h[Q];
     sfor<0, Q>([&](auto I) { h[I] = make_float2(P::lof(raw[I]), P::hif(raw[I])); });
     ok = collide_fluid_x2<Q>([&](int i) { return h[i]; }, [&](int i, float2 v) { h[i] = v; }, gam, a);
@@ -508,8 +528,8 @@ __device__ __forceinline__ void pair_update(const Args& a, S* f, int x0, int y, 
 #ifndef LBM_BULK2_MINB_ODD
 #define LBM_BULK2_MINB_ODD 7
 #endif
-template <int Q, class S, bool ODD>
-__global__ void __launch_bounds__(BULK_THREADS, (Q == 19 ? (ODD ? LBM_BULK2_MINB_ODD : LBM_BULK2_MINB_EVEN) : 4))
+template <int Q, class S, bool ODD, bool HRR = false>
+__global__ void __launch_bounds__(BULK_THREADS, (Q == 19 && !HRR ? (ODD ? LBM_BULK2_MINB_ODD : LBM_BULK2_MINB_EVEN) : 4))
     k_bulk2(const Args a) {
   const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -519,13 +539,13 @@ __global__ void __launch_bounds__(BULK_THREADS, (Q == 19 ? (ODD ? LBM_BULK2_MINB
   S* f = static_cast<S*>(a.f);
   const unsigned short tt = *reinterpret_cast<const unsigned short*>(a.type + n0);
   if (tt) {
-    bulk_cell<Q, S, ODD>(a, f, x0, y, z, n0, uint8_t(tt & 0xff));
-    bulk_cell<Q, S, ODD>(a, f, x0 + 1, y, z, n0 + 1, uint8_t(tt >> 8));
+    bulk_cell<Q, S, ODD, HRR>(a, f, x0, y, z, n0, uint8_t(tt & 0xff));
+    bulk_cell<Q, S, ODD, HRR>(a, f, x0 + 1, y, z, n0 + 1, uint8_t(tt >> 8));
     return;
   }
   typename Pair<S>::V raw[Q];
   pair_load<Q, S, ODD>(a, f, x0, y, z, raw);
-  pair_update<Q, S, ODD>(a, f, x0, y, z, raw);
+  pair_update<Q, S, ODD, HRR>(a, f, x0, y, z, raw);
 }
 
 // Wall-model state of every WALL entry from the previous step's reference velocities (fused mode).

@@ -161,11 +161,14 @@ def test_16bit_channel_mean_profile_vs_fp32(storage, bound):
     assert np.abs(got - ref).max() < bound * np.abs(ref).max()
 
 
-def test_16bit_matches_oracle_storage_emulation_one_step():
+@pytest.mark.parametrize("model,sigma", [(0, 1.0), (1, 1.0), (1, 0.5)])
+def test_16bit_matches_oracle_storage_emulation_one_step(model, sigma):
     """One step of FP16 storage equals the oracle's FP16-rounded storage to within a few units in
     the last place of the stored deviation: FP32 (GPU) and FP64 (oracle) arithmetic can round the
-    initial state and the stored result to neighbouring FP16 values."""
+    initial state and the stored result to neighbouring FP16 values. BGK and the HRR collision (with
+    and without the finite-difference strain), both through the paired 16-bit kernel."""
     w = I.random_box(12, 8, 6, seed=9, q=19, solid_frac=0.1, tau=0.7, cs=0.1)
+    w.model, w.sigma = model, sigma
     g = gpu_from(w, lbm.F16)
     o = oracle_from(w, storage=2)
     g.step(1)
