@@ -263,14 +263,15 @@ def secondary(lbm, I, torch):
     # hybrid recursive regularised collision on the same channel: local stress only (sigma = 1) and
     # blended with the finite-difference strain (sigma = 1/2, reads and writes the velocity field)
     for sg in (1.0, 0.5):
-        lat = lbm.Lattice.from_workload(w, storage=lbm.F32)
-        lat.set_collision(lbm.HRR, sg)
-        g, ms = timed_glups(lat, 40, 3)
-        info = lat.info()
-        nb = info["N"] - info["n_solid"] - info["n_list"]
-        bw = (nb * (152 + (24 if sg < 1 else 0)) + info["N"]) / (ms[0] / 40 * 1e-3) / 1e9
-        out[f"channel_hrr_sigma{sg:g}_fp32"] = {"glups": g, "vs_bgk_fp32": g / g32, "interior_kernel_gbs": bw}
-        lat.close()
+        for name, st, pb in (("fp32", lbm.F32, 152), ("fp16", lbm.F16, 76)):
+            lat = lbm.Lattice.from_workload(w, storage=st)
+            lat.set_collision(lbm.HRR, sg)
+            g, ms = timed_glups(lat, 40, 3)
+            info = lat.info()
+            nb = info["N"] - info["n_solid"] - info["n_list"]
+            bw = (nb * (pb + (24 if sg < 1 else 0)) + info["N"]) / (ms[0] / 40 * 1e-3) / 1e9
+            out[f"channel_hrr_sigma{sg:g}_{name}"] = {"glups": g, "vs_bgk_fp32": g / g32, "interior_kernel_gbs": bw}
+            lat.close()
     # precision configuration: the canopy generator on 1024 x 512 x 256, 16-bit storage against FP32
     wp = I.canopy(nx=1024, ny=512, nz=256, q=19, seed=2506, dtype=np.float32)
     lat = lbm.Lattice.from_workload(wp, storage=lbm.F32)
