@@ -197,13 +197,15 @@ def run_reference(args):
 
 
 # ---- GPU arm ---------------------------------------------------------------------------------------------------
-def interior_kernel_name(args, nx, hrr):
-    sixteen = args.storage in ("f16", "bf16")
-    if hrr:
-        return "k_bulk2<HRR>" if (sixteen and nx % 2 == 0) else "k_bulk_hrr"
-    if args.kernel == "staged" and nx % 128 == 0:
-        return "k_bulk_tma"
-    return "k_bulk2" if (sixteen and nx % 2 == 0) else "k_bulk"
+def interior_kernel_name(code, q, storage, hrr):
+    s = {"f32": "float", "f16": "__half", "bf16": "__nv_bfloat16"}[storage]
+    if code == 2:
+        return f"k_bulk_tma<{q}, {s}>"
+    if code == 1:
+        return f"k_bulk2<{q}, {s}{', HRR' if hrr else ''}>"
+    return f"k_bulk_hrr<{q}, {s}>" if hrr else f"k_bulk<{q}, {s}>"
+
+
 def timed_glups(lat, steps, warmup):
     lat.step(warmup)
     lat.sync()
@@ -383,6 +385,7 @@ def main():
         lat.set_vortex_inlet(args.vortex, 4.0, 0.1, 2506)
         wname += f", vortex inlet n={args.vortex}"
     info = lat.info()
+    kname = interior_kernel_name(lat.interior_kernel(), args.lattice, args.storage, hrr)
     lat.step(args.warmup)
     lat.sync()
 
@@ -405,7 +408,7 @@ def main():
     bulk_ms = ms[0] / args.steps
     peak, peak_src = peaks()
     achieved = bytes_bulk / (bulk_ms * 1e-3) / 1e9
-    traffic = kernel_traffic("k_bulk", "channel256") if headline else None
+    traffic = kernel_traffic("interior", "channel256") if headline else None
     step_bytes = (info["N"] - info["n_solid"]) * per_cell + info["N"]
 
     # end to end through the C ABI with pinned host buffers: geometry + initial state in, fields out
@@ -444,7 +447,7 @@ def main():
         "config": {"workload": wname, "kernel": args.kernel, "cells": w.N, "parallelism": f"replicas x{world}",
                    "l2": "state of 2.6 GB > 129 MB L2 between steps, no flush needed",
                    "non_solid_cells": info["N"] - info["n_solid"], "boundary_list_cells": info["n_list"]},
-        "roofline": {"bound": "hbm", "kernel": interior_kernel_name(args, w.nx, hrr) + " (interior cells)", "achieved": achieved, "peak": peak,
+        "roofline": {"bound": "hbm", "kernel": kname + " (interior cells)", "achieved": achieved, "peak": peak,
                      "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "bytes_per_launch": bytes_bulk, "launch_ms": bulk_ms,
                      "share_of_step": ms[0] / ms[2]},

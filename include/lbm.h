@@ -202,6 +202,11 @@ int lbm_set_option(lbm_ctx* ctx, int option, int value);
 /* Counters: out[0] N, [1] boundary-list length, [2] WALL, [3] reference cells, [4] INFLOW,
  * [5] OUTFLOW, [6] SOLID, [7] steps done, [8] storage, [9] lattice q. */
 int lbm_info(lbm_ctx* ctx, int64_t out[10]);
+/* Interior kernel the next step runs: 0 one cell per thread, 1 cell pairs (two cells per thread with
+ * packed FP32 arithmetic, FP32 or 16-bit storage, when at most 2 % of the 64-cell x-groups would mix
+ * pairs of plain cells with pairs on the per-cell path; nx even, indices within 32 bits), 2 the
+ * staged kernel (LBM_OPT_KERNEL = 2). Negative on a null context. */
+int lbm_interior_kernel(lbm_ctx* ctx);
 /* Integer maps for bit-exact tests: which = 0 type byte per cell (N; bits 0-2 kind, bit 3
  * reference cell, bit 4 a source position is solid or outside, bit 5 boundary list, bit 6 list cell
  * updated by the interior kernel: INFLOW/OUTFLOW cells, and WALL/reference cells in 32-cell

@@ -100,6 +100,7 @@ struct lbm_ctx {
   DevBuf uvel0, uvel1;  // HRR velocity fields (step t reads uvel[t & 1], writes the other)
   DevBuf uin_a, uin_b, vort, vpart;  // vortex inlet: current/previous inlet fields, vortex list, partial fields
   DevBuf geo_counts, geo_sub, geo_kinds;  // geometry set-up scratch (per-block counts, kind counters)
+  double pair_mixed = 1.0;  // fraction of 64-cell x-groups mixing plain and per-cell pairs
   int n_sub = 0, n_wall = 0, n_bc = 0;
   bool has_gamma = false, has_wdist = false;
   int n_list = 0;
@@ -148,6 +149,19 @@ GeoArgs geo_args(const lbm_ctx* c) {
   for (int i = 0; i < 6; ++i) g.face[i] = c->face[i];
   g.q = c->q;
   return g;
+}
+
+// The paired interior kernel (two cells per thread, packed FP32 collision) runs when nx is even, the
+// indices fit 32 bits, the storage is not FP64, and few warps would mix plain pairs with pairs on the
+// per-cell path (a mixed warp runs both): at most PAIR_MIX_MAX of the 64-cell x-groups mixed (the
+// plane channel: none; a city canopy or a duct with inlet and outlet planes: many).
+#ifndef LBM_PAIR_MIX_MAX
+#define LBM_PAIR_MIX_MAX 0.02
+#endif
+bool pairs_selected(const lbm_ctx* c) {
+  const bool idx32 = (unsigned long long)c->q * (unsigned long long)c->stride < (1ull << 32) && c->N < (1ll << 31);
+  if (c->storage == LBM_F64 || c->nx % 2 != 0 || !idx32 || c->kernel != 0) return false;
+  return c->pair_mixed <= LBM_PAIR_MIX_MAX;
 }
 
 Args make_args(const lbm_ctx* c) {
@@ -200,6 +214,7 @@ Args make_args(const lbm_ctx* c) {
   a.sigma = c->sigma;
   a.uvel_rd = (c->t & 1) ? c->uvel1.p : c->uvel0.p;
   a.uvel_wr = (c->t & 1) ? c->uvel0.p : c->uvel1.p;
+  a.pairs = pairs_selected(c) ? 1 : 0;
   return a;
 }
 
@@ -372,6 +387,14 @@ int build_geometry(lbm_ctx* c) {
     CK(cudaStreamSynchronize(s));
     CK(cudaGetLastError());
     for (int i = 0; i < 5; ++i) c->counts[i] = (long long)hk[i];
+    c->pair_mixed = 1.0;
+    if (c->nx % 2 == 0) {
+      geo_pair_mix(g, type, static_cast<unsigned long long*>(kc.p), s);
+      unsigned long long pm[2];
+      CK(cudaMemcpyAsync(pm, kc.p, sizeof(pm), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      c->pair_mixed = pm[0] ? double(pm[1]) / double(pm[0]) : 1.0;
+    }
   }
   c->type_host_valid = false;
   return LBM_OK;
@@ -862,6 +885,15 @@ int lbm_set_option(lbm_ctx* c, int option, int value) {
       return LBM_OK;
   }
   return fail(LBM_EINVAL, "unknown option %d", option);
+}
+
+int lbm_interior_kernel(lbm_ctx* c) {
+  if (!c) {
+    fail(LBM_EINVAL, "null context");
+    return -1;
+  }
+  if (c->kernel == 2) return 2;
+  return pairs_selected(c) ? 1 : 0;
 }
 
 int lbm_info(lbm_ctx* c, int64_t out[10]) {

@@ -188,6 +188,7 @@ struct Args {
   Param sigma;             // hybridisation factor
   const void* uvel_rd;     // C[3][N] velocity field of the previous step
   void* uvel_wr;           // C[3][N] velocity field written by this step
+  int pairs;               // interior kernel over cell pairs (nx even, 32-bit indices, few mixed warps)
 };
 
 // ---- AA-pattern slot map ------------------------------------------------------------------------------

@@ -303,6 +303,36 @@ __global__ void __launch_bounds__(SUB_THREADS) k_sub_write(const uint8_t* type, 
     if (f[c]) dst[c][wo[w][c] + __popc(b[c] & ((1u << lane) - 1u))] = k;
 }
 
+// Groups of 64 cells along x (the cells of one warp of the paired kernels) that mix plain cell
+// pairs (both cells plain FLUID, type byte 0) with pairs that take the per-cell path: such a warp
+// runs both paths. out[0] += groups, out[1] += mixed groups. nx even.
+__global__ void k_pair_mix(const GeoArgs g, const uint8_t* type, unsigned long long* out) {
+  const int groups = (g.nx + 63) / 64;
+  const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  unsigned long long mixed = 0, tot = 0;
+  if (j < (long long)groups * g.ny * g.nz) {
+    const long long row = j / groups;
+    const int g0 = int(j - row * groups) * 64;
+    const int g1 = g0 + 64 < g.nx ? g0 + 64 : g.nx;
+    const unsigned short* t2 = reinterpret_cast<const unsigned short*>(type + row * g.nx);
+    bool plain = false, other = false;
+    for (int x = g0; x < g1; x += 2) {
+      if (t2[x >> 1] == 0) plain = true;
+      else other = true;
+    }
+    tot = 1;
+    mixed = (plain && other) ? 1 : 0;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    tot += __shfl_down_sync(0xffffffffu, tot, o);
+    mixed += __shfl_down_sync(0xffffffffu, mixed, o);
+  }
+  if ((threadIdx.x & 31) == 0 && tot) {
+    atomicAdd(&out[0], tot);
+    atomicAdd(&out[1], mixed);
+  }
+}
+
 // Counts of WALL, reference, INFLOW, OUTFLOW and SOLID cells.
 __global__ void k_count_kinds(const uint8_t* type, long long N, unsigned long long* out) {
   __shared__ unsigned long long sc[5];
@@ -397,6 +427,12 @@ void geo_sub_write(const uint8_t* type, const long long* lcell, int n_list, cons
                    int* lbc, cudaStream_t s) {
   if (n_list <= 0) return;
   k_sub_write<<<nblocks(n_list, SUB_THREADS), SUB_THREADS, 0, s>>>(type, lcell, n_list, offsets, lsub, lwall, lbc);
+}
+
+void geo_pair_mix(const GeoArgs& g, const uint8_t* type, unsigned long long* out, cudaStream_t s) {
+  cudaMemsetAsync(out, 0, 2 * sizeof(unsigned long long), s);
+  const long long groups = (long long)((g.nx + 63) / 64) * g.ny * g.nz;
+  k_pair_mix<<<nblocks(groups, 256), 256, 0, s>>>(g, type, out);
 }
 
 void geo_count_kinds(const uint8_t* type, long long N, unsigned long long* out, cudaStream_t s) {

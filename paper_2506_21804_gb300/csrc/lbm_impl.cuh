@@ -71,8 +71,8 @@ struct Impl {
   }
   static void step_bulk(const Args& a, int odd, cudaStream_t s) {
     if (a.model != 0) {
-      if constexpr (sizeof(S) == 2) {
-        if (a.idx32 && a.nx % 2 == 0 && a.N % 2 == 0) {
+      if constexpr (sizeof(S) <= 4) {
+        if (a.pairs && a.N % 2 == 0) {
           const int bx = (a.nx / 2) >= 64 ? 64 : (((a.nx / 2) + 31) / 32) * 32;
           const dim3 b(bx, BULK_THREADS / bx, 1);
           const dim3 g((a.nx / 2 + b.x - 1) / b.x, (a.ny + b.y - 1) / b.y, a.nz);
@@ -89,8 +89,8 @@ struct Impl {
     if (L.stages >= 2) {
       if (odd ? launch_tma<true>(a, L, s) : launch_tma<false>(a, L, s)) return;
     }
-    if constexpr (sizeof(S) == 2) {
-      if (a.idx32 && a.nx % 2 == 0) {
+    if constexpr (sizeof(S) <= 4) {
+      if (a.pairs) {
         Args h = a;
         h.nx = a.nx;  // launch shape over cell pairs
         dim3 b = bulk_block(a);

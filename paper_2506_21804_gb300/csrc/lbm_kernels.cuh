@@ -418,6 +418,18 @@ template <> struct Pair<__half> {
   static __device__ __forceinline__ V with_hi(V v, float x) { return __halves2half2(__low2half(v), __float2half_rn(x)); }
   static __device__ __forceinline__ V pack(float lo, float hi) { return __floats2half2_rn(lo, hi); }
 };
+// FP32 storage: the pair is a float2 (8-byte accesses), packing and unpacking are moves.
+template <> struct Pair<float> {
+  using V = float2;
+  static __device__ __forceinline__ V ld(const float* p) { return *reinterpret_cast<const float2*>(p); }
+  static __device__ __forceinline__ void st(float* p, V v) { *reinterpret_cast<float2*>(p) = v; }
+  static __device__ __forceinline__ V make(float lo, float hi) { return make_float2(lo, hi); }
+  static __device__ __forceinline__ float lo(V v) { return v.x; }
+  static __device__ __forceinline__ float hi(V v) { return v.y; }
+  static __device__ __forceinline__ float lof(V v) { return v.x; }
+  static __device__ __forceinline__ float hif(V v) { return v.y; }
+  static __device__ __forceinline__ V pack(float lo, float hi) { return make_float2(lo, hi); }
+};
 template <> struct Pair<__nv_bfloat16> {
   using V = __nv_bfloat162;
   static __device__ __forceinline__ V ld(const __nv_bfloat16* p) { return *reinterpret_cast<const __nv_bfloat162*>(p); }

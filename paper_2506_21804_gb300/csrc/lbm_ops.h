@@ -68,6 +68,8 @@ void geo_sub_count(const uint8_t* type, const long long* lcell, int n_list, int*
 void geo_sub_write(const uint8_t* type, const long long* lcell, int n_list, const int* offsets, int* lsub, int* lwall,
                    int* lbc, cudaStream_t);
 void geo_count_kinds(const uint8_t* type, long long N, unsigned long long* out, cudaStream_t);
+// 64-cell x-groups and the groups mixing plain pairs with per-cell pairs (nx even): out[0], out[1]
+void geo_pair_mix(const GeoArgs&, const uint8_t* type, unsigned long long* out, cudaStream_t);
 // source map (debug): for each (i, n): source population and cell, -1 for solid cells
 void geo_source_map(const GeoArgs&, const uint8_t* type, int64_t* src_dir, int64_t* src_cell, cudaStream_t);
 // FP64 final reduction of nblk partials (4 doubles each) into out[4], fixed order

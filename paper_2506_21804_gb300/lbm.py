@@ -46,6 +46,7 @@ SIGNATURES = {
     "lbm_last_error": (ctypes.c_char_p, []),
     "lbm_set_precision": (_i, [_p, _i]),
     "lbm_set_collision": (_i, [_p, _i, _d]),
+    "lbm_interior_kernel": (_i, [_p]),
     "lbm_set_vortex_inlet": (_i, [_p, _i, _d, _d, ctypes.c_ulonglong]),
     "lbm_set_permeability": (_i, [_p, _p]),
     "lbm_set_permeability_ex": (_i, [_p, _p, _i]),
@@ -205,6 +206,13 @@ class Lattice:
 
     def set_wall_model(self, kappa=0.41, E=9.52):
         _check(lib().lbm_set_wall_model(self.h, float(kappa), float(E)))
+
+    def interior_kernel(self):
+        """0: one cell per thread, 1: cell pairs, 2: staged."""
+        k = lib().lbm_interior_kernel(self.h)
+        if k < 0:
+            raise LBMError(EINVAL, lib().lbm_last_error().decode())
+        return k
 
     def set_vortex_inlet(self, n, sigma=4.0, intensity=0.1, seed=0):
         """Vortex-method inlet with n vortices per step (0: off)."""
