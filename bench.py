@@ -201,6 +201,8 @@ def interior_kernel_name(code, q, storage, hrr):
     s = {"f32": "float", "f16": "__half", "bf16": "__nv_bfloat16"}[storage]
     if code == 2:
         return f"k_bulk_tma<{q}, {s}>"
+    if code == 3:
+        return f"k_bulk4<{q}, {s}> (even steps) + k_bulk2<{q}, {s}> (odd steps)"
     if code == 1:
         return f"k_bulk2<{q}, {s}{', HRR' if hrr else ''}>"
     return f"k_bulk_hrr<{q}, {s}>" if hrr else f"k_bulk<{q}, {s}>"

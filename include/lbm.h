@@ -205,7 +205,9 @@ int lbm_info(lbm_ctx* ctx, int64_t out[10]);
 /* Interior kernel the next step runs: 0 one cell per thread, 1 cell pairs (two cells per thread with
  * packed FP32 arithmetic, FP32 or 16-bit storage, when at most 2 % of the 64-cell x-groups would mix
  * pairs of plain cells with pairs on the per-cell path; nx even, indices within 32 bits), 2 the
- * staged kernel (LBM_OPT_KERNEL = 2). Negative on a null context. */
+ * staged kernel (LBM_OPT_KERNEL = 2), 3 four cells per thread on even steps and cell pairs on odd
+ * steps (where 1 would be chosen, for D3Q19 BGK with FP16 or BF16 storage and nx a multiple of 4).
+ * Negative on a null context. */
 int lbm_interior_kernel(lbm_ctx* ctx);
 /* Integer maps for bit-exact tests: which = 0 type byte per cell (N; bits 0-2 kind, bit 3
  * reference cell, bit 4 a source position is solid or outside, bit 5 boundary list, bit 6 list cell

@@ -893,7 +893,10 @@ int lbm_interior_kernel(lbm_ctx* c) {
     return -1;
   }
   if (c->kernel == 2) return 2;
-  return pairs_selected(c) ? 1 : 0;
+  if (!pairs_selected(c)) return 0;
+  const bool quads = (c->storage == LBM_F16 || c->storage == LBM_BF16) && c->q == 19 && c->model == LBM_BGK &&
+                     c->nx % 4 == 0;
+  return quads ? 3 : 1;
 }
 
 int lbm_info(lbm_ctx* c, int64_t out[10]) {

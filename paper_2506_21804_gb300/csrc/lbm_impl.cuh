@@ -97,6 +97,19 @@ struct Impl {
         int bx = (a.nx / 2) >= 64 ? 64 : (((a.nx / 2) + 31) / 32) * 32;
         b = dim3(bx, BULK_THREADS / bx, 1);
         const dim3 g((a.nx / 2 + b.x - 1) / b.x, (a.ny + b.y - 1) / b.y, a.nz);
+        if constexpr (sizeof(S) == 2 && Q == 19) {
+          if (a.nx % 4 == 0 && !odd) {
+            // 16-bit storage, even steps: four cells per thread (k_bulk4), 32 quads x 4 rows per CTA.
+            // Odd steps stay with cell pairs: the quad's neighbour addressing spills at 80 registers
+            // there (measured on the 256^3 FP16 channel: even 111 us vs 121 us, odd 156 us vs 149 us
+            // per 8.4M cells, quads vs pairs).
+            const int qx = (a.nx / 4) >= 32 ? 32 : (((a.nx / 4) + 31) / 32) * 32;
+            const dim3 b4(qx, BULK_THREADS / qx, 1);
+            const dim3 g4((a.nx / 4 + b4.x - 1) / b4.x, (a.ny + b4.y - 1) / b4.y, a.nz);
+            k_bulk4<Q, S, false><<<g4, b4, 0, s>>>(h);
+            return;
+          }
+        }
         if (odd) k_bulk2<Q, S, true><<<g, b, 0, s>>>(h);
         else k_bulk2<Q, S, false><<<g, b, 0, s>>>(h);
         return;

@@ -560,6 +560,165 @@ __global__ void __launch_bounds__(BULK_THREADS, (Q == 19 && !HRR ? (ODD ? LBM_BU
   pair_update<Q, S, ODD, HRR>(a, f, x0, y, z, raw);
 }
 
+// ---- 16-bit storage, four cells per thread ---------------------------------------------------------------
+// The thread owns cells x0 = 4j .. x0 + 3 (nx a multiple of 4): 8 bytes per population, the bytes a
+// thread of the FP32 pair kernel keeps in flight. Directions without an x-component move the four
+// values with one 8-byte access. On odd steps an x-shifted quad is one 16-bit value, the aligned
+// 32-bit word of the two middle cells, and another 16-bit value. The quad collides as two pairs in
+// turn (packed FP32 lanes, the pair kernel's arithmetic). The library launches the even-step form;
+// the odd-step form is correct but spills at this register budget and measured slower than pairs.
+struct Nbr32Quad {
+  unsigned n;  // index of x0
+  int dxm, dxp, dym, dyp, dzm, dzp;
+  __device__ __forceinline__ Nbr32Quad(const Args& a, int x0, int y, int z, unsigned n0) {
+    n = n0;
+    const int nx = a.nx, nxy = int(a.nxy);
+    dxm = x0 == 0 ? nx - 1 : -1;
+    dxp = x0 + 3 == nx - 1 ? 1 - nx : 1;
+    dym = y == 0 ? (a.ny - 1) * nx : -nx;
+    dyp = y == a.ny - 1 ? (1 - a.ny) * nx : nx;
+    dzm = z == 0 ? (a.nz - 1) * nxy : -nxy;
+    dzp = z == a.nz - 1 ? (1 - a.nz) * nxy : nxy;
+  }
+  // index of population p at cell x0 + CELL displaced by (dx, dy, dz); only x0 - 1 and x0 + 4 can wrap
+  template <int CELL, int DX, int DY, int DZ>
+  __device__ __forceinline__ unsigned at(unsigned pbase) const {
+    unsigned r = pbase + n;
+    if constexpr (CELL == 0 && DX < 0) r += unsigned(dxm);
+    else if constexpr (CELL == 3 && DX > 0) r += 3u + unsigned(dxp);
+    else r += unsigned(CELL + DX);
+    if constexpr (DY < 0) r += unsigned(dym);
+    if constexpr (DY > 0) r += unsigned(dyp);
+    if constexpr (DZ < 0) r += unsigned(dzm);
+    if constexpr (DZ > 0) r += unsigned(dzp);
+    return r;
+  }
+};
+
+template <class V> __device__ __forceinline__ V as_pair(unsigned u) {
+  V v;
+  __builtin_memcpy(&v, &u, sizeof(v));
+  return v;
+}
+template <class V> __device__ __forceinline__ unsigned as_word(V v) {
+  unsigned u;
+  __builtin_memcpy(&u, &v, sizeof(u));
+  return u;
+}
+
+// Collision of one pair held in 16-bit pair registers (cells at un, un + 1); false if not finite.
+// Each read decodes the 16-bit pair again (an opaque copy keeps the two decodes apart), so the
+// decoded populations are not held across the collision.
+template <int Q, class S>
+__device__ __forceinline__ bool pair_collide(const Args& a, unsigned un, typename Pair<S>::V* raw) {
+  using P = Pair<S>;
+  using V = typename P::V;
+  const float2 gam = a.gamma ? make_float2(static_cast<const float*>(a.gamma)[un], static_cast<const float*>(a.gamma)[un + 1])
+                             : bc2(1.f);
+  return collide_fluid_x2<Q>(
+      [&](int i) {
+        unsigned w = as_word(raw[i]);
+        asm volatile("" : "+r"(w));
+        const V v = as_pair<V>(w);
+        return make_float2(P::lof(v), P::hif(v));
+      },
+      [&](int i, float2 v) { raw[i] = P::pack(v.x, v.y); }, gam, a);
+}
+
+template <int Q, class S, bool ODD>
+__device__ __forceinline__ void quad_load(const Args& a, const S* f, int x0, int y, int z, unsigned un,
+                                          typename Pair<S>::V* ra, typename Pair<S>::V* rb) {
+  using P = Pair<S>;
+  using V = typename P::V;
+  const unsigned us = unsigned(a.stride);
+  if constexpr (!ODD) {
+    sfor<0, Q>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      const uint2 v = *reinterpret_cast<const uint2*>(f + (unsigned(i) * us + un));
+      ra[i] = as_pair<V>(v.x);
+      rb[i] = as_pair<V>(v.y);
+    });
+  } else {
+    const Nbr32Quad nb(a, x0, y, z, un);
+    sfor<0, Q>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      constexpr int cx = -Lat<Q>::cx(i), cy = -Lat<Q>::cy(i), cz = -Lat<Q>::cz(i);
+      const unsigned pb = unsigned(opp<Q>(i)) * us;
+      if constexpr (cx == 0) {
+        const uint2 v = *reinterpret_cast<const uint2*>(f + nb.at<0, 0, cy, cz>(pb));
+        ra[i] = as_pair<V>(v.x);
+        rb[i] = as_pair<V>(v.y);
+      } else {
+        const V w = P::ld(f + nb.at<1, cx, cy, cz>(pb));  // cells 1 and 2: an aligned word
+        ra[i] = P::make(f[nb.at<0, cx, cy, cz>(pb)], P::lo(w));
+        rb[i] = P::make(P::hi(w), f[nb.at<3, cx, cy, cz>(pb)]);
+      }
+    });
+  }
+}
+
+template <int Q, class S, bool ODD>
+__device__ __forceinline__ void quad_store(const Args& a, S* f, int x0, int y, int z, unsigned un,
+                                           const typename Pair<S>::V* ra, const typename Pair<S>::V* rb) {
+  using P = Pair<S>;
+  const unsigned us = unsigned(a.stride);
+  if constexpr (!ODD) {
+    sfor<0, Q>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      *reinterpret_cast<uint2*>(f + (unsigned(opp<Q>(i)) * us + un)) = make_uint2(as_word(ra[i]), as_word(rb[i]));
+    });
+  } else {
+    const Nbr32Quad nb(a, x0, y, z, un);
+    sfor<0, Q>([&](auto I) {
+      constexpr int k = decltype(I)::value;  // f*_k goes to slot (k, x + c_k)
+      constexpr int cx = Lat<Q>::cx(k), cy = Lat<Q>::cy(k), cz = Lat<Q>::cz(k);
+      const unsigned pb = unsigned(k) * us;
+      if constexpr (cx == 0) {
+        *reinterpret_cast<uint2*>(f + nb.at<0, 0, cy, cz>(pb)) = make_uint2(as_word(ra[k]), as_word(rb[k]));
+      } else {
+        f[nb.at<0, cx, cy, cz>(pb)] = P::lo(ra[k]);
+        P::st(f + nb.at<1, cx, cy, cz>(pb), P::make(P::hi(ra[k]), P::lo(rb[k])));
+        f[nb.at<3, cx, cy, cz>(pb)] = P::hi(rb[k]);
+      }
+    });
+  }
+}
+
+// Six CTAs of 128 threads per SM (80 registers): measured against 4 (128 registers), 5 (96) and 7
+// (72, more spilling) on the 256^3 FP16 channel.
+#ifndef LBM_BULK4_MINB
+#define LBM_BULK4_MINB 6
+#endif
+template <int Q, class S, bool ODD>
+__global__ void __launch_bounds__(BULK_THREADS, LBM_BULK4_MINB) k_bulk4(const Args a) {
+  static_assert(sizeof(S) == 2 && Q == 19, "four cells per thread: D3Q19, 16-bit storage");
+  const int x0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x0 >= a.nx || y >= a.ny) return;
+  const long long n0 = x0 + (long long)y * a.nx + (long long)z * a.nxy;
+  S* f = static_cast<S*>(a.f);
+  const unsigned tt = *reinterpret_cast<const unsigned*>(a.type + n0);
+  if (tt) {
+#pragma unroll 1
+    for (int c = 0; c < 4; ++c) bulk_cell<Q, S, ODD>(a, f, x0 + c, y, z, n0 + c, uint8_t(tt >> (8 * c)));
+    return;
+  }
+  typename Pair<S>::V ra[Q], rb[Q];
+  const unsigned un = unsigned(n0);
+  quad_load<Q, S, ODD>(a, f, x0, y, z, un, ra, rb);
+  bool ok = pair_collide<Q, S>(a, un, ra);
+  ok = pair_collide<Q, S>(a, un + 2u, rb) && ok;
+  if (!ok) atomicOr(a.status, ST_NAN);
+  // opaque copies of the coordinates: the store addresses are recomputed, not held live
+  int x0c, yc, zc;
+  asm volatile("mov.b32 %0, %1;" : "=r"(x0c) : "r"(x0));
+  asm volatile("mov.b32 %0, %1;" : "=r"(yc) : "r"(y));
+  asm volatile("mov.b32 %0, %1;" : "=r"(zc) : "r"(z));
+  const unsigned un2 = unsigned(x0c + yc * a.nx) + unsigned(zc) * unsigned(a.nxy);
+  quad_store<Q, S, ODD>(a, f, x0c, yc, zc, un2, ra, rb);
+}
+
 // Wall-model state of every WALL entry from the previous step's reference velocities (fused mode).
 template <class C>
 __global__ void k_wall_state(const Args a) {

@@ -166,7 +166,8 @@ def test_16bit_matches_oracle_storage_emulation_one_step(model, sigma):
     """One step of FP16 storage equals the oracle's FP16-rounded storage to within a few units in
     the last place of the stored deviation: FP32 (GPU) and FP64 (oracle) arithmetic can round the
     initial state and the stored result to neighbouring FP16 values. BGK and the HRR collision (with
-    and without the finite-difference strain), both through the paired 16-bit kernel."""
+    and without the finite-difference strain). Solids in most rows make the library run the
+    one-cell-per-thread kernel here; the kernels over several cells are checked by the next test."""
     w = I.random_box(12, 8, 6, seed=9, q=19, solid_frac=0.1, tau=0.7, cs=0.1)
     w.model, w.sigma = model, sigma
     g = gpu_from(w, lbm.F16)
@@ -179,6 +180,58 @@ def test_16bit_matches_oracle_storage_emulation_one_step(model, sigma):
     c, wts, *_ = O.lattice(19)
     dev = np.abs(fo[:, fl] - wts[:, None])
     assert (np.abs(fg[:, fl] - fo[:, fl]) <= 4 * np.maximum(dev, 6.1e-5) * 2.0 ** -10 + 1e-12).all()
+
+
+@pytest.mark.parametrize("storage", [lbm.F16, lbm.BF16])
+def test_16bit_multi_cell_kernels_match_oracle_storage_emulation(storage):
+    """The interior kernels that update several cells per thread against the oracle's 16-bit-rounded
+    storage, over even and odd steps, on shapes where the library selects them (no warp mixes cell
+    kinds): four cells per thread on even steps (nx a multiple of 4; a solid-free periodic box and a
+    wall-modelled channel with whole wall rows) and cell pairs (nx = 14, and every odd step).
+    Tolerance: GPU (FP32) and oracle (FP64) arithmetic can round a stored input to neighbouring
+    16-bit values, one unit in the last place of that input. The collision mixes every population of
+    a cell, so an output can differ by a few such units of the cell's largest deviation, not of its
+    own (a small rest-population deviation then differs by many of its own units). The bound is
+    K units of the largest stored deviation max|f - w|: K = 4 after one step, 8 after two and three
+    (differences of a step feed the next). A wrong neighbour or slot gives errors of the size of the
+    deviations themselves, orders of magnitude above it."""
+    mant = 10 if storage == lbm.F16 else 7
+    cases = [(I.random_box(16, 6, 5, seed=21, q=19, solid_frac=0.0, tau=0.7, cs=0.1), 3),
+             (I.channel(nx=16, ny=10, nz=4, seed=550, dtype=np.float64), 3),
+             (I.random_box(14, 6, 5, seed=22, q=19, solid_frac=0.0, tau=0.7, cs=0.1), 1)]
+    c, wts, *_ = O.lattice(19)
+    for w, kernel in cases:
+        g = gpu_from(w, storage)
+        assert g.interior_kernel() == kernel, w.name
+        o = oracle_from(w, storage=int(storage))
+        fl = w.mask != 1
+        for t in (1, 2, 3):
+            g.step(1)
+            o.step(1)
+            fg = g.get_populations()[:, fl]
+            fo = o.populations()[:, fl]
+            hmax = np.abs(fo - wts[:, None]).max()
+            k = 4 if t == 1 else 8
+            err = np.abs(fg - fo).max()
+            assert err <= k * 2.0 ** -mant * hmax, (w.name, t, err, hmax)
+
+
+def test_interior_kernel_selection():
+    """The library's choice of interior kernel: pairs for the FP32 channel, four cells per thread
+    (even steps) for its 16-bit forms, pairs for 16-bit D3Q27 and for the HRR collision, one cell per
+    thread on the urban canopy (most x-groups mix cell kinds)."""
+    ch = I.channel(nx=32, ny=12, nz=4, seed=550, dtype=np.float32)
+    assert gpu_from(ch, lbm.F32).interior_kernel() == 1
+    assert gpu_from(ch, lbm.F16).interior_kernel() == 3
+    assert gpu_from(ch, lbm.BF16).interior_kernel() == 3
+    g = gpu_from(ch, lbm.F16)
+    g.set_collision(lbm.HRR, 1.0)
+    assert g.interior_kernel() == 1
+    ch27 = I.channel(nx=32, ny=12, nz=4, seed=550, q=27, dtype=np.float32)
+    assert gpu_from(ch27, lbm.F16).interior_kernel() == 1
+    cw = I.canopy(nx=64, ny=48, nz=40, n_buildings=8, seed=2506, domain=(256, 48, 60), crop=(64, 0, 0),
+                  dtype=np.float32)
+    assert gpu_from(cw, lbm.F16).interior_kernel() == 0
 
 
 # ---- adjoint -------------------------------------------------------------------------------------------------------------
