@@ -167,14 +167,17 @@ int lbm_set_populations(lbm_ctx* ctx, const void* f, int dtype);
  * lbm_objective_forward runs T steps from the current state, keeping a copy of the state every
  * ckpt steps (ckpt even), and returns J. lbm_objective_backward then recomputes each segment from
  * its checkpoint into a ring of states and sweeps the adjoint kernel backwards, accumulating
- * dJ/dgamma (N values, FP64) and dJ/du_in (3*ny*nz values, FP64); either may be NULL. The wall
- * model is not differentiated (LBM_ESTATE if it is on). After backward the state is the one at the
- * end of the forward run. */
+ * dJ/dgamma and dJ/du_in over all T steps in FP64 device arrays (whatever the storage), and writes
+ * them to dJ_dgamma (N doubles) and dJ_duin (3*ny*nz doubles), host memory or device memory of the
+ * context's device; either may be NULL. The wall model is not differentiated (LBM_ESTATE if it is
+ * on). After backward the state is the one at the end of the forward run. */
 int lbm_objective_forward(lbm_ctx* ctx, int T, int W, int xa, int xb, int ckpt, double* J);
 int lbm_objective_backward(lbm_ctx* ctx, double* dJ_dgamma, double* dJ_duin);
 /* One reverse step at the current state: lam_out = (dS_{t+1}/dS_t)^T lam_in (q*N values each,
- * natural layout, dtype LBM_DTYPE_*), and adds (dS_{t+1}/dgamma)^T lam_in to dgamma (N, FP64) and
- * (dS_{t+1}/du_in)^T lam_in to duin (3*ny*nz, FP64); both nullable. */
+ * natural layout, dtype LBM_DTYPE_*), and writes (dS_{t+1}/dgamma)^T lam_in to dgamma (N, FP64) and
+ * (dS_{t+1}/du_in)^T lam_in to duin (3*ny*nz, FP64); both nullable; host or device memory. This is
+ * the single-step building block (the vector-Jacobian product of one step); the whole-run gradient
+ * with checkpointing is lbm_objective_forward/backward. */
 int lbm_adjoint_step(lbm_ctx* ctx, const void* lam_in, void* lam_out, int dtype, double* dgamma, double* duin);
 /* Device times (CUDA events) of the last differentiation run: ms[0] segment recomputation and
  * ms[1] reverse sweep of lbm_objective_backward, ms[2] the whole lbm_objective_forward. */
@@ -209,6 +212,11 @@ int lbm_info(lbm_ctx* ctx, int64_t out[10]);
  * steps (where 1 would be chosen, for D3Q19 BGK with FP16 or BF16 storage and nx a multiple of 4).
  * Negative on a null context. */
 int lbm_interior_kernel(lbm_ctx* ctx);
+/* Number of kernels the step calls (lbm_step, lbm_step_timed) of this context have launched so far:
+ * per step the wall-model state pass (when the wall model is on and WALL cells are handled inline),
+ * the interior kernel, the boundary-list kernel (when list cells remain for it), and the vortex-inlet
+ * and velocity-field kernels when those forms are on. */
+int lbm_launch_count(lbm_ctx* ctx, int64_t* n);
 /* Integer maps for bit-exact tests: which = 0 type byte per cell (N; bits 0-2 kind, bit 3
  * reference cell, bit 4 a source position is solid or outside, bit 5 boundary list, bit 6 list cell
  * updated by the interior kernel: INFLOW/OUTFLOW cells, and WALL/reference cells in 32-cell
@@ -226,16 +234,20 @@ int lbm_debug_dump(lbm_ctx* ctx, int which, int64_t* out, size_t count);
  * sum_i f_i c_i over the cells of a caller-owned population array, keeping its partial sums in a
  * fixed static device array (4 doubles per 65536 cells, 128 KiB, held by every GPU that loads the
  * library until the process exits) and calling no cudaMalloc, cudaFree or allocating routine.
- *   lattice: 19 or 27 (velocity order as above); f: device pointer to q*n_cells values of dtype
- *   (LBM_DTYPE_F32 or LBM_DTYPE_F64), f[i*n_cells + n] (populations, not deviations);
- *   mask: device pointer to n_cells mask bytes (cells with code LBM_CELL_SOLID are skipped) or NULL;
+ *   lattice: 19 or 27 (velocity order as above); f: q*n_cells values of dtype (LBM_DTYPE_F32 or
+ *   LBM_DTYPE_F64), f[i*n_cells + n] (populations, not deviations), device or managed memory of the
+ *   current device; mask: n_cells mask bytes in device or managed memory of the current device
+ *   (cells with code LBM_CELL_SOLID are skipped) or NULL;
  *   n_cells: 1..LBM_REDUCE_STATIC_MAX_CELLS, larger sizes are rejected with LBM_EINVAL;
- *   out: 4 doubles (mass, momentum x, y, z), device memory (written on the stream) or host memory
- *   (the call then synchronises the stream); stream: cudaStream_t or NULL for the default stream.
+ *   out: 4 doubles (mass, momentum x, y, z), device or managed memory of the current device (written
+ *   on the stream) or host memory (the call then synchronises the stream); stream: cudaStream_t or
+ *   NULL for the default stream. A pointer of the wrong kind or on another device gives LBM_EINVAL
+ *   before any work is queued.
  * The first call made on a device looks up the static array's device address (make that first
- * call before any stream capture). All calls share the array, so calls that overlap on the GPU
- * race; each call overwrites the partial sums it reads. Errors: LBM_EINVAL (arguments), LBM_ECUDA;
- * message in lbm_reduce_static_error(). */
+ * call before any stream capture); the address stays cached for the process, so the call must not
+ * be used on a device after a cudaDeviceReset of it. All calls share the array, so calls that
+ * overlap on the GPU race; each call overwrites the partial sums it reads. Errors: LBM_EINVAL
+ * (arguments), LBM_ECUDA; message in lbm_reduce_static_error(). */
 #define LBM_REDUCE_STATIC_MAX_CELLS 268435456LL
 int lbm_reduce_static(int lattice, const void* f, int dtype, const uint8_t* mask, int64_t n_cells, double* out,
                       void* stream);

@@ -1,9 +1,11 @@
 """PyTorch autograd wrapper of the checkpointed objective (forward = T steps of the lattice with the
 time-averaged pressure-drop objective, backward = the discrete adjoint): porosity gamma and inlet
-velocity u_in are the differentiable inputs. All arithmetic runs in the CUDA library through its C
-ABI (`lbm_objective_forward`, `lbm_objective_backward`); this module only moves arrays.
+velocity u_in are the differentiable inputs. All arithmetic of the method runs in the CUDA library
+through its C ABI (`lbm_set_porosity_ex`, `lbm_set_inflow_ex`, `lbm_objective_forward`,
+`lbm_objective_backward`); tensors are handed over by pointer where they live (CUDA tensors stay on
+the device), and the gradients come back as FP64 tensors on the inputs' device. The only torch
+arithmetic is the chain rule's product with the incoming gradient.
 """
-import numpy as np
 import torch
 
 from . import lbm
@@ -19,10 +21,9 @@ class PressureDropObjective(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, gamma, u_in, lattice, rho0, u0, T, W, xa, xb, ckpt=32):
-        dt = np.float64 if lattice.storage == lbm.F64 else np.float32
-        lattice.set_porosity(gamma.detach().to("cpu", torch.float64).numpy().astype(dt))
-        lattice.set_inflow(u_in.detach().to("cpu", torch.float64).numpy().astype(dt))
-        lattice.init_equilibrium(np.asarray(rho0, dt), np.asarray(u0, dt))
+        lattice.set_porosity(gamma.detach().contiguous())
+        lattice.set_inflow(u_in.detach().reshape(3, -1).contiguous())
+        lattice.init_equilibrium(rho0, u0)
         J = lattice.objective_forward(int(T), int(W), int(xa), int(xb), ckpt=int(ckpt))
         ctx.lattice = lattice
         ctx.like = (gamma, u_in)
@@ -30,11 +31,14 @@ class PressureDropObjective(torch.autograd.Function):
 
     @staticmethod
     def backward(ctx, gJ):
-        g, gu = ctx.lattice.objective_backward()
         gamma, u_in = ctx.like
-        s = gJ.detach().to("cpu", torch.float64).item()
-        dg = torch.from_numpy(g * s).to(gamma.device, gamma.dtype)
-        du = torch.from_numpy(gu * s).to(u_in.device, u_in.dtype).reshape(u_in.shape)
+        lat = ctx.lattice
+        g = torch.empty(lat.N, dtype=torch.float64, device=gamma.device)
+        gu = torch.empty((3, lat.ny * lat.nz), dtype=torch.float64, device=u_in.device)
+        lat.objective_backward(g, gu)
+        s = gJ.detach().to(torch.float64)
+        dg = (g * s.to(g.device)).to(gamma.dtype)
+        du = (gu * s.to(gu.device)).to(u_in.dtype).reshape(u_in.shape)
         return dg, du, None, None, None, None, None, None, None, None
 
 

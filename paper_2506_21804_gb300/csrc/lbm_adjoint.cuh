@@ -18,8 +18,8 @@ struct AdjArgs {
   const void* fst;     // S_t, natural layout, storage type
   const void* lam_in;  // lambda_{t+1}, natural layout, compute type
   void* lam_out;       // lambda_t
-  void* dgam;          // dJ/dgamma accumulator (compute type, N) or null
-  void* duin;          // dJ/du_in accumulator (compute type, 3 ny nz) or null
+  double* dgam;        // dJ/dgamma accumulator (FP64, N) or null
+  double* duin;        // dJ/du_in accumulator (FP64, 3 ny nz) or null
   int add_dj;          // add the objective weights to lambda_t (window step)
   int xa, xb;
   double wa, wb;

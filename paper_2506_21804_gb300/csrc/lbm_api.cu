@@ -93,6 +93,7 @@ struct lbm_ctx {
   cudaStream_t stream = 0;
   const Ops* ops = nullptr;
   long long t = 0;
+  long long launches = 0;  // kernels launched by the step calls (lbm_step, lbm_step_timed)
   unsigned status_seen = 0;
   // device buffers
   DevBuf f, type, mask, wdist, gamma, uin, lcell, nsum, wref, lxyz, lcode, wnrm, wyw, ref0, ref1, status, red, redout, stage;
@@ -445,15 +446,28 @@ void vm_step(lbm_ctx* c) {
 }
 
 void launch_step(lbm_ctx* c, cudaEvent_t before_bulk = nullptr, cudaEvent_t after_bulk = nullptr) {
-  if (c->model == LBM_HRR && c->uvel_stale) fill_uvel(c);
-  if (c->vm_n > 0) vm_step(c);
+  if (c->model == LBM_HRR && c->uvel_stale) {
+    fill_uvel(c);
+    ++c->launches;
+  }
+  if (c->vm_n > 0) {
+    vm_step(c);
+    c->launches += 3;  // vortex generation, partial fields, final field
+  }
   const Args a = make_args(c);
   const int odd = int(c->t & 1);
-  if (a.fuse && a.wm) c->ops->wall_pass(a, c->stream);
+  if (a.fuse && a.wm && a.n_wall > 0) {
+    c->ops->wall_pass(a, c->stream);
+    ++c->launches;
+  }
   if (before_bulk) cudaEventRecord(before_bulk, c->stream);
   c->ops->step_bulk(a, odd, c->stream);
+  ++c->launches;
   if (after_bulk) cudaEventRecord(after_bulk, c->stream);
-  c->ops->step_list(a, odd, c->stream);
+  if ((a.lsub ? a.n_sub : a.n_list) > 0) {
+    c->ops->step_list(a, odd, c->stream);
+    ++c->launches;
+  }
   ++c->t;
 }
 
@@ -899,6 +913,12 @@ int lbm_interior_kernel(lbm_ctx* c) {
   return quads ? 3 : 1;
 }
 
+int lbm_launch_count(lbm_ctx* c, int64_t* n) {
+  if (!c || !n) return fail(LBM_EINVAL, "null argument");
+  *n = c->launches;
+  return LBM_OK;
+}
+
 int lbm_info(lbm_ctx* c, int64_t out[10]) {
   if (!c || !out) return fail(LBM_EINVAL, "null argument");
   out[0] = c->N; out[1] = c->n_list; out[2] = c->counts[0]; out[3] = c->counts[1]; out[4] = c->counts[2];
@@ -1129,6 +1149,9 @@ int lbm_objective_backward(lbm_ctx* c, double* dJ_dgamma, double* dJ_duin) {
   if (c->model != LBM_BGK) return fail(LBM_ESTATE, "the adjoint is defined for the BGK collision only");
   if (c->vm_n > 0) return fail(LBM_ESTATE, "the adjoint is defined for a steady inlet only");
   if (c->wm) return fail(LBM_ESTATE, "the wall model is not differentiated");
+  int rc0;
+  if (dJ_dgamma && (rc0 = check_ptr(c, dJ_dgamma, "dJ_dgamma")) != LBM_OK) return rc0;
+  if (dJ_duin && (rc0 = check_ptr(c, dJ_duin, "dJ_duin")) != LBM_OK) return rc0;
   const int T = c->adj_T, W = c->adj_W, ck = c->adj_ck;
   const int nck = (T + ck - 1) / ck;
   const size_t sb = (size_t)c->q * c->stride * c->ops->elem;
@@ -1141,11 +1164,11 @@ int lbm_objective_backward(lbm_ctx* c, double* dJ_dgamma, double* dJ_duin) {
   }
   CK(c->lamA.ensure(lb));
   CK(c->lamB.ensure(lb));
-  CK(c->dgam.ensure((size_t)c->N * c->ops->celem));
-  CK(c->duin.ensure(pl * c->ops->celem));
+  CK(c->dgam.ensure((size_t)c->N * sizeof(double)));
+  CK(c->duin.ensure(pl * sizeof(double)));
   cudaStream_t s = c->stream;
-  CK(cudaMemsetAsync(c->dgam.p, 0, (size_t)c->N * c->ops->celem, s));
-  CK(cudaMemsetAsync(c->duin.p, 0, pl * c->ops->celem, s));
+  CK(cudaMemsetAsync(c->dgam.p, 0, (size_t)c->N * sizeof(double), s));
+  CK(cudaMemsetAsync(c->duin.p, 0, pl * sizeof(double), s));
   Args a = make_args(c);
   c->ops->seed(a, c->lamA.p, c->adj_xa, c->adj_xb, c->adj_wa, c->adj_wb, s);
   void* lin = c->lamA.p;
@@ -1172,8 +1195,8 @@ int lbm_objective_backward(lbm_ctx* c, double* dJ_dgamma, double* dJ_duin) {
       d.fst = st[j];
       d.lam_in = lin;
       d.lam_out = lout;
-      d.dgam = c->dgam.p;
-      d.duin = c->duin.p;
+      d.dgam = static_cast<double*>(c->dgam.p);
+      d.duin = static_cast<double*>(c->duin.p);
       d.add_dj = (t > T - W) ? 1 : 0;
       d.xa = c->adj_xa; d.xb = c->adj_xb; d.wa = c->adj_wa; d.wb = c->adj_wb;
       c->ops->reverse(a, d, s);
@@ -1193,19 +1216,10 @@ int lbm_objective_backward(lbm_ctx* c, double* dJ_dgamma, double* dJ_duin) {
   CK(cudaGetLastError());
   c->adj_ms[0] = rec_ms;
   c->adj_ms[1] = rev_ms;
-  const int cd = c->ops->celem == 8 ? LBM_DTYPE_F64 : LBM_DTYPE_F32;
-  if (dJ_dgamma) {
-    CK(c->stage.ensure((size_t)c->N * 8));
-    c->ops->convert(c->dgam.p, cd, c->stage.p, LBM_DTYPE_F64, c->N, s);
-    CK(cudaMemcpyAsync(dJ_dgamma, c->stage.p, (size_t)c->N * 8, cudaMemcpyDefault, s));
-    CK(cudaStreamSynchronize(s));
-  }
-  if (dJ_duin) {
-    CK(c->stage.ensure(pl * 8));
-    c->ops->convert(c->duin.p, cd, c->stage.p, LBM_DTYPE_F64, (long long)pl, s);
-    CK(cudaMemcpyAsync(dJ_duin, c->stage.p, pl * 8, cudaMemcpyDefault, s));
-    CK(cudaStreamSynchronize(s));
-  }
+  // the FP64 accumulators go to the caller's arrays as they are (host or device memory)
+  if (dJ_dgamma) CK(cudaMemcpyAsync(dJ_dgamma, c->dgam.p, (size_t)c->N * sizeof(double), cudaMemcpyDefault, s));
+  if (dJ_duin) CK(cudaMemcpyAsync(dJ_duin, c->duin.p, pl * sizeof(double), cudaMemcpyDefault, s));
+  CK(cudaStreamSynchronize(s));
   int rc = read_status(c);
   if (rc != LBM_OK) return rc;
   return status_code(c);
@@ -1221,6 +1235,8 @@ int lbm_adjoint_step(lbm_ctx* c, const void* lam_in, void* lam_out, int dtype, d
   int rc;
   if ((rc = check_ptr(c, lam_in, "lam_in")) != LBM_OK) return rc;
   if ((rc = check_ptr(c, lam_out, "lam_out")) != LBM_OK) return rc;
+  if (dgamma && (rc = check_ptr(c, dgamma, "dgamma")) != LBM_OK) return rc;
+  if (duin && (rc = check_ptr(c, duin, "duin")) != LBM_OK) return rc;
   const size_t cnt = (size_t)c->q * c->N;
   const size_t lb = (size_t)c->q * c->stride * c->ops->celem;
   const size_t pl = 3 * (size_t)c->ny * c->nz;
@@ -1228,10 +1244,10 @@ int lbm_adjoint_step(lbm_ctx* c, const void* lam_in, void* lam_out, int dtype, d
   cudaStream_t s = c->stream;
   CK(c->lamA.ensure(lb));
   CK(c->lamB.ensure(lb));
-  CK(c->dgam.ensure((size_t)c->N * c->ops->celem));
-  CK(c->duin.ensure(pl * c->ops->celem));
-  CK(cudaMemsetAsync(c->dgam.p, 0, (size_t)c->N * c->ops->celem, s));
-  CK(cudaMemsetAsync(c->duin.p, 0, pl * c->ops->celem, s));
+  CK(c->dgam.ensure((size_t)c->N * sizeof(double)));
+  CK(c->duin.ensure(pl * sizeof(double)));
+  CK(cudaMemsetAsync(c->dgam.p, 0, (size_t)c->N * sizeof(double), s));
+  CK(cudaMemsetAsync(c->duin.p, 0, pl * sizeof(double), s));
   // caller layout q*N -> padded q*stride
   CK(c->stage.ensure(cnt * 8));
   CK(cudaMemcpyAsync(c->stage.p, lam_in, cnt * dsize(dtype), cudaMemcpyDefault, s));
@@ -1243,8 +1259,8 @@ int lbm_adjoint_step(lbm_ctx* c, const void* lam_in, void* lam_out, int dtype, d
   d.fst = c->f.p;
   d.lam_in = c->lamA.p;
   d.lam_out = c->lamB.p;
-  d.dgam = c->dgam.p;
-  d.duin = c->duin.p;
+  d.dgam = static_cast<double*>(c->dgam.p);
+  d.duin = static_cast<double*>(c->duin.p);
   c->ops->reverse(a, d, s);
   for (int i = 0; i < c->q; ++i)
     c->ops->convert(static_cast<const char*>(c->lamB.p) + (size_t)i * c->stride * c->ops->celem, cd,
@@ -1252,16 +1268,9 @@ int lbm_adjoint_step(lbm_ctx* c, const void* lam_in, void* lam_out, int dtype, d
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(lam_out, c->stage.p, cnt * dsize(dtype), cudaMemcpyDefault, s));
   CK(cudaStreamSynchronize(s));
-  if (dgamma) {
-    c->ops->convert(c->dgam.p, cd, c->stage.p, LBM_DTYPE_F64, c->N, s);
-    CK(cudaMemcpyAsync(dgamma, c->stage.p, (size_t)c->N * 8, cudaMemcpyDefault, s));
-    CK(cudaStreamSynchronize(s));
-  }
-  if (duin) {
-    c->ops->convert(c->duin.p, cd, c->stage.p, LBM_DTYPE_F64, (long long)pl, s);
-    CK(cudaMemcpyAsync(duin, c->stage.p, pl * 8, cudaMemcpyDefault, s));
-    CK(cudaStreamSynchronize(s));
-  }
+  if (dgamma) CK(cudaMemcpyAsync(dgamma, c->dgam.p, (size_t)c->N * sizeof(double), cudaMemcpyDefault, s));
+  if (duin) CK(cudaMemcpyAsync(duin, c->duin.p, pl * sizeof(double), cudaMemcpyDefault, s));
+  CK(cudaStreamSynchronize(s));
   return LBM_OK;
 }
 

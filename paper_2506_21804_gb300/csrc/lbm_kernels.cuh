@@ -1008,7 +1008,7 @@ static __global__ void k_plane_final(const double* partial, int nblk, double* ac
 
 // ---- adjoint reverse step ---------------------------------------------------------------------------------
 // lam_out(n) = (d f*(n) / d f(n))^T mu(n) (+ objective weights), mu_k(n) = lam_in at the slot that
-// f*_k(n) streams into; gamma and inlet-velocity sensitivities accumulate in C precision.
+// f*_k(n) streams into; gamma and inlet-velocity sensitivities accumulate in FP64 over all steps.
 template <int Q, class S>
 __device__ __forceinline__ void reverse_cell(const Args& a, const AdjArgs& d, int x, int y, int z, long long n, uint8_t t) {
   using C = typename Codec<S>::C;
@@ -1054,13 +1054,12 @@ __device__ __forceinline__ void reverse_cell(const Args& a, const AdjArgs& d, in
   }
   C* lo = cptr<C>(d.lam_out);
   sfor<0, Q>([&](auto I) { lo[(long long)I * a.stride + n] = lam[I]; });
-  if (d.dgam) cptr<C>(d.dgam)[n] += ggam;
+  if (d.dgam) d.dgam[n] += double(ggam);
   if (kind == K_INFLOW && d.duin) {
     const long long pl = (long long)a.ny * a.nz, p = y + (long long)a.ny * z;
-    C* du = cptr<C>(d.duin);
-    atomicAdd(du + p, gub[0]);
-    atomicAdd(du + pl + p, gub[1]);
-    atomicAdd(du + 2 * pl + p, gub[2]);
+    atomicAdd(d.duin + p, double(gub[0]));
+    atomicAdd(d.duin + pl + p, double(gub[1]));
+    atomicAdd(d.duin + 2 * pl + p, double(gub[2]));
   }
 }
 

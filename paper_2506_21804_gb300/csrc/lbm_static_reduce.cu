@@ -10,7 +10,9 @@
 // The static array is created when the library is loaded and every GPU that loads the library keeps
 // it until the process exits. Its device address is looked up once per device (first call made on
 // that device, with the device current) through cudaGetSymbolAddress; host code never passes the
-// array's own name to a kernel, since in host code that name denotes a host-side stand-in.
+// array's own name to a kernel, since in host code that name denotes a host-side stand-in. A
+// cudaDeviceReset unloads the module and invalidates the cached address, so this entry point must
+// not be used on a device after it has been reset.
 // Every call shares the array: calls whose work overlaps on the GPU (other streams, other host
 // threads) race on it. Each call overwrites every partial it later reads, so nothing has to be
 // cleared between calls.
@@ -77,6 +79,18 @@ __global__ void k_static_final(const double* part, int nchunks, double* out) {
   for (int c = 0; c < 4; ++c) out[c] = s[c];
 }
 
+// 1: device or managed memory of device `dev`; 2: device or managed memory of another device;
+// 0: anything else (host memory, registered or not).
+int pointer_kind(const void* p, int dev) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) return 0;
+  return at.device == dev ? 1 : 2;
+}
+
 int fail_static(int code, const std::string& msg) {
   g_err_static = msg;
   return code;
@@ -111,14 +125,18 @@ extern "C" int lbm_reduce_static(int lattice, const void* f, int dtype, const ui
     }
     scratch = g_addr[dev];
   }
-  cudaPointerAttributes at;
-  if (cudaPointerGetAttributes(&at, f) != cudaSuccess || at.type != cudaMemoryTypeDevice) {
-    cudaGetLastError();
-    return fail_static(LBM_EINVAL, "f must be device memory of the current device");
+  // f and mask are read by the kernel, so they must be device-accessible memory of this device
+  // (device or managed); out is written by the kernel when it is such memory, else it is host memory
+  // and receives the result by a copy.
+  const int kf = pointer_kind(f, dev);
+  if (kf != 1) return fail_static(LBM_EINVAL, kf == 2 ? "f is device memory of another device" : "f must be device memory of the current device");
+  if (mask) {
+    const int km = pointer_kind(mask, dev);
+    if (km != 1) return fail_static(LBM_EINVAL, km == 2 ? "mask is device memory of another device" : "mask must be device memory of the current device (or NULL)");
   }
-  bool out_dev = false;
-  if (cudaPointerGetAttributes(&at, out) == cudaSuccess) out_dev = at.type == cudaMemoryTypeDevice;
-  else cudaGetLastError();
+  const int ko = pointer_kind(out, dev);
+  if (ko == 2) return fail_static(LBM_EINVAL, "out is device memory of another device");
+  const bool out_dev = ko == 1;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   double* part = static_cast<double*>(scratch);
   double* result = part + 4 * kMaxChunks;

@@ -81,6 +81,7 @@ SIGNATURES = {
     "lbm_info": (_i, [_p, _p]),
     "lbm_set_option": (_i, [_p, _i, _i]),
     "lbm_reduce_static": (_i, [_i, _p, _i, _p, ctypes.c_int64, _p, _p]),
+    "lbm_launch_count": (_i, [_p, _p]),
     "lbm_reduce_static_error": (ctypes.c_char_p, []),
     "lbm_debug_dump": (_i, [_p, _i, _p, ctypes.c_size_t]),
 }
@@ -283,6 +284,12 @@ class Lattice:
         keys = ["N", "n_list", "n_wall", "n_ref", "n_inflow", "n_outflow", "n_solid", "t", "storage", "q"]
         return dict(zip(keys, (int(v) for v in out)))
 
+    def launch_count(self):
+        """Kernels launched by the step calls of this lattice so far."""
+        n = np.zeros(1, np.int64)
+        _check(lib().lbm_launch_count(self.h, n.ctypes.data_as(_p)))
+        return int(n[0])
+
     def debug_dump(self, which):
         info = self.info()
         count = {0: self.N, 1: info["n_list"], 2: info["n_list"], 3: 3 * info["n_list"],
@@ -308,11 +315,21 @@ class Lattice:
         _check(lib().lbm_objective_forward(self.h, int(T), int(W), int(xa), int(xb), int(ckpt), J.ctypes.data_as(_p)))
         return J[0]
 
-    def objective_backward(self):
-        g = np.zeros(self.N)
-        u = np.zeros(3 * self.ny * self.nz)
-        _check(lib().lbm_objective_backward(self.h, g.ctypes.data_as(_p), u.ctypes.data_as(_p)))
-        return g, u.reshape(3, self.ny * self.nz)
+    def objective_backward(self, dgamma=None, duin=None):
+        """dJ/dgamma (N) and dJ/du_in (3, ny*nz) in FP64. Without arguments they come back as host
+        arrays; given FP64 torch tensors (device or host) of those sizes, the library writes them."""
+        if dgamma is None and duin is None:
+            g = np.zeros(self.N)
+            u = np.zeros(3 * self.ny * self.nz)
+            _check(lib().lbm_objective_backward(self.h, g.ctypes.data_as(_p), u.ctypes.data_as(_p)))
+            return g, u.reshape(3, self.ny * self.nz)
+        for t, n in ((dgamma, self.N), (duin, 3 * self.ny * self.nz)):
+            if t is not None and (str(t.dtype) != "torch.float64" or t.numel() != n or not t.is_contiguous()):
+                raise ValueError("gradient outputs must be contiguous float64 tensors of N and 3*ny*nz values")
+        gp = None if dgamma is None else ctypes.c_void_p(dgamma.data_ptr())
+        up = None if duin is None else ctypes.c_void_p(duin.data_ptr())
+        _check(lib().lbm_objective_backward(self.h, gp, up))
+        return dgamma, duin
 
     def adjoint_step(self, lam_in):
         a = _Arr(lam_in, dtype=np.float64)

@@ -64,3 +64,48 @@ def test_static_reduce_rejects_sizes_beyond_the_scratch(torch):
     rc = lbm.lib().lbm_reduce_static(19, _ptr(f), lbm.DTYPE_F32, None, (1 << 28) + 1, _ptr(out), None)
     assert rc == lbm.EINVAL
     assert b"outside" in lbm.lib().lbm_reduce_static_error()
+
+
+@pytest.mark.parametrize("q,dt", [(19, "float64"), (27, "float32")])
+def test_static_reduce_many_chunks_null_mask_side_stream(torch, q, dt):
+    # 3 * 65536 + 123 cells: four partial sums, the last one over a ragged chunk, summed in a fixed
+    # order; no mask; a device out and then a host out, both ordered on a side stream
+    n = 3 * 65536 + 123
+    rng = np.random.default_rng(123 + q)
+    host = (1.0 / q + 0.01 * rng.standard_normal((q, n))).astype(dt)
+    import oracle.oracle as O  # lattice vectors for the reference sums
+    c = O.lattice(q)[0].astype(np.float64)
+    h64 = host.astype(np.float64)
+    ref = np.concatenate([[h64.sum()], c.T @ h64.sum(axis=1)])
+    code = lbm.DTYPE_F64 if dt == "float64" else lbm.DTYPE_F32
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        f = torch.from_numpy(host).to("cuda", non_blocking=False)
+        for call in range(2):
+            out = torch.full((4,), float("nan"), dtype=torch.float64, device="cuda")
+            rc = lbm.lib().lbm_reduce_static(q, _ptr(f), code, None, n, _ptr(out), ctypes.c_void_p(side.cuda_stream))
+            assert rc == 0, lbm.lib().lbm_reduce_static_error()
+            side.synchronize()
+            got = out.cpu().numpy()
+            tol = 1e-12 * np.abs(h64).sum()
+            assert np.abs(got - ref).max() <= tol, (call, got, ref)
+            hout = np.full(4, np.nan)
+            rc = lbm.lib().lbm_reduce_static(q, _ptr(f), code, None, n, hout.ctypes.data_as(ctypes.c_void_p),
+                                             ctypes.c_void_p(side.cuda_stream))
+            assert rc == 0, lbm.lib().lbm_reduce_static_error()
+            assert np.array_equal(hout, got)
+
+
+def test_static_reduce_rejects_host_inputs(torch):
+    f = torch.zeros(19 * 64, dtype=torch.float32, device="cuda")
+    out = torch.zeros(4, dtype=torch.float64, device="cuda")
+    host_mask = np.zeros(64, np.uint8)
+    rc = lbm.lib().lbm_reduce_static(19, _ptr(f), lbm.DTYPE_F32, host_mask.ctypes.data_as(ctypes.c_void_p), 64,
+                                     _ptr(out), None)
+    assert rc == lbm.EINVAL
+    assert b"mask" in lbm.lib().lbm_reduce_static_error()
+    host_f = np.zeros(19 * 64, np.float32)
+    rc = lbm.lib().lbm_reduce_static(19, host_f.ctypes.data_as(ctypes.c_void_p), lbm.DTYPE_F32, None, 64,
+                                     _ptr(out), None)
+    assert rc == lbm.EINVAL
+    assert b"f must be device memory" in lbm.lib().lbm_reduce_static_error()
