@@ -165,6 +165,9 @@ struct Oracle {
   double vm_sigma = 4.0, vm_I = 0.1;
   uint64_t vm_seed = 0;
   std::vector<double> uin_cur;  // inlet velocity of the current (last) step, 3 * ny * nz
+  // outlet fringe zone (Sec. 3.2); off when fr_L == 0
+  int fr_L = 0;
+  double fr_smax = 0.0, fr_p = 2.0;
   long t = 0;
   // adjoint bookkeeping
   std::vector<std::vector<double>> hist;  // stored pre-collision states S_0..S_{T-1}
@@ -617,8 +620,8 @@ void strain_fd(const Oracle& o, long n, double S[3][3]) {
 // on return fs holds the post-collision populations, urep the reported velocity
 // u = j/rho + F/(2 rho) and rho_out the density.
 template <class T>
-void collide_cell(const Oracle& o, long n, T f[27], T gamma, const T ub[3], const double* uref, T fs[27],
-                  T urep[3], T* rho_out) {
+void collide_cell_core(const Oracle& o, long n, T f[27], T gamma, const T ub[3], const double* uref, T fs[27],
+                       T urep[3], T* rho_out) {
   const Lat& L = o.L;
   int k = o.kind[n];
   if (k == K_INFLOW) bc_velocity(L, f, ub);
@@ -693,6 +696,32 @@ void collide_cell(const Oracle& o, long n, T f[27], T gamma, const T ub[3], cons
     return;
   }
   for (int i = 0; i < L.Q; ++i) fs[i] = feq(L, i, rho, uh) + (1.0 - 1.0 / tau) * (f[i] - fe[i]);
+}
+
+// Outlet fringe zone (Sec. 3.2: the outlet is a fixed local pressure with a fringe zone in front
+// of it; the paper gives no parameters, so the layer is a reading). The last L planes x >= nx - L
+// form the layer; in it every cell that is neither INFLOW nor OUTFLOW relaxes its post-collision
+// populations towards the equilibrium at the outlet density and its own reported velocity:
+//   f*_i <- f*_i - s(x) (f*_i - f^eq_i(rho_out, u)),   s(x) = s_max xi^p,  xi = (x - (nx - L) + 1)/L,
+// so the strength rises from s_max L^-p at the first plane to s_max at the last (p = 0: constant).
+double fringe_strength(const Oracle& o, int x) {
+  if (o.fr_L <= 0 || x < o.nx - o.fr_L) return 0.0;
+  const double xi = double(x - (o.nx - o.fr_L) + 1) / double(o.fr_L);
+  return o.fr_smax * std::pow(xi, o.fr_p);
+}
+
+// One cell's update: the collision of collide_cell_core, then the fringe-zone relaxation.
+template <class T>
+void collide_cell(const Oracle& o, long n, T f[27], T gamma, const T ub[3], const double* uref, T fs[27],
+                  T urep[3], T* rho_out) {
+  collide_cell_core<T>(o, n, f, gamma, ub, uref, fs, urep, rho_out);
+  const int k = o.kind[n];
+  if (o.fr_L <= 0 || k == K_INFLOW || k == K_OUTFLOW) return;
+  int x, y, z;
+  coords(o, n, x, y, z);
+  const double sx = fringe_strength(o, x);
+  if (sx == 0.0) return;
+  for (int i = 0; i < o.L.Q; ++i) fs[i] = fs[i] - sx * (fs[i] - feq(o.L, i, T(o.rho_out), urep));
 }
 
 double round_storage(int mode, double x);
@@ -1095,6 +1124,18 @@ void orc_inflow_field(void* h, double* out) {
 unsigned long long orc_splitmix64(unsigned long long z) { return splitmix64_out(z); }
 double orc_vm_uniform(unsigned long long seed, unsigned long long counter) { return vm_uniform(seed, counter); }
 void orc_set_outflow(void* h, double rho) { static_cast<Oracle*>(h)->rho_out = rho; }
+int orc_set_fringe(void* h, int L, double smax, double p) {
+  Oracle* o = static_cast<Oracle*>(h);
+  if (L < 0 || L > o->nx || !(smax >= 0.0 && smax <= 1.0) || !(p >= 0.0)) {
+    g_err = "fringe: need 0 <= L <= nx, 0 <= s_max <= 1, p >= 0";
+    return 1;
+  }
+  o->fr_L = L;
+  o->fr_smax = smax;
+  o->fr_p = p;
+  return 0;
+}
+double orc_fringe_strength(void* h, int x) { return fringe_strength(*static_cast<Oracle*>(h), x); }
 void orc_set_porosity(void* h, const double* g) {
   Oracle& o = *static_cast<Oracle*>(h);
   if (g) o.gamma.assign(g, g + o.N); else o.gamma.clear();

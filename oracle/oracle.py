@@ -40,6 +40,8 @@ def lib():
             "orc_set_force": (None, [_p, _d, _d, _d]),
             "orc_set_inflow": (None, [_p, _p]),
             "orc_set_outflow": (None, [_p, _d]),
+            "orc_set_fringe": (_i, [_p, _i, _d, _d]),
+            "orc_fringe_strength": (_d, [_p, _i]),
             "orc_set_porosity": (None, [_p, _p]),
             "orc_set_wall_model": (None, [_p, _i, _d, _d]),
             "orc_set_storage": (None, [_p, _i]),
@@ -268,6 +270,13 @@ class Oracle:
 
     def set_outflow(self, rho):
         lib().orc_set_outflow(self.h, rho)
+
+    def set_fringe(self, L, s_max, p=2.0):
+        """Outlet fringe zone over the last L planes (L = 0: off), strength s_max xi^p."""
+        self._chk(lib().orc_set_fringe(self.h, int(L), float(s_max), float(p)))
+
+    def fringe_strength(self, x):
+        return lib().orc_fringe_strength(self.h, int(x))
 
     def set_porosity(self, gamma):
         g = _f64(None if gamma is None else np.asarray(gamma).reshape(-1))

@@ -75,6 +75,7 @@ class Workload:
     model: int = 0                         # collision: 0 BGK, 1 hybrid recursive regularised
     sigma: float = 1.0                     # hybridisation factor of the HRR collision
     vortex: Optional[tuple] = None         # vortex-method inlet (n, sigma, intensity, seed) or None
+    fringe: Optional[tuple] = None         # outlet fringe zone (L, s_max, p) or None
     meta: dict = field(default_factory=dict)
 
     @property

@@ -30,6 +30,8 @@ def oracle_from(w, storage=0, cast32=False):
         o.set_collision(w.model, w.sigma)
     if getattr(w, "vortex", None):
         o.set_vortex_inlet(*w.vortex)
+    if getattr(w, "fringe", None):
+        o.set_fringe(*w.fringe)
     o.init_equilibrium(_arr(w.rho0, cast32), _arr(w.u0, cast32))
     return o
 
