@@ -107,6 +107,15 @@ int lbm_set_inflow_ex(lbm_ctx* ctx, const void* u_in, int dtype);
 int lbm_set_vortex_inlet(lbm_ctx* ctx, int n, double sigma, double intensity, unsigned long long seed);
 /* Outlet density of OUTFLOW cells (inward normal -x). */
 int lbm_set_outflow(lbm_ctx* ctx, double rho_out);
+/* Outlet fringe zone (Sec. 3.2: the fixed-pressure outlet has a fringe zone in front of it; the
+ * paper gives no parameters, so this layer is a reading). In the last L planes x >= nx - L, every
+ * cell that is neither INFLOW nor OUTFLOW relaxes its post-collision populations towards the
+ * equilibrium at the outlet density (lbm_set_outflow) and its own reported velocity u:
+ *   f*_i <- f*_i - s(x) (f*_i - f^eq_i(rho_out, u)),  s(x) = s_max xi^p,  xi = (x - (nx - L) + 1) / L,
+ * so s rises from s_max L^-p at the first plane of the layer to s_max at x = nx - 1 (p = 0: constant).
+ * L = 0 switches it off. The adjoint calls return LBM_ESTATE while it is on. Errors: LBM_EINVAL for L
+ * outside [0, nx], s_max outside [0, 1] or p < 0. Device memory: nx compute-type values. */
+int lbm_set_fringe(lbm_ctx* ctx, int L, double s_max, double p);
 /* Per-cell porosity gamma (N values in [0,1], 1 = fluid); NULL removes it. */
 int lbm_set_porosity(lbm_ctx* ctx, const float* gamma);
 int lbm_set_porosity_ex(lbm_ctx* ctx, const void* gamma, int dtype);

@@ -100,6 +100,9 @@ struct lbm_ctx {
   DevBuf lidx, lsub, lwall, lbc, wst;
   DevBuf uvel0, uvel1;  // HRR velocity fields (step t reads uvel[t & 1], writes the other)
   DevBuf uin_a, uin_b, vort, vpart;  // vortex inlet: current/previous inlet fields, vortex list, partial fields
+  DevBuf fringe;  // outlet fringe zone: strength per x-plane (compute type)
+  int fr_L = 0;
+  double fr_smax = 0.0, fr_p = 2.0;
   DevBuf geo_counts, geo_sub, geo_kinds;  // geometry set-up scratch (per-block counts, kind counters)
   double pair_mixed = 1.0;  // fraction of 64-cell x-groups mixing plain and per-cell pairs
   int n_sub = 0, n_wall = 0, n_bc = 0;
@@ -120,7 +123,7 @@ struct lbm_ctx {
   double adj_ms[3] = {0, 0, 0};
 
   ~lbm_ctx() {
-    DevBuf* all[] = {&geo_counts, &geo_sub, &geo_kinds, &uin_a, &uin_b, &vort, &vpart, &uvel0, &uvel1, &lidx, &lsub, &lwall, &lbc, &wst, &f, &type, &mask, &wdist, &gamma, &uin, &lcell, &nsum, &wref, &lxyz, &lcode, &wnrm, &wyw, &ref0, &ref1, &status, &red,
+    DevBuf* all[] = {&fringe, &geo_counts, &geo_sub, &geo_kinds, &uin_a, &uin_b, &vort, &vpart, &uvel0, &uvel1, &lidx, &lsub, &lwall, &lbc, &wst, &f, &type, &mask, &wdist, &gamma, &uin, &lcell, &nsum, &wref, &lxyz, &lcode, &wnrm, &wyw, &ref0, &ref1, &status, &red,
                      &redout, &stage, &lamA, &lamB, &dgam, &duin, &plane};
     for (DevBuf* b : all) b->release();
     for (auto& b : ckpts) b.release();
@@ -161,7 +164,7 @@ GeoArgs geo_args(const lbm_ctx* c) {
 #endif
 bool pairs_selected(const lbm_ctx* c) {
   const bool idx32 = (unsigned long long)c->q * (unsigned long long)c->stride < (1ull << 32) && c->N < (1ll << 31);
-  if (c->storage == LBM_F64 || c->nx % 2 != 0 || !idx32 || c->kernel != 0) return false;
+  if (c->storage == LBM_F64 || c->nx % 2 != 0 || !idx32 || c->kernel != 0 || c->fr_L > 0) return false;
   return c->pair_mixed <= LBM_PAIR_MIX_MAX;
 }
 
@@ -200,6 +203,7 @@ Args make_args(const lbm_ctx* c) {
   a.E = c->E;
   a.kernel = c->kernel;
   a.fuse = c->kernel == 0 ? 1 : 0;
+  a.inline_all = (a.fuse && c->model == LBM_BGK) ? 1 : 0;
   a.lidx = static_cast<const int*>(c->lidx.p);
   a.lsub = a.fuse ? static_cast<const int*>(c->lsub.p) : nullptr;
   a.n_sub = c->n_sub;
@@ -216,6 +220,8 @@ Args make_args(const lbm_ctx* c) {
   a.uvel_rd = (c->t & 1) ? c->uvel1.p : c->uvel0.p;
   a.uvel_wr = (c->t & 1) ? c->uvel0.p : c->uvel1.p;
   a.pairs = pairs_selected(c) ? 1 : 0;
+  a.fringe = c->fr_L > 0 ? c->fringe.p : nullptr;
+  a.fr_x0 = c->nx - c->fr_L;
   return a;
 }
 
@@ -464,7 +470,7 @@ void launch_step(lbm_ctx* c, cudaEvent_t before_bulk = nullptr, cudaEvent_t afte
   c->ops->step_bulk(a, odd, c->stream);
   ++c->launches;
   if (after_bulk) cudaEventRecord(after_bulk, c->stream);
-  if ((a.lsub ? a.n_sub : a.n_list) > 0) {
+  if (!a.inline_all && (a.lsub ? a.n_sub : a.n_list) > 0) {
     c->ops->step_list(a, odd, c->stream);
     ++c->launches;
   }
@@ -605,6 +611,10 @@ int lbm_set_precision(lbm_ctx* c, int storage) {
   c->wnrm.release(); c->wyw.release(); c->ref0.release(); c->ref1.release();
   c->uvel0.release(); c->uvel1.release();
   c->uin_a.release(); c->uin_b.release(); c->vort.release(); c->vpart.release();
+  if (c->fr_L > 0) {
+    c->fringe.release();
+    if ((rc = lbm_set_fringe(c, c->fr_L, c->fr_smax, c->fr_p)) != LBM_OK) return rc;
+  }
   if ((rc = build_geometry(c)) != LBM_OK) return rc;
   return reset_state(c);
 }
@@ -634,15 +644,26 @@ int lbm_set_geometry(lbm_ctx* c, const uint8_t* mask, const float* wall_dist) {
   int rc;
   if ((rc = check_ptr(c, mask, "mask")) != LBM_OK) return rc;
   if (wall_dist && (rc = check_ptr(c, wall_dist, "wall_dist")) != LBM_OK) return rc;
-  if (!is_device_ptr(mask, c->device)) {
-    for (long long n = 0; n < c->N; ++n) {
-      const uint8_t m = mask[n];
-      if (!(m == 0 || m == 1 || m == 3 || m == 4))
-        return fail(LBM_EINVAL, "mask[%lld] = %d: codes are 0 fluid, 1 solid, 3 inflow, 4 outflow", n, int(m));
-    }
-  }
   CK(cudaStreamSynchronize(c->stream));
-  if ((rc = upload(c, c->mask.p, mask, (size_t)c->N)) != LBM_OK) return rc;
+  // The mask goes to a staging buffer and its codes are checked there, on the device; only a valid
+  // mask replaces the current one, so a rejected call changes nothing.
+  {
+    cudaStream_t s = c->stream;
+    CK(c->stage.ensure((size_t)c->N));
+    CK(c->geo_kinds.ensure(5 * sizeof(unsigned long long)));
+    CK(cudaMemcpyAsync(c->stage.p, mask, (size_t)c->N, cudaMemcpyDefault, s));
+    unsigned long long* first_bad = static_cast<unsigned long long*>(c->geo_kinds.p);
+    geo_check_mask(static_cast<const uint8_t*>(c->stage.p), c->N, first_bad, s);
+    unsigned long long bad = 0;
+    CK(cudaMemcpyAsync(&bad, first_bad, sizeof(bad), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (bad != ~0ull) {
+      uint8_t v = 0;
+      CK(cudaMemcpy(&v, static_cast<const uint8_t*>(c->stage.p) + bad, 1, cudaMemcpyDeviceToHost));
+      return fail(LBM_EINVAL, "mask[%lld] = %d: codes are 0 fluid, 1 solid, 3 inflow, 4 outflow", (long long)bad, int(v));
+    }
+    CK(cudaMemcpyAsync(c->mask.p, c->stage.p, (size_t)c->N, cudaMemcpyDeviceToDevice, s));
+  }
   if (wall_dist) {
     CK(c->wdist.ensure((size_t)c->N * sizeof(float)));
     if ((rc = upload(c, c->wdist.p, wall_dist, (size_t)c->N * sizeof(float))) != LBM_OK) return rc;
@@ -690,6 +711,33 @@ int lbm_set_outflow(lbm_ctx* c, double rho_out) {
   if (!c) return fail(LBM_EINVAL, "null context");
   if (!(rho_out > 0.0) || !std::isfinite(rho_out)) return fail(LBM_EINVAL, "rho_out must be > 0");
   c->rho_out = rho_out;
+  return LBM_OK;
+}
+
+int lbm_set_fringe(lbm_ctx* c, int L, double s_max, double p) {
+  if (!c) return fail(LBM_EINVAL, "null context");
+  if (L < 0 || L > c->nx) return fail(LBM_EINVAL, "fringe length %d outside 0..nx = %d", L, c->nx);
+  if (!(s_max >= 0.0 && s_max <= 1.0)) return fail(LBM_EINVAL, "fringe strength must lie in [0, 1]");
+  if (!(p >= 0.0) || !std::isfinite(p)) return fail(LBM_EINVAL, "fringe exponent must be finite and >= 0");
+  if (L == 0) {
+    c->fringe.release();
+    c->fr_L = 0;
+    return LBM_OK;
+  }
+  // s(x) = s_max xi^p, xi = (x - (nx - L) + 1) / L on the layer, 0 before it (formed in double)
+  std::vector<double> sd(c->nx, 0.0);
+  for (int x = c->nx - L; x < c->nx; ++x) sd[x] = s_max * std::pow(double(x - (c->nx - L) + 1) / double(L), p);
+  CK(c->fringe.ensure((size_t)c->nx * c->ops->celem));
+  if (c->ops->celem == 8) {
+    CK(cudaMemcpyAsync(c->fringe.p, sd.data(), (size_t)c->nx * 8, cudaMemcpyHostToDevice, c->stream));
+  } else {
+    std::vector<float> sf(sd.begin(), sd.end());
+    CK(cudaMemcpyAsync(c->fringe.p, sf.data(), (size_t)c->nx * 4, cudaMemcpyHostToDevice, c->stream));
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  c->fr_L = L;
+  c->fr_smax = s_max;
+  c->fr_p = p;
   return LBM_OK;
 }
 
@@ -1077,6 +1125,7 @@ int lbm_set_collision(lbm_ctx* c, int model, double sigma) {
 // ---- adjoint ---------------------------------------------------------------------------------------------
 static int adj_check(lbm_ctx* c, int xa, int xb, double* wa, double* wb, int W) {
   if (c->model != LBM_BGK) return fail(LBM_ESTATE, "the adjoint is defined for the BGK collision only");
+  if (c->fr_L > 0) return fail(LBM_ESTATE, "the adjoint is defined without the outlet fringe zone");
   if (c->vm_n > 0) return fail(LBM_ESTATE, "the adjoint is defined for a steady inlet only");
   if (c->wm) return fail(LBM_ESTATE, "the wall model is not differentiated; switch it off (kappa <= 0)");
   if (xa < 0 || xa >= c->nx || xb < 0 || xb >= c->nx || xa == xb) return fail(LBM_EINVAL, "objective planes out of range");
@@ -1146,6 +1195,7 @@ int lbm_objective_forward(lbm_ctx* c, int T, int W, int xa, int xb, int ckpt, do
 int lbm_objective_backward(lbm_ctx* c, double* dJ_dgamma, double* dJ_duin) {
   if (!c) return fail(LBM_EINVAL, "null context");
   if (c->adj_t0 != c->t) return fail(LBM_ESTATE, "no forward run to differentiate (run lbm_objective_forward first)");
+  if (c->fr_L > 0) return fail(LBM_ESTATE, "the adjoint is defined without the outlet fringe zone");
   if (c->model != LBM_BGK) return fail(LBM_ESTATE, "the adjoint is defined for the BGK collision only");
   if (c->vm_n > 0) return fail(LBM_ESTATE, "the adjoint is defined for a steady inlet only");
   if (c->wm) return fail(LBM_ESTATE, "the wall model is not differentiated");
@@ -1232,6 +1282,7 @@ int lbm_adjoint_step(lbm_ctx* c, const void* lam_in, void* lam_out, int dtype, d
   if (c->vm_n > 0) return fail(LBM_ESTATE, "the adjoint is defined for a steady inlet only");
   if (c->wm) return fail(LBM_ESTATE, "the wall model is not differentiated");
   if (c->t & 1) return fail(LBM_ESTATE, "the reverse step needs the state after an even number of steps");
+  if (c->fr_L > 0) return fail(LBM_ESTATE, "the adjoint is defined without the outlet fringe zone");
   int rc;
   if ((rc = check_ptr(c, lam_in, "lam_in")) != LBM_OK) return rc;
   if ((rc = check_ptr(c, lam_out, "lam_out")) != LBM_OK) return rc;

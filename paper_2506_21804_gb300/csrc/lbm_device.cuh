@@ -170,6 +170,8 @@ struct Args {
   int wm;                  // wall model on
   int fuse;                // 1: list cells flagged T_INLINE are updated by the interior kernel; the
                            //    boundary-list kernel then runs over the other entries only
+  int inline_all;          // fused mode with the BGK collision: the interior kernel updates every list
+                           //    cell (no boundary-list kernel)
   const int* lidx;         // list position of every cell (-1 off the list)
   const int* lsub;         // list positions handled by the boundary-list kernel (fused mode)
   int n_sub;
@@ -189,6 +191,9 @@ struct Args {
   const void* uvel_rd;     // C[3][N] velocity field of the previous step
   void* uvel_wr;           // C[3][N] velocity field written by this step
   int pairs;               // interior kernel over cell pairs (nx even, 32-bit indices, few mixed warps)
+  // outlet fringe zone: strength s(x) per x-plane (compute type, nx values; 0 before the layer) or null
+  const void* fringe;
+  int fr_x0;               // first plane of the layer
 };
 
 // ---- AA-pattern slot map ------------------------------------------------------------------------------
@@ -452,6 +457,82 @@ __device__ __forceinline__ bool collide_fluid_x2(Get&& get, Put&& put, float2 ga
   });
   const float2 chk = add2(add2(abs2(rho), abs2(ux)), add2(abs2(uy), abs2(uz)));
   return chk.x < 1e30f && chk.y < 1e30f;
+}
+
+// The BGK collision of a fluid cell and the sigma = 0 update of a wall-model cell as one instruction
+// stream, for warps that mix the two (the mixed path of the interior kernel). In the opposite-pair
+// form of collide_fluid, with k the relaxation factor, v the homogenised velocity, g a weight and S a
+// strain,
+//   h*_i = k h_i + w_i [base + 4.5 rho ((c.v)^2 - k (c.u)^2) + g Q_i : S  +-  3 rho (c.v - k c.u)],
+//   base = (1 - k) drho - 1.5 rho (v.v - k u.u).
+// Fluid lanes (ws == nullptr): k = 1 - 1/tau_eff, v = gamma u + F/rho, g = 0, i.e. collide_fluid.
+// Wall lanes: k = 0, v = u^B + F/rho, g = -3 rho (tau - 1), S the modelled strain, i.e.
+// f* = f^eq(rho, v) + (1 - 1/tau) f^(1,FD) with f^(1,FD)_i = -(w_i rho tau / cs^2) Q_i : S
+// (collide_wall_state). Returns the density and the reported velocity u + F/(2 rho).
+template <int Q, class C>
+__device__ __forceinline__ void collide_unified(C* h, C gamma, const Args& a, const C* ws, C& rho_o, C& urx, C& ury,
+                                                C& urz) {
+  constexpr int H = Lat<Q>::H;
+  C drho = h[0], jx = C(0), jy = C(0), jz = C(0);
+  C sxx = C(0), syy = C(0), szz = C(0), sxy = C(0), sxz = C(0), syz = C(0);
+  sfor<1, H + 1>([&](auto I) {
+    constexpr int i = decltype(I)::value, cx = Lat<Q>::cx(i), cy = Lat<Q>::cy(i), cz = Lat<Q>::cz(i);
+    const C sp = h[i] + h[i + H], dp = h[i] - h[i + H];
+    drho += sp;
+    if constexpr (cx != 0) { jx += cmul<cx>(dp); sxx += sp; }
+    if constexpr (cy != 0) { jy += cmul<cy>(dp); syy += sp; }
+    if constexpr (cz != 0) { jz += cmul<cz>(dp); szz += sp; }
+    if constexpr (cx * cy != 0) sxy += cmul<cx * cy>(sp);
+    if constexpr (cx * cz != 0) sxz += cmul<cx * cz>(sp);
+    if constexpr (cy * cz != 0) syz += cmul<cy * cz>(sp);
+  });
+  const C rho = C(1) + drho, ir = rcp(rho);
+  const C ux = jx * ir, uy = jy * ir, uz = jz * ir;
+  const C usq = ux * ux + uy * uy + uz * uz;
+  C tau = a.tau0.get<C>();
+  if (a.use_smag != 0) {
+    const C d3 = drho * C(1.0 / 3.0);
+    const C pxx = sxx - d3 - rho * ux * ux, pyy = syy - d3 - rho * uy * uy, pzz = szz - d3 - rho * uz * uz;
+    const C pxy = sxy - rho * ux * uy, pxz = sxz - rho * ux * uz, pyz = syz - rho * uy * uz;
+    const C pn = sqrt(pxx * pxx + pyy * pyy + pzz * pzz + C(2) * (pxy * pxy + pxz * pxz + pyz * pyz));
+    const C t0 = a.tau0.get<C>();
+    tau = C(0.5) * (t0 + sqrt(t0 * t0 + a.smag.get<C>() * pn * ir));
+  }
+  C k = C(1) - rcp(tau);
+  C vx = gamma * ux, vy = gamma * uy, vz = gamma * uz;
+  C g = C(0), qxx = C(0), qyy = C(0), qzz = C(0), qxy = C(0), qxz = C(0), qyz = C(0);
+  if (ws != nullptr) {
+    k = C(0);
+    vx = ws[0]; vy = ws[1]; vz = ws[2];
+    g = -C(3) * rho * (ws[3] - C(1));
+    qxx = ws[4]; qyy = ws[5]; qzz = ws[6]; qxy = ws[7]; qxz = ws[8]; qyz = ws[9];
+  }
+  vx += a.fx.get<C>() * ir; vy += a.fy.get<C>() * ir; vz += a.fz.get<C>() * ir;
+  const C vsq = vx * vx + vy * vy + vz * vz;
+  const C base = (C(1) - k) * drho - C(1.5) * rho * (vsq - k * usq);
+  const C r45 = C(4.5) * rho, r3 = C(3) * rho;
+  const C tr3 = (qxx + qyy + qzz) * C(1.0 / 3.0);
+  h[0] = k * h[0] + wgt<Q, C>(0) * (base - g * tr3);
+  sfor<1, H + 1>([&](auto I) {
+    constexpr int i = decltype(I)::value, cx = Lat<Q>::cx(i), cy = Lat<Q>::cy(i), cz = Lat<Q>::cz(i);
+    const C cu = cdot_i<Q, i>(ux, uy, uz), cv = cdot_i<Q, i>(vx, vy, vz);
+    C qs = -tr3;  // Q_i : S, the same for i and its opposite
+    if constexpr (cx != 0) qs += qxx;
+    if constexpr (cy != 0) qs += qyy;
+    if constexpr (cz != 0) qs += qzz;
+    if constexpr (cx * cy != 0) qs += cmul<2 * cx * cy>(qxy);
+    if constexpr (cx * cz != 0) qs += cmul<2 * cx * cz>(qxz);
+    if constexpr (cy * cz != 0) qs += cmul<2 * cy * cz>(qyz);
+    const C sym = base + r45 * (cv * cv - k * (cu * cu)) + g * qs;
+    const C anti = r3 * (cv - k * cu);
+    h[i] = k * h[i] + wgt<Q, C>(i) * (sym + anti);
+    h[i + H] = k * h[i + H] + wgt<Q, C>(i) * (sym - anti);
+  });
+  rho_o = rho;
+  const C hf = C(0.5) * ir;
+  urx = ux + a.fx.get<C>() * hf;
+  ury = uy + a.fy.get<C>() * hf;
+  urz = uz + a.fz.get<C>() * hf;
 }
 
 // Regularised reconstruction: unknown populations (known(i) false) take the non-equilibrium part

@@ -37,7 +37,16 @@ __device__ __forceinline__ bool beyond_wall_face(const GeoArgs& g, int crossed) 
   return w;
 }
 
+// Coordinates of cell n; 32-bit divisions whenever the grid has fewer than 2^31 cells (a 64-bit
+// integer division is a long instruction sequence on the GPU).
 __device__ __forceinline__ void coords(const GeoArgs& g, long long n, int& x, int& y, int& z) {
+  if (g.N < (1LL << 31)) {
+    const unsigned un = unsigned(n), r = un / unsigned(g.nx);
+    x = int(un - r * unsigned(g.nx));
+    z = int(r / unsigned(g.ny));
+    y = int(r - unsigned(z) * unsigned(g.ny));
+    return;
+  }
   const long long r = n / g.nx;
   x = int(n - r * g.nx);
   z = int(r / g.ny);
@@ -74,6 +83,15 @@ __device__ __forceinline__ long long ref_cell(const GeoArgs& g, const uint8_t* t
   const long long r = lin(g, p);
   if ((type[r] & T_KIND) == K_SOLID) return -1;
   return r;
+}
+
+// Smallest index of a mask byte that is not a valid code (0, 1, 3, 4); *first_bad stays ~0 if none.
+__global__ void k_check_mask(const uint8_t* __restrict__ m, long long N, unsigned long long* first_bad) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N; n += stride) {
+    const uint8_t v = m[n];
+    if (!(v == 0 || v == 1 || v == 3 || v == 4)) atomicMin(first_bad, (unsigned long long)n);
+  }
 }
 
 template <int Q>
@@ -414,6 +432,13 @@ void geo_source_map(const GeoArgs& g, const uint8_t* type, int64_t* sdir, int64_
 void geo_inline_mark(const GeoArgs& g, uint8_t* type, int inline_min, cudaStream_t s) {
   const long long groups = (long long)((g.nx + 31) / 32) * g.ny * g.nz;
   k_inline_mark<<<nblocks(groups, 256), 256, 0, s>>>(g, type, inline_min);
+}
+
+void geo_check_mask(const uint8_t* mask, long long N, unsigned long long* first_bad, cudaStream_t s) {
+  cudaMemsetAsync(first_bad, 0xFF, sizeof(unsigned long long), s);
+  long long blocks = nblocks(N, 256);
+  if (blocks > 8 * 1216) blocks = 8 * 1216;
+  k_check_mask<<<unsigned(blocks), 256, 0, s>>>(mask, N, first_bad);
 }
 
 int geo_sub_blocks(int n_list) { return int(nblocks(n_list, SUB_THREADS)); }

@@ -120,7 +120,7 @@ struct Impl {
   }
   static void step_list(const Args& a, int odd, cudaStream_t s) {
     const int nj = a.lsub ? a.n_sub : a.n_list;
-    if (nj <= 0) return;
+    if (nj <= 0 || a.inline_all) return;
     if (a.model != 0) {
       if (odd) k_list<Q, S, true, true><<<blocks_for(nj, LIST_THREADS), LIST_THREADS, 0, s>>>(a);
       else k_list<Q, S, false, true><<<blocks_for(nj, LIST_THREADS), LIST_THREADS, 0, s>>>(a);

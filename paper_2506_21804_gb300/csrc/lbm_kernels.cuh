@@ -16,6 +16,13 @@ enum { LOAD_LOCAL = 0, LOAD_SLOTS = 1 };
 enum { STORE_MIRROR = 0, STORE_SLOTS = 1 };
 
 __device__ __forceinline__ void cell_coords(const Args& a, long long n, int& x, int& y, int& z) {
+  if (a.N < (1LL << 31)) {  // 32-bit divisions (a 64-bit one is a long instruction sequence)
+    const unsigned un = unsigned(n), r = un / unsigned(a.nx);
+    x = int(un - r * unsigned(a.nx));
+    z = int(r / unsigned(a.ny));
+    y = int(r - unsigned(z) * unsigned(a.ny));
+    return;
+  }
   const long long r = n / a.nx;
   x = int(n - r * a.nx);
   z = int(r / a.ny);
@@ -261,6 +268,23 @@ __device__ __forceinline__ unsigned long long cell_code(const Args& a, long long
 template <class C> __device__ __forceinline__ const C* cptr(const void* p) { return static_cast<const C*>(p); }
 template <class C> __device__ __forceinline__ C* cptr(void* p) { return static_cast<C*>(p); }
 
+// Outlet fringe zone (Sec. 3.2: the fixed-pressure outlet has a fringe zone in front of it; the
+// paper gives no parameters, so the layer is a reading): in the last planes x >= fr_x0 the
+// post-collision deviations of every cell other than INFLOW/OUTFLOW relax towards the equilibrium at
+// the outlet density and the cell's reported velocity, h*_i <- h*_i - s(x) (h*_i - (f^eq_i(rho_out, u)
+// - w_i)), with s(x) = s_max xi^p tabulated per plane on the host.
+template <int Q, class C>
+__device__ __forceinline__ void apply_fringe(const Args& a, int x, int kind, C urx, C ury, C urz, C* h) {
+  if (a.fringe == nullptr || x < a.fr_x0 || kind == K_INFLOW || kind == K_OUTFLOW) return;
+  const C s = static_cast<const C*>(a.fringe)[x];
+  const C ro = a.rho_out.get<C>(), dro = a.drho_out.get<C>();
+  const C usq = urx * urx + ury * ury + urz * urz;
+  sfor<0, Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    h[i] -= s * (h[i] - heq<Q, C, i>(dro, ro, urx, ury, urz, usq));
+  });
+}
+
 // Boundary reconstruction of INFLOW/OUTFLOW cells (in place on h).
 template <int Q, class C>
 __device__ __forceinline__ void apply_bc(const Args& a, int kind, int y, int z, C* h) {
@@ -300,6 +324,7 @@ __device__ __forceinline__ void collide_any(const Args& a, int kind, uint8_t t, 
   } else {
     collide_fluid<Q, C>(h, gamma_at<C>(a, n), a, rho, urx, ury, urz);
   }
+  apply_fringe<Q, C>(a, x, kind, urx, ury, urz, h);
   if ((t & T_REF) && k >= 0) {
     C* w = cptr<C>(a.ref_wr) + 3 * (long long)k;
     w[0] = urx; w[1] = ury; w[2] = urz;
@@ -340,6 +365,7 @@ __device__ __forceinline__ void list_cell_inline(const Args& a, S* f, int x, int
     if (kind == K_WALL && a.wm) collide_wall_state<Q, C>(h, a, cptr<C>(a.wst) + (long long)WALL_STATE * k, rho, urx, ury, urz);
     else collide_fluid<Q, C>(h, gamma_at<C>(a, n), a, rho, urx, ury, urz);
   }
+  apply_fringe<Q, C>(a, x, kind, urx, ury, urz, h);
   if (t & T_REF) {
     C* w = cptr<C>(a.ref_wr) + 3 * (long long)k;
     w[0] = urx; w[1] = ury; w[2] = urz;
@@ -364,7 +390,7 @@ template <int Q, class S, bool ODD, bool HRR = false>
 __device__ __forceinline__ void bulk_cell(const Args& a, S* f, int x, int y, int z, long long n, uint8_t t) {
   using C = typename Codec<S>::C;
   if (t & (T_LIST | T_KIND)) {
-    if ((t & T_INLINE) && a.fuse) list_cell_inline<Q, S, ODD, HRR>(a, f, x, y, z, n, t);
+    if (a.fuse && ((t & T_INLINE) || a.inline_all)) list_cell_inline<Q, S, ODD, HRR>(a, f, x, y, z, n, t);
     return;
   }
   const bool near = (t & T_NEAR) != 0;
@@ -379,17 +405,64 @@ __device__ __forceinline__ void bulk_cell(const Args& a, S* f, int x, int y, int
   } else {
     collide_fluid<Q, C>(h, gamma_at<C>(a, n), a, rho, urx, ury, urz);
   }
+  apply_fringe<Q, C>(a, x, K_FLUID, urx, ury, urz, h);
   if (!finite_all<C>(rho, urx, ury, urz)) atomicOr(a.status, ST_NAN);
   scatter<Q, S, ODD ? STORE_SLOTS : STORE_MIRROR>(a, f, x, y, z, n, near, h);
 }
+// Mixed path of the BGK interior kernel (fused mode, every list cell inline): one instruction stream
+// for every non-solid kind. Even steps gather and scatter the cell's own slots whatever its kind; odd
+// steps use per-lane slot codes (0 for plain cells, the list entry's codes for list cells, the
+// general rule for other cells next to a face), so lanes of different kinds only diverge in the
+// inlet/outlet reconstruction, the wall-state load and the general slot rule.
+template <int Q, class S, bool ODD>
+__device__ __forceinline__ void mixed_cell(const Args& a, S* f, int x, int y, int z, long long n, uint8_t t) {
+  using C = typename Codec<S>::C;
+  const int kind = t & T_KIND;
+  if (kind == K_SOLID) return;
+  const bool list = (t & T_LIST) != 0;
+  const int k = list ? a.lidx[n] : -1;
+  C h[Q];
+  unsigned long long code = 0;
+  if constexpr (ODD) {
+    code = list ? a.lcode[k] : ((t & T_NEAR) ? 0xAAAAAAAAAAAAAAAAull : 0ull);
+    gather_coded<Q, S>(a, f, x, y, z, n, code, h);
+  } else {
+    gather<Q, S, LOAD_LOCAL>(a, f, x, y, z, n, false, h);
+  }
+  if (kind == K_INFLOW || kind == K_OUTFLOW) apply_bc<Q, C>(a, kind, y, z, h);
+  const C* ws = (kind == K_WALL && a.wm) ? cptr<C>(a.wst) + (long long)WALL_STATE * k : nullptr;
+  C rho, urx, ury, urz;
+  collide_unified<Q, C>(h, gamma_at<C>(a, n), a, ws, rho, urx, ury, urz);
+  apply_fringe<Q, C>(a, x, kind, urx, ury, urz, h);
+  if (t & T_REF) {
+    C* w = cptr<C>(a.ref_wr) + 3 * (long long)k;
+    w[0] = urx; w[1] = ury; w[2] = urz;
+  }
+  if (!finite_all<C>(rho, urx, ury, urz)) atomicOr(a.status, ST_NAN);
+  if constexpr (ODD) scatter_coded<Q, S>(a, f, x, y, z, n, code, h);
+  else scatter<Q, S, STORE_MIRROR>(a, f, x, y, z, n, false, h);
+}
+
+// The warp decides its path with one ballot: 32 plain FLUID cells (no list entry, no solid or outside
+// source) take the plain path; any other warp takes the mixed path when every list cell is updated
+// here (BGK, fused mode), else the per-cell dispatch of bulk_cell. Blocks are whole warps, and every
+// thread reaches the ballot before any returns.
 template <int Q, class S, bool ODD>
 __global__ void __launch_bounds__(BULK_THREADS, (bulk_min_blocks<Q, S, ODD>())) k_bulk(const Args a) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y * blockDim.y + threadIdx.y;
   const int z = blockIdx.z;
-  if (x >= a.nx || y >= a.ny) return;
+  const bool in = x < a.nx && y < a.ny;
   const long long n = x + (long long)y * a.nx + (long long)z * a.nxy;
-  bulk_cell<Q, S, ODD>(a, static_cast<S*>(a.f), x, y, z, n, a.type[n]);
+  const uint8_t t = in ? a.type[n] : uint8_t(0);
+  const bool plain_warp = __all_sync(0xffffffffu, t == 0);
+  if (!in) return;
+  S* f = static_cast<S*>(a.f);
+  if (!plain_warp && a.inline_all) {
+    mixed_cell<Q, S, ODD>(a, f, x, y, z, n, t);
+    return;
+  }
+  bulk_cell<Q, S, ODD>(a, f, x, y, z, n, t);
 }
 // Interior kernel of the HRR collision (same cell set and slot handling as k_bulk).
 template <int Q, class S, bool ODD>

@@ -50,6 +50,8 @@ struct GeoArgs {
   int q;
 };
 void geo_classify(const GeoArgs&, const uint8_t* mask, uint8_t* type, unsigned* status, cudaStream_t);
+// smallest index of an invalid mask code (first_bad = ~0 when every code is valid)
+void geo_check_mask(const uint8_t* mask, long long N, unsigned long long* first_bad, cudaStream_t);
 void geo_mark_ref(const GeoArgs&, uint8_t* type, cudaStream_t);
 // list compaction: per-block counts (blocks of 256 cells), then scatter with block offsets
 int geo_count_blocks(const GeoArgs&);

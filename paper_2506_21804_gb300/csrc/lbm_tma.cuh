@@ -225,6 +225,7 @@ __global__ void __launch_bounds__(TMA_W + 32, 6) k_bulk_tma(const Args a, const 
     }
     C rho, urx, ury, urz;
     collide_fluid<Q, C>(h, gam, a, rho, urx, ury, urz);
+    apply_fringe<Q, C>(a, x, K_FLUID, urx, ury, urz, h);
     if (!finite_all<C>(rho, urx, ury, urz)) atomicOr(a.status, ST_NAN);
     scatter<Q, S, ODD ? STORE_SLOTS : STORE_MIRROR>(a, f, x, y, z, n, near, h);
   }

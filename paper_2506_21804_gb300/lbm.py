@@ -82,6 +82,7 @@ SIGNATURES = {
     "lbm_set_option": (_i, [_p, _i, _i]),
     "lbm_reduce_static": (_i, [_i, _p, _i, _p, ctypes.c_int64, _p, _p]),
     "lbm_launch_count": (_i, [_p, _p]),
+    "lbm_set_fringe": (_i, [_p, _i, _d, _d]),
     "lbm_reduce_static_error": (ctypes.c_char_p, []),
     "lbm_debug_dump": (_i, [_p, _i, _p, ctypes.c_size_t]),
 }
@@ -192,6 +193,10 @@ class Lattice:
 
     def set_outflow(self, rho_out):
         _check(lib().lbm_set_outflow(self.h, float(rho_out)))
+
+    def set_fringe(self, L, s_max, p=2.0):
+        """Outlet fringe zone over the last L planes (L = 0: off), strength s_max xi^p."""
+        _check(lib().lbm_set_fringe(self.h, int(L), float(s_max), float(p)))
 
     def set_porosity(self, gamma):
         if gamma is None:
@@ -366,6 +371,8 @@ class Lattice:
             lat.set_collision(w.model, w.sigma)
         if getattr(w, "vortex", None):
             lat.set_vortex_inlet(*w.vortex)
+        if getattr(w, "fringe", None):
+            lat.set_fringe(*w.fringe)
         if init:
             dt = np.float64 if storage == F64 else np.float32
             lat.init_equilibrium(np.asarray(w.rho0, dt), np.asarray(w.u0, dt))
