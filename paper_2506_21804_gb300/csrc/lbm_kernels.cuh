@@ -390,7 +390,9 @@ template <int Q, class S, bool ODD, bool HRR = false>
 __device__ __forceinline__ void bulk_cell(const Args& a, S* f, int x, int y, int z, long long n, uint8_t t) {
   using C = typename Codec<S>::C;
   if (t & (T_LIST | T_KIND)) {
-    if (a.fuse && ((t & T_INLINE) || a.inline_all)) list_cell_inline<Q, S, ODD, HRR>(a, f, x, y, z, n, t);
+    // list cells updated here (T_INLINE, or every list cell when inline_all); solid cells and the
+    // list cells of the boundary-list kernel are skipped
+    if ((t & T_LIST) && a.fuse && ((t & T_INLINE) || a.inline_all)) list_cell_inline<Q, S, ODD, HRR>(a, f, x, y, z, n, t);
     return;
   }
   const bool near = (t & T_NEAR) != 0;
