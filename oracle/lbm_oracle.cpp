@@ -167,6 +167,7 @@ struct Oracle {
   std::vector<double> uin_cur;  // inlet velocity of the current (last) step, 3 * ny * nz
   // outlet fringe zone (Sec. 3.2); off when fr_L == 0
   int fr_L = 0;
+  int fr_x0 = 0;  // first plane of the layer (nx - L for the whole domain; any value for a crop)
   double fr_smax = 0.0, fr_p = 2.0;
   long t = 0;
   // adjoint bookkeeping
@@ -222,10 +223,26 @@ bool solid_like(const Oracle& o, int x, int y, int z, const int d[3]) {
   return o.mask[idx(o, p[0], p[1], p[2])] == M_SOLID;
 }
 
+// A cell "next to the boundary": some streaming source x - c_i is a SOLID cell or lies beyond a
+// non-periodic face.
+bool near_boundary(const Oracle& o, long r) {
+  int x, y, z;
+  coords(o, r, x, y, z);
+  for (int i = 1; i < o.L.Q; ++i) {
+    int q[3] = {x - o.L.c[i][0], y - o.L.c[i][1], z - o.L.c[i][2]};
+    if (resolve(o, q)) return true;
+    if (o.mask[idx(o, q[0], q[1], q[2])] == M_SOLID) return true;
+  }
+  return false;
+}
+
 // Cell classification: kind precedence SOLID > INFLOW > OUTFLOW > WALL > FLUID, where WALL is a
 // non-solid cell with at least one solid(-like) neighbour. Wall normal n = -v/|v| with
-// v = sum over solid neighbours of w_i c_i (integer weights). Reference cell of a WALL cell: one
-// step from it along the dominant axis of n (ties: lowest axis), if that cell exists and is not solid.
+// v = sum over solid neighbours of w_i c_i (integer weights). Reference cell of a WALL cell: the
+// cell one step from it along the dominant axis of n (ties: lowest axis), provided that cell is a
+// FLUID cell away from every boundary (no solid or outside streaming source). Reading of Sec. 2.2.1:
+// the wall law's reference point has to lie in the flow; in gaps one or two cells wide it would sit
+// on the opposite wall or on a domain face, and such a WALL cell has no reference (u^B = 0).
 void classify(Oracle& o) {
   const Lat& L = o.L;
   o.kind.assign(o.N, K_FLUID);
@@ -265,7 +282,7 @@ void classify(Oracle& o) {
     p[a] += (v[a] > 0) ? -1 : 1;  // along n = -v
     if (resolve(o, p)) continue;
     long r = idx(o, p[0], p[1], p[2]);
-    if (o.kind[r] == K_SOLID) continue;
+    if (o.kind[r] != K_FLUID || near_boundary(o, r)) continue;
     o.refcell[n] = r;
     o.isref[r] = 1;
   }
@@ -699,14 +716,16 @@ void collide_cell_core(const Oracle& o, long n, T f[27], T gamma, const T ub[3],
 }
 
 // Outlet fringe zone (Sec. 3.2: the outlet is a fixed local pressure with a fringe zone in front
-// of it; the paper gives no parameters, so the layer is a reading). The last L planes x >= nx - L
-// form the layer; in it every cell that is neither INFLOW nor OUTFLOW relaxes its post-collision
-// populations towards the equilibrium at the outlet density and its own reported velocity:
-//   f*_i <- f*_i - s(x) (f*_i - f^eq_i(rho_out, u)),   s(x) = s_max xi^p,  xi = (x - (nx - L) + 1)/L,
+// of it; the paper gives no parameters, so the layer is a reading). The last L planes x >= x0 =
+// nx - L form the layer; in it every cell that is neither INFLOW nor OUTFLOW relaxes its
+// post-collision populations towards the equilibrium at the outlet density and its own reported
+// velocity:
+//   f*_i <- f*_i - s(x) (f*_i - f^eq_i(rho_out, u)),   s(x) = s_max xi^p,  xi = (x - x0 + 1)/L,
 // so the strength rises from s_max L^-p at the first plane to s_max at the last (p = 0: constant).
+// (A crop of a larger domain keeps the domain's layer by giving its own x0.)
 double fringe_strength(const Oracle& o, int x) {
-  if (o.fr_L <= 0 || x < o.nx - o.fr_L) return 0.0;
-  const double xi = double(x - (o.nx - o.fr_L) + 1) / double(o.fr_L);
+  if (o.fr_L <= 0 || x < o.fr_x0) return 0.0;
+  const double xi = double(x - o.fr_x0 + 1) / double(o.fr_L);
   return o.fr_smax * std::pow(xi, o.fr_p);
 }
 
@@ -1124,13 +1143,14 @@ void orc_inflow_field(void* h, double* out) {
 unsigned long long orc_splitmix64(unsigned long long z) { return splitmix64_out(z); }
 double orc_vm_uniform(unsigned long long seed, unsigned long long counter) { return vm_uniform(seed, counter); }
 void orc_set_outflow(void* h, double rho) { static_cast<Oracle*>(h)->rho_out = rho; }
-int orc_set_fringe(void* h, int L, double smax, double p) {
+int orc_set_fringe(void* h, int L, double smax, double p, int x0) {
   Oracle* o = static_cast<Oracle*>(h);
   if (L < 0 || L > o->nx || !(smax >= 0.0 && smax <= 1.0) || !(p >= 0.0)) {
     g_err = "fringe: need 0 <= L <= nx, 0 <= s_max <= 1, p >= 0";
     return 1;
   }
   o->fr_L = L;
+  o->fr_x0 = x0;
   o->fr_smax = smax;
   o->fr_p = p;
   return 0;

@@ -40,7 +40,7 @@ def lib():
             "orc_set_force": (None, [_p, _d, _d, _d]),
             "orc_set_inflow": (None, [_p, _p]),
             "orc_set_outflow": (None, [_p, _d]),
-            "orc_set_fringe": (_i, [_p, _i, _d, _d]),
+            "orc_set_fringe": (_i, [_p, _i, _d, _d, _i]),
             "orc_fringe_strength": (_d, [_p, _i]),
             "orc_set_porosity": (None, [_p, _p]),
             "orc_set_wall_model": (None, [_p, _i, _d, _d]),
@@ -271,9 +271,11 @@ class Oracle:
     def set_outflow(self, rho):
         lib().orc_set_outflow(self.h, rho)
 
-    def set_fringe(self, L, s_max, p=2.0):
-        """Outlet fringe zone over the last L planes (L = 0: off), strength s_max xi^p."""
-        self._chk(lib().orc_set_fringe(self.h, int(L), float(s_max), float(p)))
+    def set_fringe(self, L, s_max, p=2.0, x0=None):
+        """Outlet fringe zone over the last L planes (L = 0: off), strength s_max xi^p with
+        xi = (x - x0 + 1)/L; x0 = nx - L unless given (a crop keeps its domain's layer)."""
+        x0 = self.nx - int(L) if x0 is None else int(x0)
+        self._chk(lib().orc_set_fringe(self.h, int(L), float(s_max), float(p), x0))
 
     def fringe_strength(self, x):
         return lib().orc_fringe_strength(self.h, int(x))

@@ -4,7 +4,8 @@ finite-difference non-equilibrium part f^(1,FD)) against quantities this file co
 Nothing here goes through the oracle's wall-model functions. For every WALL cell the test derives,
 from the mask and the oracle's populations alone:
   * the wall normal n = -sum_{solid i} w_i c_i / |...| and the reference cell one step along the
-    dominant axis of n;
+    dominant axis of n, used only when it is a FLUID cell away from every boundary (no solid or
+    outside streaming source: the reference point lies in the flow);
   * the reference velocity (the reported velocity j/rho + F/(2 rho) of that cell in the state the
     step starts from) and its tangential part u_t = u_r - (u_r . n) n, t = u_t/|u_t|;
   * u+ at the reference distance y_r = y_w + 1 from u+ y+(u+) = |u_t| y_r / nu, u_tau = |u_t|/u+,
@@ -87,11 +88,23 @@ def _solid_at(w, p):
     return w.mask[q[0] + w.nx * (q[1] + w.ny * q[2])] == I.MASK_SOLID
 
 
+def _plain_fluid(w, c, r):
+    """Fluid cell with no solid or outside streaming source (the only admissible reference cell)."""
+    if w.mask[r] != I.MASK_FLUID:
+        return False
+    x, y, z = r % w.nx, (r // w.nx) % w.ny, r // (w.nx * w.ny)
+    for i in range(1, len(c)):
+        q = _wrap(w, (x - c[i, 0], y - c[i, 1], z - c[i, 2]))
+        if q is None or w.mask[q[0] + w.nx * (q[1] + w.ny * q[2])] == I.MASK_SOLID:
+            return False
+    return True
+
+
 def expected_wall_update(w, c, wts, f0, n, meta_nu):
     """The sigma = 0 update of WALL cell n, derived in the test: (rho, u_hat, tau, S). A cell whose
     weighted solid-neighbour sum vanishes (solids on opposite sides) has no normal and gets u^B = 0,
-    S = 0; so does a cell whose reference position is solid or outside, or whose tangential reference
-    velocity is below 1e-12."""
+    S = 0; so does a cell whose reference position is not a plain fluid cell, or whose tangential
+    reference velocity is below 1e-12."""
     x, y, z = n % w.nx, (n // w.nx) % w.ny, n // (w.nx * w.ny)
     # integer sum of W_i c_i (W_i = w_i times the common denominator), so that ties between axes
     # are exact
@@ -115,7 +128,7 @@ def expected_wall_update(w, c, wts, f0, n, meta_nu):
     dudn = 0.0
     if rp is not None:
         r = rp[0] + w.nx * (rp[1] + w.ny * rp[2])
-        if w.mask[r] != I.MASK_SOLID:
+        if _plain_fluid(w, c, r):
             rho_r = f0[:, r].sum()
             u_r = (c.T @ f0[:, r]) / rho_r + F / (2.0 * rho_r)
             u_t = u_r - (u_r @ nrm) * nrm
