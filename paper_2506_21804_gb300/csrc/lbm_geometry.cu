@@ -69,8 +69,11 @@ __device__ __forceinline__ void normal_sum(const GeoArgs& g, const uint8_t* type
   });
 }
 
-// Reference cell of a WALL cell: one step along the dominant axis of n = -v (ties: lowest axis);
-// -1 when v = 0, or the cell lies outside the domain or is solid.
+// Reference cell of a WALL cell: one step along the dominant axis of n = -v (ties: lowest axis),
+// provided that cell is a FLUID cell away from every boundary (kind FLUID, T_NEAR clear: no solid or
+// outside streaming source); -1 otherwise, and when v = 0. Reading of Sec. 2.2.1: the wall law's
+// reference point has to lie in the flow; in gaps one or two cells wide it would sit on the opposite
+// wall or on a domain face (such WALL cells get u^B = 0).
 __device__ __forceinline__ long long ref_cell(const GeoArgs& g, const uint8_t* type, int x, int y, int z, const int v[3]) {
   if (v[0] == 0 && v[1] == 0 && v[2] == 0) return -1;
   int a = 0;
@@ -81,7 +84,7 @@ __device__ __forceinline__ long long ref_cell(const GeoArgs& g, const uint8_t* t
   const Pos p = wrap(g, x + d[0], y + d[1], z + d[2]);
   if (p.crossed) return -1;
   const long long r = lin(g, p);
-  if ((type[r] & T_KIND) == K_SOLID) return -1;
+  if ((type[r] & (T_KIND | T_NEAR)) != K_FLUID) return -1;
   return r;
 }
 

@@ -75,7 +75,7 @@ class Workload:
     model: int = 0                         # collision: 0 BGK, 1 hybrid recursive regularised
     sigma: float = 1.0                     # hybridisation factor of the HRR collision
     vortex: Optional[tuple] = None         # vortex-method inlet (n, sigma, intensity, seed) or None
-    fringe: Optional[tuple] = None         # outlet fringe zone (L, s_max, p) or None
+    fringe: Optional[tuple] = None         # outlet fringe zone (L, s_max, p[, first plane]) or None
     meta: dict = field(default_factory=dict)
 
     @property
@@ -156,12 +156,13 @@ def loglaw_profile(z, u_ref=0.05, z_ref=200.0, z0=0.5):
 
 
 def canopy(nx=512, ny=512, nz=256, q=19, n_buildings=200, seed=2506, cs=0.1, nu=1e-4, crop=None,
-           domain=None, wall_model=True, dtype=np.float32):
+           domain=None, wall_model=True, fringe=True, dtype=np.float32):
     """Urban canopy: solid ground z = 0, seeded box buildings, log-law inlet at x = 0, pressure outlet
-    at x = nx-1, full-slip faces y = 0, y = ny-1, z = nz-1. Every fluid cell next to a solid gets the
-    wall function. `domain` = (NX, NY, NZ) of the seeded geometry when it differs from the grid and
-    `crop` = (x0, y0, z0) selects the sub-box that is simulated (the crop keeps the same face
-    conditions)."""
+    at x = nx-1 with a fringe zone over the last NX/8 planes (strength 0.2 xi^2), full-slip faces
+    y = 0, y = ny-1, z = nz-1. Every fluid cell next to a solid gets the wall function. `domain` =
+    (NX, NY, NZ) of the seeded geometry when it differs from the grid and `crop` = (x0, y0, z0)
+    selects the sub-box that is simulated (the crop keeps the same face conditions and the domain's
+    fringe layer: fringe = (L, s_max, p, first layer plane in crop coordinates))."""
     NX, NY, NZ = domain if domain is not None else (nx, ny, nz)
     ox, oy, oz = crop if crop is not None else (0, 0, 0)
     bl = canopy_buildings(NX, NY, NZ, n_buildings=n_buildings, seed=seed)
@@ -191,9 +192,14 @@ def canopy(nx=512, ny=512, nz=256, q=19, n_buildings=200, seed=2506, cs=0.1, nu=
     u[:, solid] = 0.0
     rho = np.ones(x.size, dtype)
     tau = 0.5 + 3.0 * nu
+    fr = None
+    if fringe:
+        L = max(1, NX // 8)
+        if NX - L - ox < nx:  # the layer reaches into the simulated box
+            fr = (L, 0.2, 2.0, NX - L - ox)
     return Workload(name=f"canopy{nx}x{ny}x{nz}q{q}", q=q, nx=nx, ny=ny, nz=nz, tau=tau, cs=cs,
                     faces=(FACE_OPEN, FACE_OPEN, FACE_SLIP, FACE_SLIP, FACE_WALL, FACE_SLIP),
-                    mask=mask, uin=uin, rho_out=1.0, wall_model=wall_model, rho0=rho, u0=u,
+                    mask=mask, uin=uin, rho_out=1.0, wall_model=wall_model, rho0=rho, u0=u, fringe=fr,
                     meta=dict(buildings=bl, nu=nu, crop=crop, domain=(NX, NY, NZ)))
 
 

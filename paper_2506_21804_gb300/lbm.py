@@ -372,7 +372,10 @@ class Lattice:
         if getattr(w, "vortex", None):
             lat.set_vortex_inlet(*w.vortex)
         if getattr(w, "fringe", None):
-            lat.set_fringe(*w.fringe)
+            fr = w.fringe
+            if len(fr) > 3 and fr[3] != w.nx - fr[0]:
+                raise ValueError("the library's fringe layer ends at the outlet plane (a crop of it is oracle-only)")
+            lat.set_fringe(*fr[:3])
         if init:
             dt = np.float64 if storage == F64 else np.float32
             lat.init_equilibrium(np.asarray(w.rho0, dt), np.asarray(w.u0, dt))

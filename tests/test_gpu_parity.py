@@ -458,6 +458,10 @@ def _crop_oracle(w, centre, R):
         sub.ywall = np.asarray(w.ywall)[gidx]
     if w.gamma is not None:
         sub.gamma = np.asarray(w.gamma)[gidx]
+    if getattr(w, "fringe", None):
+        L, s_max, p = w.fringe[:3]
+        first = w.fringe[3] if len(w.fringe) > 3 else w.nx - L
+        sub.fringe = (L, s_max, p, first - int(xs[0]))  # the domain's layer in crop coordinates
     if w.uin is not None:
         YY, ZZ = np.meshgrid(ys, zs, indexing="xy")
         pidx = (YY + w.ny * ZZ).reshape(-1)
