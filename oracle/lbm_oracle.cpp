@@ -1145,8 +1145,9 @@ double orc_vm_uniform(unsigned long long seed, unsigned long long counter) { ret
 void orc_set_outflow(void* h, double rho) { static_cast<Oracle*>(h)->rho_out = rho; }
 int orc_set_fringe(void* h, int L, double smax, double p, int x0) {
   Oracle* o = static_cast<Oracle*>(h);
-  if (L < 0 || L > o->nx || !(smax >= 0.0 && smax <= 1.0) || !(p >= 0.0)) {
-    g_err = "fringe: need 0 <= L <= nx, 0 <= s_max <= 1, p >= 0";
+  // L may exceed nx: a crop of a larger domain keeps the domain's layer (first plane x0)
+  if (L < 0 || !(smax >= 0.0 && smax <= 1.0) || !(p >= 0.0)) {
+    g_err = "fringe: need L >= 0, 0 <= s_max <= 1, p >= 0";
     return 1;
   }
   o->fr_L = L;

@@ -44,7 +44,7 @@ def test_fringe_strength_profile():
         assert o.fringe_strength(x) == pytest.approx(want, rel=0, abs=1e-16)
     assert o.fringe_strength(nx - 1) == s_max
     with pytest.raises(ValueError):
-        o.set_fringe(nx + 1, 0.1, 2.0)
+        o.set_fringe(-1, 0.1, 2.0)
     with pytest.raises(ValueError):
         o.set_fringe(3, 1.5, 2.0)
 
