@@ -101,8 +101,6 @@ struct lbm_ctx {
   DevBuf uvel0, uvel1;  // HRR velocity fields (step t reads uvel[t & 1], writes the other)
   DevBuf uin_a, uin_b, vort, vpart;  // vortex inlet: current/previous inlet fields, vortex list, partial fields
   DevBuf fringe;  // outlet fringe zone: strength per x-plane (compute type)
-  DevBuf mseg, mseg_cnt;  // mixed 32-cell x-segments of the split interior update, and their block counts
-  int n_mseg = 0;
   int fr_L = 0;
   double fr_smax = 0.0, fr_p = 2.0;
   DevBuf geo_counts, geo_sub, geo_kinds;  // geometry set-up scratch (per-block counts, kind counters)
@@ -125,7 +123,7 @@ struct lbm_ctx {
   double adj_ms[3] = {0, 0, 0};
 
   ~lbm_ctx() {
-    DevBuf* all[] = {&mseg, &mseg_cnt, &fringe, &geo_counts, &geo_sub, &geo_kinds, &uin_a, &uin_b, &vort, &vpart, &uvel0, &uvel1, &lidx, &lsub, &lwall, &lbc, &wst, &f, &type, &mask, &wdist, &gamma, &uin, &lcell, &nsum, &wref, &lxyz, &lcode, &wnrm, &wyw, &ref0, &ref1, &status, &red,
+    DevBuf* all[] = {&fringe, &geo_counts, &geo_sub, &geo_kinds, &uin_a, &uin_b, &vort, &vpart, &uvel0, &uvel1, &lidx, &lsub, &lwall, &lbc, &wst, &f, &type, &mask, &wdist, &gamma, &uin, &lcell, &nsum, &wref, &lxyz, &lcode, &wnrm, &wyw, &ref0, &ref1, &status, &red,
                      &redout, &stage, &lamA, &lamB, &dgam, &duin, &plane};
     for (DevBuf* b : all) b->release();
     for (auto& b : ckpts) b.release();
@@ -222,8 +220,6 @@ Args make_args(const lbm_ctx* c) {
   a.uvel_rd = (c->t & 1) ? c->uvel1.p : c->uvel0.p;
   a.uvel_wr = (c->t & 1) ? c->uvel0.p : c->uvel1.p;
   a.pairs = pairs_selected(c) ? 1 : 0;
-  a.mseg = (a.inline_all && !a.pairs && c->mseg.p) ? static_cast<const int*>(c->mseg.p) : nullptr;
-  a.n_mseg = c->n_mseg;
   a.fringe = c->fr_L > 0 ? c->fringe.p : nullptr;
   a.fr_x0 = c->nx - c->fr_L;
   return a;
@@ -407,27 +403,6 @@ int build_geometry(lbm_ctx* c) {
       c->pair_mixed = pm[0] ? double(pm[1]) / double(pm[0]) : 1.0;
     }
   }
-  {
-    // mixed 32-cell x-segments for the split interior update (ascending, two passes like the list)
-    const int sb = geo_segment_blocks(g);
-    CK(c->mseg_cnt.ensure((size_t)sb * sizeof(int)));
-    geo_segment_count(g, static_cast<const uint8_t*>(c->type.p), static_cast<int*>(c->mseg_cnt.p), s);
-    std::vector<int> hs(sb);
-    CK(cudaMemcpyAsync(hs.data(), c->mseg_cnt.p, sb * sizeof(int), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    long long tot = 0;
-    for (int b = 0; b < sb; ++b) {
-      const int v = hs[b];
-      hs[b] = int(tot);
-      tot += v;
-    }
-    c->n_mseg = int(tot);
-    CK(c->mseg.ensure(std::max<size_t>(1, (size_t)tot) * sizeof(int)));
-    CK(cudaMemcpyAsync(c->mseg_cnt.p, hs.data(), sb * sizeof(int), cudaMemcpyHostToDevice, s));
-    geo_segment_write(g, static_cast<const uint8_t*>(c->type.p), static_cast<const int*>(c->mseg_cnt.p),
-                      static_cast<int*>(c->mseg.p), s);
-    CK(cudaGetLastError());
-  }
   c->type_host_valid = false;
   return LBM_OK;
 }
@@ -493,7 +468,7 @@ void launch_step(lbm_ctx* c, cudaEvent_t before_bulk = nullptr, cudaEvent_t afte
   }
   if (before_bulk) cudaEventRecord(before_bulk, c->stream);
   c->ops->step_bulk(a, odd, c->stream);
-  c->launches += (a.mseg && a.n_mseg > 0) ? 2 : 1;
+  ++c->launches;
   if (after_bulk) cudaEventRecord(after_bulk, c->stream);
   if (!a.inline_all && (a.lsub ? a.n_sub : a.n_list) > 0) {
     c->ops->step_list(a, odd, c->stream);

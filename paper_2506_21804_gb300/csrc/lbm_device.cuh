@@ -191,10 +191,6 @@ struct Args {
   const void* uvel_rd;     // C[3][N] velocity field of the previous step
   void* uvel_wr;           // C[3][N] velocity field written by this step
   int pairs;               // interior kernel over cell pairs (nx even, 32-bit indices, few mixed warps)
-  // split interior update (BGK, every list cell inline, one cell per thread): k_bulk_plain updates
-  // the all-plain 32-cell x-segments, k_bulk_mixed the n_mseg mixed segments listed in mseg
-  const int* mseg;
-  int n_mseg;
   // outlet fringe zone: strength s(x) per x-plane (compute type, nx values; 0 before the layer) or null
   const void* fringe;
   int fr_x0;               // first plane of the layer

@@ -327,45 +327,6 @@ __global__ void __launch_bounds__(SUB_THREADS) k_sub_write(const uint8_t* type, 
 // Groups of 64 cells along x (the cells of one warp of the paired kernels) that mix plain cell
 // pairs (both cells plain FLUID, type byte 0) with pairs that take the per-cell path: such a warp
 // runs both paths. out[0] += groups, out[1] += mixed groups. nx even.
-// Mixed 32-cell x-segments (the warps of the interior kernel): a segment is mixed when it holds a
-// cell that is not a plain FLUID cell (type byte != 0) and is not entirely solid. Two passes like the
-// boundary list: per-block counts, then ascending segment indices at exclusive block offsets.
-__device__ __forceinline__ bool segment_mixed(const GeoArgs& g, const uint8_t* type, long long s) {
-  const int segs = (g.nx + 31) / 32;
-  const long long row = s / segs;
-  const int x0 = int(s - row * segs) * 32;
-  const int x1 = x0 + 32 < g.nx ? x0 + 32 : g.nx;
-  const uint8_t* t = type + row * g.nx;
-  bool other = false, fluid = false;
-  for (int x = x0; x < x1; ++x) {
-    const uint8_t v = t[x];
-    if (v != 0) other = true;
-    if ((v & T_KIND) != K_SOLID) fluid = true;
-  }
-  return other && fluid;
-}
-
-__global__ void k_segment_count(const GeoArgs g, const uint8_t* type, long long n_seg, int* counts) {
-  const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const bool f = s < n_seg && segment_mixed(g, type, s);
-  const int c = __syncthreads_count(f);
-  if (threadIdx.x == 0) counts[blockIdx.x] = c;
-}
-
-__global__ void k_segment_write(const GeoArgs g, const uint8_t* type, long long n_seg, const int* offsets,
-                                int* list) {
-  __shared__ int wcount[256 / 32];
-  const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const bool f = s < n_seg && segment_mixed(g, type, s);
-  const unsigned b = __ballot_sync(0xffffffffu, f);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (lane == 0) wcount[w] = __popc(b);
-  __syncthreads();
-  int base = offsets[blockIdx.x];
-  for (int i = 0; i < w; ++i) base += wcount[i];
-  if (f) list[base + __popc(b & ((1u << lane) - 1u))] = int(s);
-}
-
 __global__ void k_pair_mix(const GeoArgs g, const uint8_t* type, unsigned long long* out) {
   const int groups = (g.nx + 63) / 64;
   const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -494,15 +455,6 @@ void geo_sub_write(const uint8_t* type, const long long* lcell, int n_list, cons
                    int* lbc, cudaStream_t s) {
   if (n_list <= 0) return;
   k_sub_write<<<nblocks(n_list, SUB_THREADS), SUB_THREADS, 0, s>>>(type, lcell, n_list, offsets, lsub, lwall, lbc);
-}
-
-long long geo_segments(const GeoArgs& g) { return (long long)((g.nx + 31) / 32) * g.ny * g.nz; }
-int geo_segment_blocks(const GeoArgs& g) { return int(nblocks(geo_segments(g), 256)); }
-void geo_segment_count(const GeoArgs& g, const uint8_t* type, int* counts, cudaStream_t s) {
-  k_segment_count<<<nblocks(geo_segments(g), 256), 256, 0, s>>>(g, type, geo_segments(g), counts);
-}
-void geo_segment_write(const GeoArgs& g, const uint8_t* type, const int* offsets, int* list, cudaStream_t s) {
-  k_segment_write<<<nblocks(geo_segments(g), 256), 256, 0, s>>>(g, type, geo_segments(g), offsets, list);
 }
 
 void geo_pair_mix(const GeoArgs& g, const uint8_t* type, unsigned long long* out, cudaStream_t s) {

@@ -115,17 +115,6 @@ struct Impl {
         return;
       }
     }
-    if (a.mseg) {
-      // split form: plain warps, then the listed mixed segments (4 warps per CTA)
-      if (odd) k_bulk_plain<Q, S, true><<<bulk_grid(a), bulk_block(a), 0, s>>>(a);
-      else k_bulk_plain<Q, S, false><<<bulk_grid(a), bulk_block(a), 0, s>>>(a);
-      if (a.n_mseg > 0) {
-        const unsigned g = unsigned((a.n_mseg + BULK_THREADS / 32 - 1) / (BULK_THREADS / 32));
-        if (odd) k_bulk_mixed<Q, S, true><<<g, BULK_THREADS, 0, s>>>(a);
-        else k_bulk_mixed<Q, S, false><<<g, BULK_THREADS, 0, s>>>(a);
-      }
-      return;
-    }
     if (odd) k_bulk<Q, S, true><<<bulk_grid(a), bulk_block(a), 0, s>>>(a);
     else k_bulk<Q, S, false><<<bulk_grid(a), bulk_block(a), 0, s>>>(a);
   }

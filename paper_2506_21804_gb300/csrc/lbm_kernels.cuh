@@ -466,48 +466,6 @@ __global__ void __launch_bounds__(BULK_THREADS, (bulk_min_blocks<Q, S, ODD>())) 
   }
   bulk_cell<Q, S, ODD>(a, f, x, y, z, n, t);
 }
-// Split form of k_bulk (BGK, every list cell inline): k_bulk_plain updates the warps whose 32 cells are
-// all plain FLUID cells and leaves every other warp to k_bulk_mixed, which runs over the list of mixed
-// 32-cell x-segments built with the geometry (entirely solid segments are in neither). Each kernel
-// carries only its own path, so the plain one keeps the register budget and instruction footprint of
-// the plain update.
-template <int Q, class S, bool ODD>
-__global__ void __launch_bounds__(BULK_THREADS, (bulk_min_blocks<Q, S, ODD>())) k_bulk_plain(const Args a) {
-  using C = typename Codec<S>::C;
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
-  const int z = blockIdx.z;
-  const bool in = x < a.nx && y < a.ny;
-  const long long n = x + (long long)y * a.nx + (long long)z * a.nxy;
-  const uint8_t t = in ? a.type[n] : uint8_t(0);
-  if (!__all_sync(0xffffffffu, t == 0) || !in) return;
-  S* f = static_cast<S*>(a.f);
-  C h[Q];
-  gather<Q, S, ODD ? LOAD_SLOTS : LOAD_LOCAL>(a, f, x, y, z, n, false, h);
-  C rho, urx, ury, urz;
-  collide_fluid<Q, C>(h, gamma_at<C>(a, n), a, rho, urx, ury, urz);
-  apply_fringe<Q, C>(a, x, K_FLUID, urx, ury, urz, h);
-  if (!finite_all<C>(rho, urx, ury, urz)) atomicOr(a.status, ST_NAN);
-  scatter<Q, S, ODD ? STORE_SLOTS : STORE_MIRROR>(a, f, x, y, z, n, false, h);
-}
-
-#ifndef LBM_MIXED_MINB
-#define LBM_MIXED_MINB 6
-#endif
-template <int Q, class S, bool ODD>
-__global__ void __launch_bounds__(BULK_THREADS, (sizeof(S) == 8 ? 1 : LBM_MIXED_MINB)) k_bulk_mixed(const Args a) {
-  const int wi = blockIdx.x * (BULK_THREADS / 32) + (threadIdx.x >> 5);
-  if (wi >= a.n_mseg) return;
-  const unsigned segs = unsigned(a.nx + 31) / 32u;
-  const unsigned sidx = unsigned(a.mseg[wi]);
-  const unsigned row = sidx / segs;
-  const int x = int(sidx - row * segs) * 32 + int(threadIdx.x & 31);
-  if (x >= a.nx) return;
-  const unsigned z = row / unsigned(a.ny), y = row - z * unsigned(a.ny);
-  const long long n = x + (long long)row * a.nx;
-  mixed_cell<Q, S, ODD>(a, static_cast<S*>(a.f), x, int(y), int(z), n, a.type[n]);
-}
-
 // Interior kernel of the HRR collision (same cell set and slot handling as k_bulk).
 template <int Q, class S, bool ODD>
 __global__ void __launch_bounds__(BULK_THREADS) k_bulk_hrr(const Args a) {

@@ -70,12 +70,6 @@ void geo_sub_count(const uint8_t* type, const long long* lcell, int n_list, int*
 void geo_sub_write(const uint8_t* type, const long long* lcell, int n_list, const int* offsets, int* lsub, int* lwall,
                    int* lbc, cudaStream_t);
 void geo_count_kinds(const uint8_t* type, long long N, unsigned long long* out, cudaStream_t);
-// mixed 32-cell x-segments (a cell that is not plain FLUID, not all solid): per-block counts (blocks of
-// 256 segments), then the ascending segment indices at the block offsets
-long long geo_segments(const GeoArgs&);
-int geo_segment_blocks(const GeoArgs&);
-void geo_segment_count(const GeoArgs&, const uint8_t* type, int* counts, cudaStream_t);
-void geo_segment_write(const GeoArgs&, const uint8_t* type, const int* offsets, int* list, cudaStream_t);
 // 64-cell x-groups and the groups mixing plain pairs with per-cell pairs (nx even): out[0], out[1]
 void geo_pair_mix(const GeoArgs&, const uint8_t* type, unsigned long long* out, cudaStream_t);
 // source map (debug): for each (i, n): source population and cell, -1 for solid cells
