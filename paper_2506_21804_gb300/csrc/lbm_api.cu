@@ -470,7 +470,7 @@ void launch_step(lbm_ctx* c, cudaEvent_t before_bulk = nullptr, cudaEvent_t afte
   c->ops->step_bulk(a, odd, c->stream);
   ++c->launches;
   if (after_bulk) cudaEventRecord(after_bulk, c->stream);
-  if ((a.inline_all ? a.n_bc : (a.lsub ? a.n_sub : a.n_list)) > 0) {
+  if (!a.inline_all && (a.lsub ? a.n_sub : a.n_list) > 0) {
     c->ops->step_list(a, odd, c->stream);
     ++c->launches;
   }

@@ -171,9 +171,7 @@ struct Args {
   int fuse;                // 1: list cells flagged T_INLINE are updated by the interior kernel; the
                            //    boundary-list kernel then runs over the other entries only
   int inline_all;          // fused mode with the BGK collision: the interior kernel updates every list
-                           //    cell except INFLOW/OUTFLOW cells, which the boundary-list kernel
-                           //    updates over the sub-list lbc (their reconstruction would stall the
-                           //    row-end warps)
+                           //    cell (no boundary-list kernel)
   const int* lidx;         // list position of every cell (-1 off the list)
   const int* lsub;         // list positions handled by the boundary-list kernel (fused mode)
   int n_sub;

@@ -118,14 +118,9 @@ struct Impl {
     if (odd) k_bulk<Q, S, true><<<bulk_grid(a), bulk_block(a), 0, s>>>(a);
     else k_bulk<Q, S, false><<<bulk_grid(a), bulk_block(a), 0, s>>>(a);
   }
-  static void step_list(const Args& a0, int odd, cudaStream_t s) {
-    Args a = a0;
-    if (a.inline_all) {  // only the INFLOW/OUTFLOW entries are left for this kernel
-      a.lsub = a.lbc;
-      a.n_sub = a.n_bc;
-    }
+  static void step_list(const Args& a, int odd, cudaStream_t s) {
     const int nj = a.lsub ? a.n_sub : a.n_list;
-    if (nj <= 0) return;
+    if (nj <= 0 || a.inline_all) return;
     if (a.model != 0) {
       if (odd) k_list<Q, S, true, true><<<blocks_for(nj, LIST_THREADS), LIST_THREADS, 0, s>>>(a);
       else k_list<Q, S, false, true><<<blocks_for(nj, LIST_THREADS), LIST_THREADS, 0, s>>>(a);

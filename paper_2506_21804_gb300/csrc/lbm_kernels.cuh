@@ -390,12 +390,9 @@ template <int Q, class S, bool ODD, bool HRR = false>
 __device__ __forceinline__ void bulk_cell(const Args& a, S* f, int x, int y, int z, long long n, uint8_t t) {
   using C = typename Codec<S>::C;
   if (t & (T_LIST | T_KIND)) {
-    // list cells updated here (T_INLINE, or with inline_all every list cell but INFLOW/OUTFLOW);
-    // solid cells and the list cells of the boundary-list kernel are skipped
-    const int kind = t & T_KIND;
-    const bool bc = kind == K_INFLOW || kind == K_OUTFLOW;
-    if ((t & T_LIST) && a.fuse && (a.inline_all ? !bc : (t & T_INLINE) != 0))
-      list_cell_inline<Q, S, ODD, HRR>(a, f, x, y, z, n, t);
+    // list cells updated here (T_INLINE, or every list cell when inline_all); solid cells and the
+    // list cells of the boundary-list kernel are skipped
+    if ((t & T_LIST) && a.fuse && ((t & T_INLINE) || a.inline_all)) list_cell_inline<Q, S, ODD, HRR>(a, f, x, y, z, n, t);
     return;
   }
   const bool near = (t & T_NEAR) != 0;
@@ -414,17 +411,16 @@ __device__ __forceinline__ void bulk_cell(const Args& a, S* f, int x, int y, int
   if (!finite_all<C>(rho, urx, ury, urz)) atomicOr(a.status, ST_NAN);
   scatter<Q, S, ODD ? STORE_SLOTS : STORE_MIRROR>(a, f, x, y, z, n, near, h);
 }
-// Mixed path of the BGK interior kernel (fused mode, every list cell but the inlet/outlet cells
-// inline): one instruction stream for FLUID and WALL cells. Even steps gather and scatter the cell's
-// own slots whatever its kind; odd steps use per-lane slot codes (0 for plain cells, the list entry's
-// codes for list cells, the general rule for other cells next to a face), so lanes of different kinds
-// only diverge in the wall-state load and the general slot rule.
+// Mixed path of the BGK interior kernel (fused mode, every list cell inline): one instruction stream
+// for every non-solid kind. Even steps gather and scatter the cell's own slots whatever its kind; odd
+// steps use per-lane slot codes (0 for plain cells, the list entry's codes for list cells, the
+// general rule for other cells next to a face), so lanes of different kinds only diverge in the
+// inlet/outlet reconstruction, the wall-state load and the general slot rule.
 template <int Q, class S, bool ODD>
 __device__ __forceinline__ void mixed_cell(const Args& a, S* f, int x, int y, int z, long long n, uint8_t t) {
   using C = typename Codec<S>::C;
   const int kind = t & T_KIND;
-  // solid cells do nothing; INFLOW/OUTFLOW cells belong to the boundary-list kernel
-  if (kind == K_SOLID || kind == K_INFLOW || kind == K_OUTFLOW) return;
+  if (kind == K_SOLID) return;
   const bool list = (t & T_LIST) != 0;
   const int k = list ? a.lidx[n] : -1;
   C h[Q];
@@ -435,6 +431,7 @@ __device__ __forceinline__ void mixed_cell(const Args& a, S* f, int x, int y, in
   } else {
     gather<Q, S, LOAD_LOCAL>(a, f, x, y, z, n, false, h);
   }
+  if (kind == K_INFLOW || kind == K_OUTFLOW) apply_bc<Q, C>(a, kind, y, z, h);
   const C* ws = (kind == K_WALL && a.wm) ? cptr<C>(a.wst) + (long long)WALL_STATE * k : nullptr;
   C rho, urx, ury, urz;
   collide_unified<Q, C>(h, gamma_at<C>(a, n), a, ws, rho, urx, ury, urz);
