@@ -166,6 +166,10 @@ struct Oracle {
   uint64_t vm_seed = 0;
   std::vector<double> uin_cur;  // inlet velocity of the current (last) step, 3 * ny * nz
   // outlet fringe zone (Sec. 3.2); off when fr_L == 0
+  // sub-domain of a z-slab decomposition: the first gh_lo and last gh_hi z-planes are ghost planes
+  // (cells owned by the neighbouring sub-domains): classified like every cell, never collided or
+  // streamed, filled by the halo exchange
+  int gh_lo = 0, gh_hi = 0;
   int fr_L = 0;
   int fr_x0 = 0;  // first plane of the layer (nx - L for the whole domain; any value for a crop)
   double fr_smax = 0.0, fr_p = 2.0;
@@ -913,14 +917,22 @@ void vm_reset(Oracle& o) {
   if (o.uin_cur.empty()) o.uin_cur.assign(3L * o.ny * o.nz, 0.0);
 }
 
-// One time step: collide every non-solid cell of F into P, record the reference velocities, then
-// pull-stream P into F through the source map.
-void step_once(Oracle& o) {
+inline bool is_ghost(const Oracle& o, long n) {
+  if (o.gh_lo == 0 && o.gh_hi == 0) return false;
+  const long z = n / (long(o.nx) * o.ny);
+  return z < o.gh_lo || z >= o.nz - o.gh_hi;
+}
+
+// One time step in two phases. Collide: every non-solid cell of F into P, recording the reference
+// velocities. Stream: pull P into F through the source map. Between the two, a sub-domain of a slab
+// decomposition receives the post-collision populations of its ghost cells that stream into it and
+// the reference velocities its wall cells read next step (the halo exchange).
+void step_collide(Oracle& o) {
   const Lat& L = o.L;
   if (o.vm_n > 0) vm_update(o, o.t);
 #pragma omp parallel for schedule(static)
   for (long n = 0; n < o.N; ++n) {
-    if (o.kind[n] == K_SOLID) {
+    if (o.kind[n] == K_SOLID || is_ghost(o, n)) {
       for (int i = 0; i < L.Q; ++i) o.P[long(i) * o.N + n] = 0.0;
       continue;
     }
@@ -933,10 +945,14 @@ void step_once(Oracle& o) {
       for (int a = 0; a < 3; ++a) o.uref_cur[3 * n + a] = urep[a];
     for (int a = 0; a < 3; ++a) o.uvel_cur[long(a) * o.N + n] = urep[a];
   }
+}
+
+void step_stream(Oracle& o) {
+  const Lat& L = o.L;
 #pragma omp parallel for schedule(static)
   for (long n = 0; n < o.N; ++n) {
     for (int i = 0; i < L.Q; ++i) {
-      if (o.kind[n] == K_SOLID) { o.Fn[long(i) * o.N + n] = 0.0; continue; }
+      if (o.kind[n] == K_SOLID || is_ghost(o, n)) { o.Fn[long(i) * o.N + n] = 0.0; continue; }
       int j; long m;
       source(o, n, i, j, m);
       o.Fn[long(i) * o.N + n] = o.P[long(j) * o.N + m];
@@ -947,6 +963,55 @@ void step_once(Oracle& o) {
   o.uref_prev = o.uref_cur;
   o.uvel_prev = o.uvel_cur;
   ++o.t;
+}
+
+void step_once(Oracle& o) {
+  step_collide(o);
+  step_stream(o);
+}
+
+// Halo lists of one side of a sub-domain (side 0: the z- cut, side 1: the z+ cut). With zr the real
+// boundary plane and zg the adjacent ghost plane, and an entry (p, pos) meaning population slot p of
+// the plane cell at pos = x + nx y (the population opp(p) in transit, stored as in the in-place
+// scheme's slot p):
+//   list 0: (p, pos) of the non-solid cells of zr, c_p pointing into the sub-domain: the
+//           post-collision populations opp(p) that leave through the cut;
+//   list 1: (p, pos) of the non-solid cells of zg, c_p pointing out: the populations opp(p) of the
+//           neighbour that stream in;
+//   list 2: pos of the cells of zr that a WALL cell of zg takes as reference cell;
+//   list 3: pos of the cells of zg that a WALL cell of zr takes as reference cell.
+// Entries run over pos ascending, then p ascending. The neighbour's list 1 (resp. 3) on the other
+// side of the same cut equals this list 0 (resp. 2).
+std::vector<long> halo_list(const Oracle& o, int side, int list) {
+  std::vector<long> out;
+  const long nxy = long(o.nx) * o.ny;
+  const int zr = side == 0 ? o.gh_lo : o.nz - o.gh_hi - 1;
+  const int zg = side == 0 ? o.gh_lo - 1 : o.nz - o.gh_hi;
+  const int inward = side == 0 ? 1 : -1;
+  if ((side == 0 ? o.gh_lo : o.gh_hi) == 0) return out;
+  if (list == 0 || list == 1) {
+    const int z = list == 0 ? zr : zg;
+    const int want = list == 0 ? inward : -inward;
+    for (long pos = 0; pos < nxy; ++pos) {
+      const long n = pos + nxy * z;
+      if (o.kind[n] == K_SOLID) continue;
+      for (int p = 0; p < o.L.Q; ++p)
+        if (o.L.c[p][2] == want) out.push_back(long(p) * nxy + pos);
+    }
+    return out;
+  }
+  const int zw = list == 2 ? zg : zr;  // plane of the wall cells
+  const int zt = list == 2 ? zr : zg;  // plane of their reference cells
+  std::vector<uint8_t> hit(nxy, 0);
+  for (long pos = 0; pos < nxy; ++pos) {
+    const long w = pos + nxy * zw;
+    if (o.kind[w] != K_WALL || o.refcell[w] < 0) continue;
+    const long r = o.refcell[w];
+    if (r / nxy == zt) hit[r - nxy * zt] = 1;
+  }
+  for (long pos = 0; pos < nxy; ++pos)
+    if (hit[pos]) out.push_back(pos);
+  return out;
 }
 
 // ---- 16-bit codecs written from the IEEE 754 binary16 and the bfloat16 definitions ------------
@@ -1289,6 +1354,58 @@ void orc_step(void* h, int n) {
   for (int k = 0; k < n; ++k) step_once(o);
 }
 
+// Slab sub-domain: the first lo and last hi z-planes are ghost planes (0 or 2 each).
+int orc_set_ghost(void* h, int lo, int hi) {
+  Oracle& o = *static_cast<Oracle*>(h);
+  if (!(lo == 0 || lo == 2) || !(hi == 0 || hi == 2) || lo + hi >= o.nz) {
+    g_err = "ghost planes: 0 or 2 per side, fewer than nz in total";
+    return 1;
+  }
+  o.gh_lo = lo;
+  o.gh_hi = hi;
+  return 0;
+}
+void orc_step_collide(void* h) { step_collide(*static_cast<Oracle*>(h)); }
+void orc_step_stream(void* h) { step_stream(*static_cast<Oracle*>(h)); }
+long long orc_halo_count(void* h, int side, int list) {
+  return (long long)halo_list(*static_cast<Oracle*>(h), side, list).size();
+}
+void orc_halo_list(void* h, int side, int list, long long* out) {
+  const std::vector<long> v = halo_list(*static_cast<Oracle*>(h), side, list);
+  for (size_t k = 0; k < v.size(); ++k) out[k] = v[k];
+}
+// After the collide phase: list 0 packs the leaving post-collision populations, list 2 the
+// reference velocities of this step; unpack of list 1 / list 3 stores the neighbour's into the ghost
+// plane (populations into P, velocities into the reference buffer read by the next step).
+void orc_halo_pack(void* h, int side, int list, double* buf) {
+  Oracle& o = *static_cast<Oracle*>(h);
+  const long nxy = long(o.nx) * o.ny;
+  const int zr = side == 0 ? o.gh_lo : o.nz - o.gh_hi - 1;
+  const std::vector<long> v = halo_list(o, side, list);
+  for (size_t k = 0; k < v.size(); ++k) {
+    if (list == 0) {
+      const long p = v[k] / nxy, pos = v[k] % nxy;
+      buf[k] = o.P[long(o.L.opp[p]) * o.N + pos + nxy * zr];
+    } else {
+      for (int a = 0; a < 3; ++a) buf[3 * k + a] = o.uref_cur[3 * (v[k] + nxy * zr) + a];
+    }
+  }
+}
+void orc_halo_unpack(void* h, int side, int list, const double* buf) {
+  Oracle& o = *static_cast<Oracle*>(h);
+  const long nxy = long(o.nx) * o.ny;
+  const int zg = side == 0 ? o.gh_lo - 1 : o.nz - o.gh_hi;
+  const std::vector<long> v = halo_list(o, side, list);
+  for (size_t k = 0; k < v.size(); ++k) {
+    if (list == 1) {
+      const long p = v[k] / nxy, pos = v[k] % nxy;
+      o.P[long(o.L.opp[p]) * o.N + pos + nxy * zg] = buf[k];
+    } else {
+      for (int a = 0; a < 3; ++a) o.uref_cur[3 * (v[k] + nxy * zg) + a] = buf[3 * k + a];
+    }
+  }
+}
+
 void orc_moments(void* h, double* rho, double* u) {
   Oracle& o = *static_cast<Oracle*>(h);
   moments_of(o, o.F, rho, u);
@@ -1301,7 +1418,7 @@ void orc_reduce(void* h, double* mass, double* mom) {
   moments_of(o, o.F, rho.data(), u.data());
   double m = 0, p[3] = {0, 0, 0};
   for (long n = 0; n < o.N; ++n) {
-    if (o.kind[n] == K_SOLID) continue;
+    if (o.kind[n] == K_SOLID || is_ghost(o, n)) continue;
     m += rho[n];
     for (int a = 0; a < 3; ++a) p[a] += rho[n] * u[a * o.N + n];
   }

@@ -88,6 +88,13 @@ def lib():
             "orc_objective_run": (_i, [_p, _i, _i, _i, _i, _p]),
             "orc_adjoint": (_i, [_p, _p, _p]),
             "orc_set_threads": (None, [_i]),
+            "orc_set_ghost": (_i, [_p, _i, _i]),
+            "orc_step_collide": (None, [_p]),
+            "orc_step_stream": (None, [_p]),
+            "orc_halo_count": (ctypes.c_longlong, [_p, _i, _i]),
+            "orc_halo_list": (None, [_p, _i, _i, _p]),
+            "orc_halo_pack": (None, [_p, _i, _i, _p]),
+            "orc_halo_unpack": (None, [_p, _i, _i, _p]),
             "orc_get_threads": (_i, []),
         }
         for name, (res, args) in sig.items():
@@ -364,6 +371,33 @@ class Oracle:
 
     def step(self, n=1):
         lib().orc_step(self.h, int(n))
+
+    # ---- slab sub-domain (z decomposition) -------------------------------------------------------
+    def set_ghost(self, lo, hi):
+        """First lo and last hi z-planes are ghost planes (0 or 2 each)."""
+        self._chk(lib().orc_set_ghost(self.h, int(lo), int(hi)))
+
+    def step_collide(self):
+        lib().orc_step_collide(self.h)
+
+    def step_stream(self):
+        lib().orc_step_stream(self.h)
+
+    def halo_list(self, side, which):
+        n = lib().orc_halo_count(self.h, int(side), int(which))
+        out = np.zeros(max(n, 1), np.int64)
+        lib().orc_halo_list(self.h, int(side), int(which), _ptr(out))
+        return out[:n]
+
+    def halo_pack(self, side, which):
+        n = lib().orc_halo_count(self.h, int(side), int(which))
+        buf = np.zeros(max(n, 1) * (1 if which == 0 else 3))
+        lib().orc_halo_pack(self.h, int(side), int(which), _ptr(buf))
+        return buf[: n * (1 if which == 0 else 3)]
+
+    def halo_unpack(self, side, which, buf):
+        b = _f64(np.asarray(buf).reshape(-1))
+        lib().orc_halo_unpack(self.h, int(side), int(which), _ptr(b))
 
     def moments(self):
         rho = np.zeros(self.N)

@@ -263,3 +263,47 @@ def random_box(nx, ny, nz, seed, q=19, solid_frac=0.1, tau=0.7, cs=0.1, faces=(0
     ywall = 0.3 + 0.4 * uniform(seed, 26, idx)
     return Workload(name=f"random{nx}x{ny}x{nz}", q=q, nx=nx, ny=ny, nz=nz, tau=tau, cs=cs, faces=tuple(faces),
                     mask=mask, ywall=ywall, uin=uin, rho_out=1.0, rho0=rho, u0=u)
+
+
+GHOST = 2  # ghost planes per cut of a z-slab decomposition
+
+
+def slab(w, parts, k):
+    """Sub-domain k of a decomposition of workload w into `parts` z-slabs (layout only, no LB
+    arithmetic). Slab k owns the planes [z0, z1), z0 = k nz // parts; every side that is a cut (both
+    sides when z is periodic and parts > 1, else the inner ones) gets GHOST extra planes holding the
+    neighbour's mask, wall distance, porosity, inlet velocity and initial state, with the z face of the
+    sub-domain beyond them a bounce-back wall (it only shapes the classification of the outer ghost
+    plane). Returns (workload, z0, z1, lo, hi), lo/hi the ghost planes below/above."""
+    import dataclasses
+    nz = w.nz
+    z0, z1 = k * nz // parts, (k + 1) * nz // parts
+    if z1 - z0 < GHOST:
+        raise ValueError("every slab needs at least %d planes" % GHOST)
+    periodic = w.faces[4] == FACE_PERIODIC
+    if parts == 1:
+        return w, 0, nz, 0, 0
+    lo = GHOST if (periodic or k > 0) else 0
+    hi = GHOST if (periodic or k < parts - 1) else 0
+    zs = np.arange(z0 - lo, z1 + hi) % nz
+    nxy = w.nx * w.ny
+    cells = (zs[:, None] * nxy + np.arange(nxy)[None, :]).reshape(-1)
+    faces = list(w.faces)
+    faces[4] = FACE_WALL if lo else w.faces[4]
+    faces[5] = FACE_WALL if hi else w.faces[5]
+    if faces[4] == FACE_PERIODIC and faces[5] != FACE_PERIODIC:
+        faces[4] = FACE_WALL
+    if faces[5] == FACE_PERIODIC and faces[4] != FACE_PERIODIC:
+        faces[5] = FACE_WALL
+
+    def cut(a):
+        return None if a is None else np.asarray(a)[..., cells].copy()
+
+    uin = None
+    if w.uin is not None:
+        cols = (zs[:, None] * w.ny + np.arange(w.ny)[None, :]).reshape(-1)
+        uin = np.asarray(w.uin)[:, cols].copy()
+    sub = dataclasses.replace(w, name=f"{w.name}_slab{k}of{parts}", nz=len(zs), faces=tuple(faces),
+                              mask=cut(w.mask), ywall=cut(w.ywall), gamma=cut(w.gamma), uin=uin,
+                              rho0=cut(w.rho0), u0=cut(w.u0), meta=dict(w.meta, slab=(k, parts, z0, z1, lo, hi)))
+    return sub, z0, z1, lo, hi
