@@ -116,6 +116,35 @@ int lbm_set_outflow(lbm_ctx* ctx, double rho_out);
  * L = 0 switches it off. The adjoint calls return LBM_ESTATE while it is on. Errors: LBM_EINVAL for L
  * outside [0, nx], s_max outside [0, 1] or p < 0. Device memory: nx compute-type values. */
 int lbm_set_fringe(lbm_ctx* ctx, int L, double s_max, double p);
+/* Slab sub-domain of a z decomposition (the paper's domain decomposition, Sec. 3.1, cut along the
+ * slowest axis). The first lo and last hi z-planes (0 or 2 each) are ghost planes: they hold the
+ * neighbouring sub-domains' cells (their mask, wall distance, porosity, inlet velocity and initial
+ * state, passed like every other cell), are classified like every cell and are never updated. The
+ * real cells then step exactly as in the whole domain provided the caller runs the halo exchange
+ * below around every step. Rebuilds the geometry and resets the state to rest. The BGK collision
+ * with a steady inlet only (LBM_ESTATE for LBM_HRR, the vortex inlet and the adjoint calls).
+ * Errors: LBM_EINVAL for lo or hi not 0 or 2, or lo + hi >= nz. */
+int lbm_set_ghost_planes(lbm_ctx* ctx, int lo, int hi);
+/* Halo lists of side 0 (the z- cut) and side 1 (the z+ cut). With zr the real boundary plane and zg
+ * the adjacent ghost plane, entries run over the plane positions pos = x + nx*y ascending, then the
+ * population slots p ascending:
+ *   list 0: slots p of the non-solid cells of zr with c_p pointing into the sub-domain;
+ *   list 1: slots p of the non-solid cells of zg with c_p pointing out of it;
+ *   list 2: the zr cells that a WALL cell of zg takes as wall-model reference cell;
+ *   list 3: the zg cells that a WALL cell of zr takes as reference cell.
+ * Populations travel as stored (storage type, deviations f - w, one value per entry), reference
+ * velocities as 3 compute-type values per entry. The neighbour's list 1 (3) on the other side of the
+ * same cut equals this list 0 (2) entry by entry. Exchange schedule (in-place streaming: even steps
+ * touch only a cell's own slots), for both sides:
+ *   before a step that starts at an odd step count: pack list 0, send it; unpack the neighbour's into
+ *   list 1; after that step: pack list 1, send it; unpack the neighbour's into list 0;
+ *   after every step: pack list 2, send it; unpack the neighbour's into list 3.
+ * lbm_halo_count gives the number of entries; pack (lists 0, 1, 2) and unpack (lists 0, 1, 3) take a
+ * host or device buffer of the context's device (device buffers: ordered on the context stream;
+ * host buffers: the call synchronises). The lists are also readable through lbm_debug_dump. */
+int lbm_halo_count(lbm_ctx* ctx, int side, int list, int64_t* n);
+int lbm_halo_pack(lbm_ctx* ctx, int side, int list, void* buf);
+int lbm_halo_unpack(lbm_ctx* ctx, int side, int list, const void* buf);
 /* Per-cell porosity gamma (N values in [0,1], 1 = fluid); NULL removes it. */
 int lbm_set_porosity(lbm_ctx* ctx, const float* gamma);
 int lbm_set_porosity_ex(lbm_ctx* ctx, const void* gamma, int dtype);
@@ -227,13 +256,16 @@ int lbm_interior_kernel(lbm_ctx* ctx);
  * and velocity-field kernels when those forms are on. */
 int lbm_launch_count(lbm_ctx* ctx, int64_t* n);
 /* Integer maps for bit-exact tests: which = 0 type byte per cell (N; bits 0-2 kind, bit 3
- * reference cell, bit 4 a source position is solid or outside, bit 5 boundary list, bit 6 list cell
+ * reference cell, bit 4 a source position is solid or outside, bit 5 boundary list, bit 7 ghost
+ * plane of a slab sub-domain, bit 6 list cell
  * updated by the interior kernel: INFLOW/OUTFLOW cells, and WALL/reference cells in 32-cell
  * x-groups holding >= 8 list cells);
  * 1 boundary-list cells; 2 list position of each entry's reference cell (-1 none);
  * 3 integer wall-normal sums v of each entry (3 per entry, sum of W_i c_i over solid neighbours,
  * W_i = 36 w_i for D3Q19 and 216 w_i for D3Q27); 4 source population j and 5 source cell m of each
- * (i, n) (q*N each, i-major; f_i(n, t+1) = f*_j(m, t); -1 for solid cells). */
+ * (i, n) (q*N each, i-major; f_i(n, t+1) = f*_j(m, t); -1 for solid cells); 6..13 the halo list
+ * (which - 6) % 4 of side (which - 6) / 4 of a slab sub-domain (lbm_halo_count entries: p*nx*ny + pos
+ * for lists 0 and 1, pos for lists 2 and 3). */
 int lbm_debug_dump(lbm_ctx* ctx, int which, int64_t* out, size_t count);
 
 /* Allocation-free reduction (no counterpart in the paper: an addition for callers of this library).

@@ -101,6 +101,12 @@ struct lbm_ctx {
   DevBuf uvel0, uvel1;  // HRR velocity fields (step t reads uvel[t & 1], writes the other)
   DevBuf uin_a, uin_b, vort, vpart;  // vortex inlet: current/previous inlet fields, vortex list, partial fields
   DevBuf fringe;  // outlet fringe zone: strength per x-plane (compute type)
+  // slab sub-domain: ghost z-planes below/above, and per side (z-, z+) and halo list (0 real-plane
+  // slots, 1 ghost-plane slots, 2 reference cells sent, 3 reference cells received) the device
+  // offsets of the entries and their canonical form (slot * nx * ny + plane position, or position)
+  int gh_lo = 0, gh_hi = 0;
+  DevBuf halo_off[2][4];
+  std::vector<int64_t> halo_map[2][4];
   int fr_L = 0;
   double fr_smax = 0.0, fr_p = 2.0;
   DevBuf geo_counts, geo_sub, geo_kinds;  // geometry set-up scratch (per-block counts, kind counters)
@@ -123,6 +129,8 @@ struct lbm_ctx {
   double adj_ms[3] = {0, 0, 0};
 
   ~lbm_ctx() {
+    for (auto& side : halo_off)
+      for (auto& b : side) b.release();
     DevBuf* all[] = {&fringe, &geo_counts, &geo_sub, &geo_kinds, &uin_a, &uin_b, &vort, &vpart, &uvel0, &uvel1, &lidx, &lsub, &lwall, &lbc, &wst, &f, &type, &mask, &wdist, &gamma, &uin, &lcell, &nsum, &wref, &lxyz, &lcode, &wnrm, &wyw, &ref0, &ref1, &status, &red,
                      &redout, &stage, &lamA, &lamB, &dgam, &duin, &plane};
     for (DevBuf* b : all) b->release();
@@ -152,6 +160,8 @@ GeoArgs geo_args(const lbm_ctx* c) {
   g.N = c->N;
   for (int i = 0; i < 6; ++i) g.face[i] = c->face[i];
   g.q = c->q;
+  g.gh_lo = c->gh_lo;
+  g.gh_hi = c->gh_hi;
   return g;
 }
 
@@ -221,6 +231,7 @@ Args make_args(const lbm_ctx* c) {
   a.uvel_wr = (c->t & 1) ? c->uvel0.p : c->uvel1.p;
   a.pairs = pairs_selected(c) ? 1 : 0;
   a.fringe = c->fr_L > 0 ? c->fringe.p : nullptr;
+  a.ghost = (c->gh_lo > 0 || c->gh_hi > 0) ? 1 : 0;
   a.fr_x0 = c->nx - c->fr_L;
   return a;
 }
@@ -292,6 +303,8 @@ int upload_uin(lbm_ctx* c) {
   CK(cudaStreamSynchronize(c->stream));
   return LBM_OK;
 }
+
+int build_halo(lbm_ctx* c);
 
 // Classification and boundary list from the device mask; list auxiliary data in compute type.
 int build_geometry(lbm_ctx* c) {
@@ -404,6 +417,7 @@ int build_geometry(lbm_ctx* c) {
     }
   }
   c->type_host_valid = false;
+  if (c->gh_lo > 0 || c->gh_hi > 0) return build_halo(c);
   return LBM_OK;
 }
 
@@ -416,6 +430,84 @@ const std::vector<uint8_t>& host_types(lbm_ctx* c) {
     c->type_host_valid = true;
   }
   return c->type_host;
+}
+
+// Halo lists of a slab sub-domain (the z decomposition of Sec. 3.1), per side s (0: z-, 1: z+), with
+// zr the real boundary plane and zg the adjacent ghost plane, entries over the plane positions
+// pos = x + nx y ascending, then slots p ascending:
+//   0: slots (p, zr cell) of non-solid cells with c_p pointing into the sub-domain. After an even step
+//      they hold the post-collision populations opp(p) that leave through the cut; after an odd step
+//      the neighbour's populations that arrived there.
+//   1: slots (p, zg cell) of non-solid cells with c_p pointing out: the neighbour's leaving populations
+//      (before an odd step), then the ones this sub-domain sent into them (after it).
+//   2: zr cells that a WALL cell of zg takes as reference cell; 3: zg cells that a WALL cell of zr
+//      takes as reference cell (their wall-model reference velocities cross the cut).
+// The neighbour's list 1 (3) on the other side of the same cut is this list 0 (2), entry by entry.
+int build_halo(lbm_ctx* c) {
+  const std::vector<uint8_t>& th = host_types(c);
+  const long long nxy = (long long)c->nx * c->ny;
+  std::vector<long long> lcell(std::max(1, c->n_list));
+  std::vector<int> wref(std::max(1, c->n_list));
+  if (c->n_list > 0) {
+    CK(cudaMemcpy(lcell.data(), c->lcell.p, sizeof(long long) * c->n_list, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(wref.data(), c->wref.p, sizeof(int) * c->n_list, cudaMemcpyDeviceToHost));
+  }
+  for (int side = 0; side < 2; ++side) {
+    const int g = side == 0 ? c->gh_lo : c->gh_hi;
+    const long long zr = side == 0 ? c->gh_lo : c->nz - c->gh_hi - 1;
+    const long long zg = side == 0 ? c->gh_lo - 1 : c->nz - c->gh_hi;
+    const int inward = side == 0 ? 1 : -1;
+    std::vector<int64_t> map[4], off[4];
+    if (g > 0) {
+      for (int lst = 0; lst < 2; ++lst) {
+        const long long z = lst == 0 ? zr : zg;
+        const int want = lst == 0 ? inward : -inward;
+        for (long long pos = 0; pos < nxy; ++pos) {
+          const long long n = pos + nxy * z;
+          if ((th[n] & T_KIND) == K_SOLID) continue;
+          for (int p = 0; p < c->q; ++p) {
+            const int cz = c->q == 19 ? Lat<19>::cz(p) : Lat<27>::cz(p);
+            if (cz != want) continue;
+            map[lst].push_back((int64_t)p * nxy + pos);
+            off[lst].push_back((int64_t)p * c->stride + n);
+          }
+        }
+      }
+      // list positions of the cells of the two planes, and the reference relations across the cut
+      std::vector<int> kpos_r(nxy, -1), kpos_g(nxy, -1);
+      std::vector<uint8_t> hit2(nxy, 0), hit3(nxy, 0);
+      for (int k = 0; k < c->n_list; ++k) {
+        const long long n = lcell[k], z = n / nxy;
+        if (z == zr) kpos_r[n - nxy * zr] = k;
+        if (z == zg) kpos_g[n - nxy * zg] = k;
+      }
+      for (int k = 0; k < c->n_list; ++k) {
+        const long long w = lcell[k], z = w / nxy;
+        if ((th[w] & T_KIND) != K_WALL || wref[k] < 0) continue;
+        const long long r = lcell[wref[k]], zr_ = r / nxy;
+        if (z == zg && zr_ == zr) hit2[r - nxy * zr] = 1;
+        if (z == zr && zr_ == zg) hit3[r - nxy * zg] = 1;
+      }
+      for (long long pos = 0; pos < nxy; ++pos) {
+        if (hit2[pos]) {
+          map[2].push_back(pos);
+          off[2].push_back(3 * (int64_t)kpos_r[pos]);
+        }
+        if (hit3[pos]) {
+          map[3].push_back(pos);
+          off[3].push_back(3 * (int64_t)kpos_g[pos]);
+        }
+      }
+    }
+    for (int lst = 0; lst < 4; ++lst) {
+      c->halo_map[side][lst] = map[lst];
+      CK(c->halo_off[side][lst].ensure(std::max<size_t>(1, off[lst].size()) * sizeof(int64_t)));
+      if (!off[lst].empty())
+        CK(cudaMemcpy(c->halo_off[side][lst].p, off[lst].data(), off[lst].size() * sizeof(int64_t),
+                      cudaMemcpyHostToDevice));
+    }
+  }
+  return LBM_OK;
 }
 
 // One time step: in fused mode the wall-model states of the WALL entries first, then the interior
@@ -741,6 +833,90 @@ int lbm_set_fringe(lbm_ctx* c, int L, double s_max, double p) {
   return LBM_OK;
 }
 
+int lbm_set_ghost_planes(lbm_ctx* c, int lo, int hi) {
+  if (!c) return fail(LBM_EINVAL, "null context");
+  if (!(lo == 0 || lo == 2) || !(hi == 0 || hi == 2) || lo + hi >= c->nz)
+    return fail(LBM_EINVAL, "ghost planes: 0 or 2 per side and fewer than nz = %d in total", c->nz);
+  if ((lo || hi) && (c->model != LBM_BGK || c->vm_n > 0))
+    return fail(LBM_ESTATE, "slab sub-domains run the BGK collision with a steady inlet");
+  CK(cudaStreamSynchronize(c->stream));
+  c->gh_lo = lo;
+  c->gh_hi = hi;
+  int rc;
+  if ((rc = build_geometry(c)) != LBM_OK) return rc;
+  return reset_state(c);
+}
+
+// element bytes and width of a halo list entry, and the array it lives in
+static int halo_target(lbm_ctx* c, int side, int list, bool pack, void** base, int* width, int* elem, long long* n) {
+  if (side < 0 || side > 1 || list < 0 || list > 3) return fail(LBM_EINVAL, "side must be 0 or 1, list 0..3");
+  if (pack && list == 3) return fail(LBM_EINVAL, "list 3 (reference cells received) is unpacked only");
+  if (!pack && list == 2) return fail(LBM_EINVAL, "list 2 (reference cells sent) is packed only");
+  *n = (long long)c->halo_map[side][list].size();
+  if (list <= 1) {
+    *base = c->f.p;
+    *width = 1;
+    *elem = c->ops->elem;
+  } else {
+    // the reference buffer the last step wrote, which the next step reads
+    *base = const_cast<void*>(make_args(c).ref_rd);
+    *width = 3;
+    *elem = c->ops->celem;
+  }
+  return LBM_OK;
+}
+
+int lbm_halo_count(lbm_ctx* c, int side, int list, int64_t* n) {
+  if (!c || !n) return fail(LBM_EINVAL, "null argument");
+  if (side < 0 || side > 1 || list < 0 || list > 3) return fail(LBM_EINVAL, "side must be 0 or 1, list 0..3");
+  *n = (int64_t)c->halo_map[side][list].size();
+  return LBM_OK;
+}
+
+int lbm_halo_pack(lbm_ctx* c, int side, int list, void* buf) {
+  if (!c) return fail(LBM_EINVAL, "null context");
+  void* base;
+  int width, elem, rc;
+  long long n;
+  if ((rc = halo_target(c, side, list, true, &base, &width, &elem, &n)) != LBM_OK) return rc;
+  if (n == 0) return LBM_OK;
+  if ((rc = check_ptr(c, buf, "buf")) != LBM_OK) return rc;
+  const size_t bytes = (size_t)n * width * elem;
+  const long long* off = static_cast<const long long*>(c->halo_off[side][list].p);
+  if (is_device_ptr(buf, c->device)) {
+    halo_copy(true, base, off, n, width, elem, buf, c->stream);
+  } else {
+    CK(c->stage.ensure(bytes));
+    halo_copy(true, base, off, n, width, elem, c->stage.p, c->stream);
+    CK(cudaMemcpyAsync(buf, c->stage.p, bytes, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  CK(cudaGetLastError());
+  return LBM_OK;
+}
+
+int lbm_halo_unpack(lbm_ctx* c, int side, int list, const void* buf) {
+  if (!c) return fail(LBM_EINVAL, "null context");
+  void* base;
+  int width, elem, rc;
+  long long n;
+  if ((rc = halo_target(c, side, list, false, &base, &width, &elem, &n)) != LBM_OK) return rc;
+  if (n == 0) return LBM_OK;
+  if ((rc = check_ptr(c, buf, "buf")) != LBM_OK) return rc;
+  const size_t bytes = (size_t)n * width * elem;
+  const long long* off = static_cast<const long long*>(c->halo_off[side][list].p);
+  if (is_device_ptr(buf, c->device)) {
+    halo_copy(false, base, off, n, width, elem, const_cast<void*>(buf), c->stream);
+  } else {
+    CK(c->stage.ensure(bytes));
+    CK(cudaMemcpyAsync(c->stage.p, buf, bytes, cudaMemcpyHostToDevice, c->stream));
+    halo_copy(false, base, off, n, width, elem, c->stage.p, c->stream);
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  CK(cudaGetLastError());
+  return LBM_OK;
+}
+
 int lbm_set_porosity_ex(lbm_ctx* c, const void* gamma, int dtype) {
   if (!c) return fail(LBM_EINVAL, "null context");
   if (!gamma) {
@@ -983,7 +1159,9 @@ int lbm_debug_dump(lbm_ctx* c, int which, int64_t* out, size_t count) {
     case 1: case 2: need = c->n_list; break;
     case 3: need = 3 * (size_t)c->n_list; break;
     case 4: case 5: need = (size_t)c->q * c->N; break;
-    default: return fail(LBM_EINVAL, "which must be 0..5");
+    default:
+      if (which < 6 || which > 13) return fail(LBM_EINVAL, "which must be 0..13");
+      need = c->halo_map[(which - 6) / 4][(which - 6) % 4].size();
   }
   if (count < need) return fail(LBM_EINVAL, "output holds %zu values, %zu needed", count, need);
   if (which == 0) {
@@ -995,6 +1173,11 @@ int lbm_debug_dump(lbm_ctx* c, int which, int64_t* out, size_t count) {
     std::vector<long long> v(need);
     if (need) CK(cudaMemcpy(v.data(), c->lcell.p, need * sizeof(long long), cudaMemcpyDeviceToHost));
     for (size_t i = 0; i < need; ++i) out[i] = v[i];
+    return LBM_OK;
+  }
+  if (which >= 6) {
+    const std::vector<int64_t>& m = c->halo_map[(which - 6) / 4][(which - 6) % 4];
+    for (size_t i = 0; i < need; ++i) out[i] = m[i];
     return LBM_OK;
   }
   if (which == 2 || which == 3) {
@@ -1096,6 +1279,7 @@ int lbm_set_vortex_inlet(lbm_ctx* c, int n, double sigma, double intensity, unsi
   if (n < 0 || n > (1 << 20)) return fail(LBM_EINVAL, "n must lie in [0, 2^20]");
   if (!(sigma > 0.0) || !std::isfinite(sigma)) return fail(LBM_EINVAL, "sigma must be > 0");
   if (!(intensity >= 0.0) || !std::isfinite(intensity)) return fail(LBM_EINVAL, "intensity must be >= 0");
+  if (n > 0 && (c->gh_lo || c->gh_hi)) return fail(LBM_ESTATE, "slab sub-domains run with a steady inlet");
   c->vm_n = n; c->vm_sigma = sigma; c->vm_I = intensity; c->vm_seed = seed;
   if (n == 0) {
     c->uin_a.release(); c->uin_b.release(); c->vort.release(); c->vpart.release();
@@ -1111,6 +1295,7 @@ int lbm_set_vortex_inlet(lbm_ctx* c, int n, double sigma, double intensity, unsi
 int lbm_set_collision(lbm_ctx* c, int model, double sigma) {
   if (!c) return fail(LBM_EINVAL, "null context");
   if (model != LBM_BGK && model != LBM_HRR) return fail(LBM_EINVAL, "model must be LBM_BGK or LBM_HRR");
+  if (model != LBM_BGK && (c->gh_lo || c->gh_hi)) return fail(LBM_ESTATE, "slab sub-domains run the BGK collision");
   if (!(sigma >= 0.0 && sigma <= 1.0)) return fail(LBM_EINVAL, "sigma must lie in [0, 1]");
   c->model = model;
   c->sigma = sigma;
@@ -1126,6 +1311,7 @@ int lbm_set_collision(lbm_ctx* c, int model, double sigma) {
 static int adj_check(lbm_ctx* c, int xa, int xb, double* wa, double* wb, int W) {
   if (c->model != LBM_BGK) return fail(LBM_ESTATE, "the adjoint is defined for the BGK collision only");
   if (c->fr_L > 0) return fail(LBM_ESTATE, "the adjoint is defined without the outlet fringe zone");
+  if (c->gh_lo || c->gh_hi) return fail(LBM_ESTATE, "the adjoint is defined on a whole domain, not a slab sub-domain");
   if (c->vm_n > 0) return fail(LBM_ESTATE, "the adjoint is defined for a steady inlet only");
   if (c->wm) return fail(LBM_ESTATE, "the wall model is not differentiated; switch it off (kappa <= 0)");
   if (xa < 0 || xa >= c->nx || xb < 0 || xb >= c->nx || xa == xb) return fail(LBM_EINVAL, "objective planes out of range");
@@ -1196,6 +1382,7 @@ int lbm_objective_backward(lbm_ctx* c, double* dJ_dgamma, double* dJ_duin) {
   if (!c) return fail(LBM_EINVAL, "null context");
   if (c->adj_t0 != c->t) return fail(LBM_ESTATE, "no forward run to differentiate (run lbm_objective_forward first)");
   if (c->fr_L > 0) return fail(LBM_ESTATE, "the adjoint is defined without the outlet fringe zone");
+  if (c->gh_lo || c->gh_hi) return fail(LBM_ESTATE, "the adjoint is defined on a whole domain, not a slab sub-domain");
   if (c->model != LBM_BGK) return fail(LBM_ESTATE, "the adjoint is defined for the BGK collision only");
   if (c->vm_n > 0) return fail(LBM_ESTATE, "the adjoint is defined for a steady inlet only");
   if (c->wm) return fail(LBM_ESTATE, "the wall model is not differentiated");
@@ -1283,6 +1470,7 @@ int lbm_adjoint_step(lbm_ctx* c, const void* lam_in, void* lam_out, int dtype, d
   if (c->wm) return fail(LBM_ESTATE, "the wall model is not differentiated");
   if (c->t & 1) return fail(LBM_ESTATE, "the reverse step needs the state after an even number of steps");
   if (c->fr_L > 0) return fail(LBM_ESTATE, "the adjoint is defined without the outlet fringe zone");
+  if (c->gh_lo || c->gh_hi) return fail(LBM_ESTATE, "the adjoint is defined on a whole domain, not a slab sub-domain");
   int rc;
   if ((rc = check_ptr(c, lam_in, "lam_in")) != LBM_OK) return rc;
   if ((rc = check_ptr(c, lam_out, "lam_out")) != LBM_OK) return rc;

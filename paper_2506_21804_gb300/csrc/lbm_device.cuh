@@ -26,6 +26,7 @@ constexpr uint8_t T_REF = 8;     // wall-model reference cell (writes its veloci
 constexpr uint8_t T_NEAR = 16;   // some source position is solid or outside the domain
 constexpr uint8_t T_LIST = 32;   // on the boundary list
 constexpr uint8_t T_INLINE = 64; // list cell updated inside the interior kernel (fused mode)
+constexpr uint8_t T_GHOST = 128; // ghost plane of a slab sub-domain: classified, never updated
 enum { K_FLUID = 0, K_SOLID = 1, K_WALL = 2, K_INFLOW = 3, K_OUTFLOW = 4 };
 enum { F_PERIODIC = 0, F_WALL = 1, F_SLIP = 2, F_OPEN = 3 };
 constexpr unsigned ST_NAN = 1u, ST_BADMASK = 2u;
@@ -194,6 +195,7 @@ struct Args {
   // outlet fringe zone: strength s(x) per x-plane (compute type, nx values; 0 before the layer) or null
   const void* fringe;
   int fr_x0;               // first plane of the layer
+  int ghost;               // slab sub-domain with ghost planes (cells flagged T_GHOST are skipped)
 };
 
 // ---- AA-pattern slot map ------------------------------------------------------------------------------

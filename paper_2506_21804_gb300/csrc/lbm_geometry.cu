@@ -108,7 +108,7 @@ __global__ void k_classify(const GeoArgs g, const uint8_t* mask, uint8_t* type, 
     atomicOr(status, ST_BADMASK);
     m = 0;
   }
-  if (m == 1) { type[n] = K_SOLID; return; }
+  if (m == 1) { type[n] = K_SOLID | ((z < g.gh_lo || z >= g.nz - g.gh_hi) ? T_GHOST : 0); return; }
   bool wall = false, near = false;
   sfor<1, Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
@@ -123,7 +123,8 @@ __global__ void k_classify(const GeoArgs g, const uint8_t* mask, uint8_t* type, 
     }
   });
   uint8_t kind = m == 3 ? K_INFLOW : m == 4 ? K_OUTFLOW : (wall ? K_WALL : K_FLUID);
-  type[n] = kind | (near ? T_NEAR : 0);
+  const bool ghost = z < g.gh_lo || z >= g.nz - g.gh_hi;
+  type[n] = kind | (near ? T_NEAR : 0) | (ghost ? T_GHOST : 0);
 }
 
 template <int Q>
@@ -473,6 +474,26 @@ void geo_count_kinds(const uint8_t* type, long long N, unsigned long long* out, 
 void geo_list_index(const long long* lcell, int n_list, int* lidx, cudaStream_t s) {
   if (n_list <= 0) return;
   k_list_index<<<nblocks(n_list, 256), 256, 0, s>>>(lcell, n_list, lidx);
+}
+
+template <class T>
+__global__ void k_halo_copy(bool gather, T* base, const long long* __restrict__ off, long long n, int width, T* buf) {
+  const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const long long o = off[j];
+  for (int c = 0; c < width; ++c) {
+    if (gather) buf[j * width + c] = base[o + c];
+    else base[o + c] = buf[j * width + c];
+  }
+}
+
+void halo_copy(bool gather, void* base, const long long* off, long long n, int width, int elem, void* buf,
+               cudaStream_t s) {
+  if (n <= 0) return;
+  const unsigned g = nblocks(n, 256);
+  if (elem == 2) k_halo_copy<uint16_t><<<g, 256, 0, s>>>(gather, static_cast<uint16_t*>(base), off, n, width, static_cast<uint16_t*>(buf));
+  else if (elem == 4) k_halo_copy<uint32_t><<<g, 256, 0, s>>>(gather, static_cast<uint32_t*>(base), off, n, width, static_cast<uint32_t*>(buf));
+  else k_halo_copy<unsigned long long><<<g, 256, 0, s>>>(gather, static_cast<unsigned long long*>(base), off, n, width, static_cast<unsigned long long*>(buf));
 }
 
 void reduce_final(const double* partial, int nblk, double* out, cudaStream_t s) {

@@ -27,7 +27,8 @@ struct Impl {
   // Shared-memory layout of the staged kernel, or stages = 0 when the shape does not allow it.
   static TmaLayout tma_layout(const Args& a) {
     TmaLayout L{};
-    if (a.kernel != 2 || a.nx % TMA_W != 0 || sizeof(S) == 8) return L;  // FP64 (reference form) stays plain
+    // FP64 (reference form) and slab sub-domains (ghost planes) stay with the plain kernel
+    if (a.kernel != 2 || a.nx % TMA_W != 0 || sizeof(S) == 8 || a.ghost) return L;
     L.pop_bytes = unsigned(TMA_W * sizeof(S));
     L.type_off = unsigned(Q) * L.pop_bytes;
     unsigned end = L.type_off + unsigned(TMA_W);

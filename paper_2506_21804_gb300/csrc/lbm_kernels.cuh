@@ -382,17 +382,32 @@ __device__ __forceinline__ void list_cell_inline(const Args& a, S* f, int x, int
 // Occupancy target (CTAs of 128 threads per SM): D3Q19 10 on even steps (<= 51 registers) and 8 on
 // odd steps (<= 64), D3Q27 8 and 6; the register cap falls on the rarely taken list-cell path. The
 // FP64 (reference) form is left unconstrained.
+#ifndef LBM_BULK_MINB19_EVEN
+#define LBM_BULK_MINB19_EVEN 10
+#endif
+#ifndef LBM_BULK_MINB19_ODD
+#define LBM_BULK_MINB19_ODD 8
+#endif
+#ifndef LBM_BULK_MINB27_EVEN
+#define LBM_BULK_MINB27_EVEN 8
+#endif
+#ifndef LBM_BULK_MINB27_ODD
+#define LBM_BULK_MINB27_ODD 6
+#endif
 template <int Q, class S, bool ODD> constexpr int bulk_min_blocks() {
-  return sizeof(S) == 8 ? 1 : (Q == 19 ? (ODD ? 8 : 10) : (ODD ? 6 : 8));
+  return sizeof(S) == 8 ? 1
+                        : (Q == 19 ? (ODD ? LBM_BULK_MINB19_ODD : LBM_BULK_MINB19_EVEN)
+                                   : (ODD ? LBM_BULK_MINB27_ODD : LBM_BULK_MINB27_EVEN));
 }
 
 template <int Q, class S, bool ODD, bool HRR = false>
 __device__ __forceinline__ void bulk_cell(const Args& a, S* f, int x, int y, int z, long long n, uint8_t t) {
   using C = typename Codec<S>::C;
-  if (t & (T_LIST | T_KIND)) {
-    // list cells updated here (T_INLINE, or every list cell when inline_all); solid cells and the
-    // list cells of the boundary-list kernel are skipped
-    if ((t & T_LIST) && a.fuse && ((t & T_INLINE) || a.inline_all)) list_cell_inline<Q, S, ODD, HRR>(a, f, x, y, z, n, t);
+  if (t & (T_LIST | T_KIND | T_GHOST)) {
+    // list cells updated here (T_INLINE, or every list cell when inline_all); solid cells, ghost
+    // cells and the list cells of the boundary-list kernel are skipped
+    if ((t & (T_LIST | T_GHOST)) == T_LIST && a.fuse && ((t & T_INLINE) || a.inline_all))
+      list_cell_inline<Q, S, ODD, HRR>(a, f, x, y, z, n, t);
     return;
   }
   const bool near = (t & T_NEAR) != 0;
@@ -420,7 +435,7 @@ template <int Q, class S, bool ODD>
 __device__ __forceinline__ void mixed_cell(const Args& a, S* f, int x, int y, int z, long long n, uint8_t t) {
   using C = typename Codec<S>::C;
   const int kind = t & T_KIND;
-  if (kind == K_SOLID) return;
+  if (kind == K_SOLID || (t & T_GHOST)) return;
   const bool list = (t & T_LIST) != 0;
   const int k = list ? a.lidx[n] : -1;
   C h[Q];
@@ -819,6 +834,7 @@ __global__ void __launch_bounds__(LIST_THREADS) k_list(const Args a) {
   const long long n = a.lcell[k];
   const int x = a.lxyz[3 * k], y = a.lxyz[3 * k + 1], z = a.lxyz[3 * k + 2];
   const uint8_t t = a.type[n];
+  if (t & T_GHOST) return;  // a neighbouring sub-domain's cell
   const int kind = t & T_KIND;
   S* f = static_cast<S*>(a.f);
   C h[Q];
@@ -915,7 +931,7 @@ __global__ void k_moments(const Args a, int swapped, void* rho, void* u, int dty
   using C = typename Codec<S>::C;
   const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (n >= a.N) return;
-  if ((a.type[n] & T_KIND) == K_SOLID) {
+  if ((a.type[n] & T_KIND) == K_SOLID || (a.type[n] & T_GHOST)) {
     if (rho) store_out(rho, dtype, n, 0.0);
     for (int c = 0; c < 3; ++c) store_out(u, dtype, c * a.N + n, 0.0);
     return;
@@ -931,7 +947,7 @@ __global__ void k_get_pops(const Args a, int swapped, void* out, int dtype) {
   using C = typename Codec<S>::C;
   const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (n >= a.N) return;
-  if ((a.type[n] & T_KIND) == K_SOLID) {
+  if ((a.type[n] & T_KIND) == K_SOLID || (a.type[n] & T_GHOST)) {
     sfor<0, Q>([&](auto I) { store_out(out, dtype, (long long)I * a.N + n, 0.0); });
     return;
   }
@@ -992,7 +1008,7 @@ __global__ void __launch_bounds__(256) k_reduce(const Args a, int swapped, doubl
   using C = typename Codec<S>::C;
   double s[4] = {0, 0, 0, 0};
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < a.N; n += (long long)gridDim.x * blockDim.x) {
-    if ((a.type[n] & T_KIND) == K_SOLID) continue;
+    if ((a.type[n] & T_KIND) == K_SOLID || (a.type[n] & T_GHOST)) continue;
     C r, u[3];
     cell_macro<Q, S>(a, n, swapped != 0, r, u);
     const double rd = double(r);

@@ -48,6 +48,7 @@ struct GeoArgs {
   long long nxy, N;
   int face[6];
   int q;
+  int gh_lo, gh_hi;  // ghost z-planes below and above (slab sub-domain), flagged T_GHOST
 };
 void geo_classify(const GeoArgs&, const uint8_t* mask, uint8_t* type, unsigned* status, cudaStream_t);
 // smallest index of an invalid mask code (first_bad = ~0 when every code is valid)
@@ -74,6 +75,10 @@ void geo_count_kinds(const uint8_t* type, long long N, unsigned long long* out, 
 void geo_pair_mix(const GeoArgs&, const uint8_t* type, unsigned long long* out, cudaStream_t);
 // source map (debug): for each (i, n): source population and cell, -1 for solid cells
 void geo_source_map(const GeoArgs&, const uint8_t* type, int64_t* src_dir, int64_t* src_cell, cudaStream_t);
+// halo copies of a slab sub-domain: gather (buf[j*width + c] = base[off[j] + c]) or scatter (the
+// reverse) of n entries of width values of elem bytes (2, 4 or 8; raw bits)
+void halo_copy(bool gather, void* base, const long long* off, long long n, int width, int elem, void* buf,
+               cudaStream_t);
 // FP64 final reduction of nblk partials (4 doubles each) into out[4], fixed order
 void reduce_final(const double* partial, int nblk, double* out, cudaStream_t);
 }  // namespace lbm

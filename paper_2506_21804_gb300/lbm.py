@@ -83,6 +83,10 @@ SIGNATURES = {
     "lbm_reduce_static": (_i, [_i, _p, _i, _p, ctypes.c_int64, _p, _p]),
     "lbm_launch_count": (_i, [_p, _p]),
     "lbm_set_fringe": (_i, [_p, _i, _d, _d]),
+    "lbm_set_ghost_planes": (_i, [_p, _i, _i]),
+    "lbm_halo_count": (_i, [_p, _i, _i, _p]),
+    "lbm_halo_pack": (_i, [_p, _i, _i, _p]),
+    "lbm_halo_unpack": (_i, [_p, _i, _i, _p]),
     "lbm_reduce_static_error": (ctypes.c_char_p, []),
     "lbm_debug_dump": (_i, [_p, _i, _p, ctypes.c_size_t]),
 }
@@ -198,6 +202,25 @@ class Lattice:
         """Outlet fringe zone over the last L planes (L = 0: off), strength s_max xi^p."""
         _check(lib().lbm_set_fringe(self.h, int(L), float(s_max), float(p)))
 
+    def set_ghost_planes(self, lo, hi):
+        """Slab sub-domain: the first lo and last hi z-planes (0 or 2) are ghost planes."""
+        _check(lib().lbm_set_ghost_planes(self.h, int(lo), int(hi)))
+
+    def halo_count(self, side, which):
+        n = np.zeros(1, np.int64)
+        _check(lib().lbm_halo_count(self.h, int(side), int(which), n.ctypes.data_as(_p)))
+        return int(n[0])
+
+    def halo_pack(self, side, which, buf):
+        """Pack halo list `which` of `side` into buf (a torch tensor or numpy array of the right size)."""
+        ptr = ctypes.c_void_p(buf.data_ptr()) if _is_torch(buf) else buf.ctypes.data_as(_p)
+        _check(lib().lbm_halo_pack(self.h, int(side), int(which), ptr))
+        return buf
+
+    def halo_unpack(self, side, which, buf):
+        ptr = ctypes.c_void_p(buf.data_ptr()) if _is_torch(buf) else np.ascontiguousarray(buf).ctypes.data_as(_p)
+        _check(lib().lbm_halo_unpack(self.h, int(side), int(which), ptr))
+
     def set_porosity(self, gamma):
         if gamma is None:
             _check(lib().lbm_set_porosity_ex(self.h, None, DTYPE_F32))
@@ -297,8 +320,11 @@ class Lattice:
 
     def debug_dump(self, which):
         info = self.info()
-        count = {0: self.N, 1: info["n_list"], 2: info["n_list"], 3: 3 * info["n_list"],
-                 4: self.q * self.N, 5: self.q * self.N}[which]
+        if which >= 6:
+            count = self.halo_count((which - 6) // 4, (which - 6) % 4)
+        else:
+            count = {0: self.N, 1: info["n_list"], 2: info["n_list"], 3: 3 * info["n_list"],
+                     4: self.q * self.N, 5: self.q * self.N}[which]
         out = np.zeros(max(count, 1), np.int64)
         _check(lib().lbm_debug_dump(self.h, int(which), out.ctypes.data_as(_p), ctypes.c_size_t(out.size)))
         return out[:count]
@@ -353,11 +379,14 @@ class Lattice:
 
     # ---- convenience ---------------------------------------------------------------------------------------------
     @classmethod
-    def from_workload(cls, w, storage=F32, init=True):
+    def from_workload(cls, w, storage=F32, init=True, ghost=(0, 0)):
         """Lattice configured from a seeded `inputs.Workload` (faces, geometry, force, inlet,
-        outlet, porosity, wall model, initial equilibrium)."""
+        outlet, porosity, wall model, initial equilibrium); ghost = (lo, hi) ghost z-planes of a slab
+        sub-domain (inputs.slab)."""
         lat = cls(w.q, w.nx, w.ny, w.nz, w.tau, w.cs, storage=storage)
         lat.set_faces(w.faces)
+        if ghost != (0, 0):
+            lat.set_ghost_planes(*ghost)
         lat.set_geometry(w.mask, None if w.ywall is None else np.asarray(w.ywall, np.float32))
         lat.set_force(*w.force)
         if w.uin is not None:
