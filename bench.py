@@ -12,7 +12,8 @@ region, and secondary forms (16-bit storage with its error, D3Q27 and D3Q19 urba
 adjoint on the 128^3 duct).
 
 `--impl reference` times the CPU oracle (the reference arm of this build) on a bounded slab of the
-same workload. Multi-GPU: independent replicas (one per rank, weak scaling), max time over ranks.
+same workload. Multi-GPU (N > 1): the channel 256 x 256 x (256 N) in N z-slabs, one per rank, with the
+halo exchange of every step between neighbouring ranks (weak scaling), max time over ranks.
 """
 import argparse
 import hashlib
@@ -332,6 +333,56 @@ def secondary(lbm, I, torch):
     return out
 
 
+def run_sharded(args, rank, world):
+    """N > 1: the channel 256 x 256 x (256 N) split into N z-slabs of 256 planes, one per rank, with
+    the halo exchange of every step between neighbouring ranks (torch.distributed point-to-point
+    messages of device buffers; weak scaling: per-rank work fixed). Time = max over ranks of the
+    CUDA-event time of K steps including the exchanges."""
+    import torch
+    from paper_2506_21804_gb300 import inputs as I, lbm
+    from paper_2506_21804_gb300.shard import RankSlab
+    w = I.channel(nx=256, ny=256, nz=256 * world, seed=550, dtype=np.float32)
+    sl = RankSlab(w, rank, world, storage=lbm.F32)
+    sl.step(args.warmup)
+    sl.sync()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clk = ClockSampler(torch.cuda.current_device())
+    clk.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    l0 = sl.lat.launch_count()
+    e0.record(stream)
+    sl.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = clk.stop()
+    launches = (sl.lat.launch_count() - l0)
+    t_ms = max_over_ranks(e0.elapsed_time(e1), world)
+    cells = w.N  # all ranks' real cells
+    value = cells * args.steps / (t_ms * 1e-3) / 1e9
+    peak, peak_src = peaks()
+    per_rank = (sl.z1 - sl.z0) * w.nx * w.ny
+    step_bytes = per_rank * (2 * 19 * 4 + 1)
+    line = {
+        "metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD.replace("256x256x256", f"256x256x{256 * world}") + f", {world} z-slabs",
+                   "cells": cells, "parallelism": f"z-slabs x{world} (halo exchange every step)",
+                   "l2": "state > 129 MB L2 between steps, no flush needed"},
+        "step_roofline": {"bytes_per_step_per_rank": step_bytes,
+                          "achieved_gbs": step_bytes / (t_ms / args.steps * 1e-3) / 1e9,
+                          "frac": step_bytes / (t_ms / args.steps * 1e-3) / 1e9 / peak, "peak_source": peak_src},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -366,6 +417,11 @@ def main():
     from paper_2506_21804_gb300 import build, inputs as I, lbm
     build.build()
     lbm.lib()
+    if world > 1 and args.workload == "channel":
+        run_sharded(args, rank, world)
+        import torch.distributed as dist
+        dist.destroy_process_group()
+        return
 
     if args.workload == "duct":
         n = (args.size or (128, 128, 128))[0]

@@ -128,8 +128,10 @@ int lbm_set_ghost_planes(lbm_ctx* ctx, int lo, int hi);
 /* Halo lists of side 0 (the z- cut) and side 1 (the z+ cut). With zr the real boundary plane and zg
  * the adjacent ghost plane, entries run over the plane positions pos = x + nx*y ascending, then the
  * population slots p ascending:
- *   list 0: slots p of the non-solid cells of zr with c_p pointing into the sub-domain;
- *   list 1: slots p of the non-solid cells of zg with c_p pointing out of it;
+ *   list 0: the slots of zr cells that non-solid cells of zg read and write in an odd step (their
+ *           streaming, bounce-back and slip rules): the post-collision populations opp(p) that leave
+ *           through the cut;
+ *   list 1: the slots of zg cells that non-solid cells of zr read and write in an odd step;
  *   list 2: the zr cells that a WALL cell of zg takes as wall-model reference cell;
  *   list 3: the zg cells that a WALL cell of zr takes as reference cell.
  * Populations travel as stored (storage type, deviations f - w, one value per entry), reference

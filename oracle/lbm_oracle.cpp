@@ -974,10 +974,9 @@ void step_once(Oracle& o) {
 // boundary plane and zg the adjacent ghost plane, and an entry (p, pos) meaning population slot p of
 // the plane cell at pos = x + nx y (the population opp(p) in transit, stored as in the in-place
 // scheme's slot p):
-//   list 0: (p, pos) of the non-solid cells of zr, c_p pointing into the sub-domain: the
-//           post-collision populations opp(p) that leave through the cut;
-//   list 1: (p, pos) of the non-solid cells of zg, c_p pointing out: the populations opp(p) of the
-//           neighbour that stream in;
+//   list 0: the post-collision populations of cells of zr that stream into non-solid cells of zg
+//           (the populations that leave through the cut);
+//   list 1: the populations of cells of zg that stream into non-solid cells of zr (they come in);
 //   list 2: pos of the cells of zr that a WALL cell of zg takes as reference cell;
 //   list 3: pos of the cells of zg that a WALL cell of zr takes as reference cell.
 // Entries run over pos ascending, then p ascending. The neighbour's list 1 (resp. 3) on the other
@@ -987,17 +986,25 @@ std::vector<long> halo_list(const Oracle& o, int side, int list) {
   const long nxy = long(o.nx) * o.ny;
   const int zr = side == 0 ? o.gh_lo : o.nz - o.gh_hi - 1;
   const int zg = side == 0 ? o.gh_lo - 1 : o.nz - o.gh_hi;
-  const int inward = side == 0 ? 1 : -1;
   if ((side == 0 ? o.gh_lo : o.gh_hi) == 0) return out;
   if (list == 0 || list == 1) {
-    const int z = list == 0 ? zr : zg;
-    const int want = list == 0 ? inward : -inward;
+    // the populations that cross: f_i(n, t+1) = f*_j(m, t) with n on one side of the cut and m on
+    // the other (streaming, bounce-back and slip rules of `source`), entered as (opp(j), pos(m))
+    const int zn = list == 0 ? zg : zr;  // receiving plane
+    const int zm = list == 0 ? zr : zg;  // plane of the sending cells
+    std::vector<std::pair<long, int>> e;
     for (long pos = 0; pos < nxy; ++pos) {
-      const long n = pos + nxy * z;
+      const long n = pos + nxy * zn;
       if (o.kind[n] == K_SOLID) continue;
-      for (int p = 0; p < o.L.Q; ++p)
-        if (o.L.c[p][2] == want) out.push_back(long(p) * nxy + pos);
+      for (int i = 0; i < o.L.Q; ++i) {
+        int j;
+        long m;
+        source(o, n, i, j, m);
+        if (m / nxy == zm) e.emplace_back(m - nxy * zm, o.L.opp[j]);
+      }
     }
+    std::sort(e.begin(), e.end());
+    for (const auto& v : e) out.push_back(long(v.second) * nxy + v.first);
     return out;
   }
   const int zw = list == 2 ? zg : zr;  // plane of the wall cells

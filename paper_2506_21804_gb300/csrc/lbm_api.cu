@@ -435,10 +435,11 @@ const std::vector<uint8_t>& host_types(lbm_ctx* c) {
 // Halo lists of a slab sub-domain (the z decomposition of Sec. 3.1), per side s (0: z-, 1: z+), with
 // zr the real boundary plane and zg the adjacent ghost plane, entries over the plane positions
 // pos = x + nx y ascending, then slots p ascending:
-//   0: slots (p, zr cell) of non-solid cells with c_p pointing into the sub-domain. After an even step
-//      they hold the post-collision populations opp(p) that leave through the cut; after an odd step
-//      the neighbour's populations that arrived there.
-//   1: slots (p, zg cell) of non-solid cells with c_p pointing out: the neighbour's leaving populations
+//   0: slots (p, zr cell) that the non-solid cells of zg use in an odd step (slot_of). After an even
+//      step they hold the post-collision populations opp(p) that leave through the cut; after an odd
+//      step the neighbour's populations that arrived there. A slot that a cell of zr uses itself
+//      (bounce-back from a solid cell across the cut) is not on the list.
+//   1: slots (p, zg cell) that the non-solid cells of zr use: the neighbour's leaving populations
 //      (before an odd step), then the ones this sub-domain sent into them (after it).
 //   2: zr cells that a WALL cell of zg takes as reference cell; 3: zg cells that a WALL cell of zr
 //      takes as reference cell (their wall-model reference velocities cross the cut).
@@ -456,23 +457,35 @@ int build_halo(lbm_ctx* c) {
     const int g = side == 0 ? c->gh_lo : c->gh_hi;
     const long long zr = side == 0 ? c->gh_lo : c->nz - c->gh_hi - 1;
     const long long zg = side == 0 ? c->gh_lo - 1 : c->nz - c->gh_hi;
-    const int inward = side == 0 ? 1 : -1;
     std::vector<int64_t> map[4], off[4];
     if (g > 0) {
+      // list 0: the slots of zr that the cells of zg use in an odd step; list 1: the slots of zg that
+      // the cells of zr use (the slot map of every cell, computed on the device for the two planes)
+      const GeoArgs ga = geo_args(c);
+      DevBuf sp, sm;
+      CK(sp.ensure((size_t)c->q * nxy * sizeof(int)));
+      CK(sm.ensure((size_t)c->q * nxy * sizeof(long long)));
+      std::vector<int> hp((size_t)c->q * nxy);
+      std::vector<long long> hm((size_t)c->q * nxy);
       for (int lst = 0; lst < 2; ++lst) {
-        const long long z = lst == 0 ? zr : zg;
-        const int want = lst == 0 ? inward : -inward;
-        for (long long pos = 0; pos < nxy; ++pos) {
-          const long long n = pos + nxy * z;
-          if ((th[n] & T_KIND) == K_SOLID) continue;
-          for (int p = 0; p < c->q; ++p) {
-            const int cz = c->q == 19 ? Lat<19>::cz(p) : Lat<27>::cz(p);
-            if (cz != want) continue;
-            map[lst].push_back((int64_t)p * nxy + pos);
-            off[lst].push_back((int64_t)p * c->stride + n);
-          }
+        const int zf = int(lst == 0 ? zg : zr), zt = int(lst == 0 ? zr : zg);
+        geo_plane_slots(ga, static_cast<const uint8_t*>(c->type.p), zf, zt, static_cast<int*>(sp.p),
+                        static_cast<long long*>(sm.p), c->stream);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(hp.data(), sp.p, hp.size() * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaMemcpyAsync(hm.data(), sm.p, hm.size() * sizeof(long long), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        std::vector<std::pair<long long, int>> e;  // (pos in the target plane, slot)
+        for (size_t k = 0; k < hp.size(); ++k)
+          if (hp[k] >= 0) e.emplace_back(hm[k] - nxy * zt, hp[k]);
+        std::sort(e.begin(), e.end());
+        for (const auto& v : e) {
+          map[lst].push_back((int64_t)v.second * nxy + v.first);
+          off[lst].push_back((int64_t)v.second * c->stride + v.first + nxy * zt);
         }
       }
+      sp.release();
+      sm.release();
       // list positions of the cells of the two planes, and the reference relations across the cut
       std::vector<int> kpos_r(nxy, -1), kpos_g(nxy, -1);
       std::vector<uint8_t> hit2(nxy, 0), hit3(nxy, 0);

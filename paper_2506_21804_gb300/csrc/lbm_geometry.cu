@@ -243,6 +243,29 @@ __global__ void k_source_map(const Args a, int64_t* sdir, int64_t* scell) {
   });
 }
 
+// Slots that the non-solid cells of plane z_from use in an odd step and that lie in plane z_to:
+// slot_of of every (cell, direction) of z_from, kept (p, m) when m is in z_to, else (-1, -1).
+// Outputs q * nx * ny values each, direction-major.
+template <int Q>
+__global__ void k_plane_slots(const Args a, int z_from, int z_to, int* sp, long long* sm) {
+  const long long pos = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (pos >= a.nxy) return;
+  const long long n = pos + a.nxy * z_from;
+  const bool solid = (a.type[n] & T_KIND) == K_SOLID;
+  const int x = int(pos % a.nx), y = int(pos / a.nx);
+  sfor<0, Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    int p = -1;
+    long long m = -1;
+    if (!solid) {
+      slot_of<Q>(a, x, y, z_from, n, i, p, m);
+      if (m / a.nxy != z_to) { p = -1; m = -1; }
+    }
+    sp[(long long)i * a.nxy + pos] = p;
+    sm[(long long)i * a.nxy + pos] = m;
+  });
+}
+
 // Inline (fused-mode) choice per 32-cell x-group of a row: INFLOW/OUTFLOW cells always; WALL and
 // reference cells when the group holds at least inline_min list cells. One thread per group.
 __global__ void k_inline_mark(const GeoArgs g, uint8_t* type, int inline_min) {
@@ -431,6 +454,17 @@ void geo_source_map(const GeoArgs& g, const uint8_t* type, int64_t* sdir, int64_
   for (int f = 0; f < 6; ++f) a.face[f] = g.face[f];
   if (g.q == 19) k_source_map<19><<<nblocks(g.N, 128), 128, 0, s>>>(a, sdir, scell);
   else k_source_map<27><<<nblocks(g.N, 128), 128, 0, s>>>(a, sdir, scell);
+}
+
+void geo_plane_slots(const GeoArgs& g, const uint8_t* type, int z_from, int z_to, int* sp, long long* sm,
+                     cudaStream_t s) {
+  Args a{};
+  a.type = type;
+  a.nx = g.nx; a.ny = g.ny; a.nz = g.nz;
+  a.nxy = g.nxy; a.N = g.N;
+  for (int f = 0; f < 6; ++f) a.face[f] = g.face[f];
+  if (g.q == 19) k_plane_slots<19><<<nblocks(g.nxy, 128), 128, 0, s>>>(a, z_from, z_to, sp, sm);
+  else k_plane_slots<27><<<nblocks(g.nxy, 128), 128, 0, s>>>(a, z_from, z_to, sp, sm);
 }
 
 void geo_inline_mark(const GeoArgs& g, uint8_t* type, int inline_min, cudaStream_t s) {

@@ -51,6 +51,10 @@ struct GeoArgs {
   int gh_lo, gh_hi;  // ghost z-planes below and above (slab sub-domain), flagged T_GHOST
 };
 void geo_classify(const GeoArgs&, const uint8_t* mask, uint8_t* type, unsigned* status, cudaStream_t);
+// odd-step slots (p, m) of the non-solid cells of plane z_from that lie in plane z_to ((-1, -1) else),
+// q * nx * ny entries each, direction-major
+void geo_plane_slots(const GeoArgs&, const uint8_t* type, int z_from, int z_to, int* sp, long long* sm,
+                     cudaStream_t);
 // smallest index of an invalid mask code (first_bad = ~0 when every code is valid)
 void geo_check_mask(const uint8_t* mask, long long N, unsigned long long* first_bad, cudaStream_t);
 void geo_mark_ref(const GeoArgs&, uint8_t* type, cudaStream_t);
