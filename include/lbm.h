@@ -141,6 +141,10 @@ int lbm_set_ghost_planes(lbm_ctx* ctx, int lo, int hi);
  *   before a step that starts at an odd step count: pack list 0, send it; unpack the neighbour's into
  *   list 1; after that step: pack list 1, send it; unpack the neighbour's into list 0;
  *   after every step: pack list 2, send it; unpack the neighbour's into list 3.
+ * After an odd number of steps the state is stored swapped (a cell's incoming populations sit in its
+ * neighbours' slots), so reading it (lbm_moments, lbm_get_populations, lbm_reduce) needs the ghost
+ * slots current: run the list 0 -> list 1 exchange of the coming odd step first (it need not be
+ * repeated before that step).
  * lbm_halo_count gives the number of entries; pack (lists 0, 1, 2) and unpack (lists 0, 1, 3) take a
  * host or device buffer of the context's device (device buffers: ordered on the context stream;
  * host buffers: the call synchronises). The lists are also readable through lbm_debug_dump. */

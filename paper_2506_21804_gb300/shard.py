@@ -29,14 +29,26 @@ def _buffers(lat, storage, side, which, device):
 
 
 class _SlabBase:
-    """The exchange schedule: before an odd step lists 0 -> 1, after it 1 -> 0, after every step 2 -> 3."""
+    """The exchange schedule: before an odd step lists 0 -> 1, after it 1 -> 0, after every step 2 -> 3.
+
+    After an even step the state is stored swapped: the incoming populations of a boundary cell sit in
+    its neighbours' slots, for the cells next to a cut in the ghost plane. Reading the state out then
+    needs the ghost slots current, i.e. the 0 -> 1 exchange of the coming odd step, done early
+    (`_ready`); the step does not repeat it."""
+
+    _fresh = False
+
+    def _ready(self):
+        if (self.t & 1) and not self._fresh:
+            self._exchange(0, 1)
+            self._fresh = True
 
     def _schedule(self, n):
         for _ in range(n):
             odd = self.t & 1
-            if odd:
-                self._exchange(0, 1)
+            self._ready()
             self._step_all()
+            self._fresh = False
             if odd:
                 self._exchange(1, 0)
             self._exchange(2, 3)
@@ -86,6 +98,7 @@ class LocalSlabs(_SlabBase):
 
     def populations(self, dtype=np.float64):
         """Populations of the whole domain (q, N) assembled from the real planes of every slab."""
+        self._ready()
         nxy = self.w.nx * self.w.ny
         parts = []
         for (sub, z0, z1, lo, hi), lat in zip(self.subs, self.lats):
@@ -93,6 +106,7 @@ class LocalSlabs(_SlabBase):
         return np.concatenate(parts, axis=1)
 
     def moments(self, dtype=np.float64):
+        self._ready()
         nxy = self.w.nx * self.w.ny
         rs, us = [], []
         for (sub, z0, z1, lo, hi), lat in zip(self.subs, self.lats):
@@ -102,6 +116,7 @@ class LocalSlabs(_SlabBase):
         return np.concatenate(rs), np.concatenate(us, axis=1)
 
     def reduce(self):
+        self._ready()
         m, p = 0.0, np.zeros(3)
         for lat in self.lats:
             mi, pi = lat.reduce()
