@@ -233,7 +233,7 @@ def adjoint_run(lbm, I, n, T, ckpt, W=None):
         res = {"cells": wd.N, "steps": T, "window": W, "checkpoint_interval": ckpt, "J": J,
                "forward_glups": cells / (fwd * 1e-3) / 1e9,
                "backward_glups": cells / ((rec + rev) * 1e-3) / 1e9,
-               "recompute_glups": cells / (rec * 1e-3) / 1e9,
+               "recompute_glups": cells / (rec * 1e-3) / 1e9 if rec > 0 else None,
                "reverse_kernel_glups": cells / (rev * 1e-3) / 1e9,
                "backward_over_forward": fwd / (rec + rev),
                "grad_l2": float(np.linalg.norm(g))}
@@ -330,6 +330,14 @@ def secondary(lbm, I, torch):
     adj = adjoint_run(lbm, I, 128, 1000, 32, W=100)
     adj["backward_over_channel_fp32_forward"] = adj["backward_glups"] / g32
     out["duct128_adjoint_T1000"] = adj
+    # the same with every state kept in HBM (1001 states, 160 GB): no recomputation in the backward
+    try:
+        adj1 = adjoint_run(lbm, I, 128, 1000, 1, W=100)
+        adj1["backward_over_channel_fp32_forward"] = adj1["backward_glups"] / g32
+        adj1["gradient_rel_diff_vs_checkpointed"] = abs(adj1["grad_l2"] - adj["grad_l2"]) / adj["grad_l2"]
+        out["duct128_adjoint_T1000_every_state"] = adj1
+    except Exception as e:  # reported, not hidden (e.g. not enough device memory)
+        out["duct128_adjoint_T1000_every_state"] = {"error": repr(e)}
     return out
 
 
@@ -425,7 +433,7 @@ def main():
 
     if args.workload == "duct":
         n = (args.size or (128, 128, 128))[0]
-        res = adjoint_run(lbm, I, n, max(args.steps, 2), 32 if args.steps >= 64 else 2)
+        res = adjoint_run(lbm, I, n, max(args.steps, 2) // 2 * 2, 1)
         print(json.dumps({"metric": "adjoint GLUPS (duct, checkpointed backward)", "value": res["backward_glups"],
                           "unit": "GLUPS", "config": {"workload": f"duct {n}^3 D3Q19 FP32 porosity"}, "adjoint": res}))
         return

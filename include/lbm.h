@@ -210,7 +210,10 @@ int lbm_set_populations(lbm_ctx* ctx, const void* f, int dtype);
  * plane means over non-solid cells of the state after each step.
  * lbm_objective_forward runs T steps from the current state, keeping a copy of the state every
  * ckpt steps (ckpt even), and returns J. lbm_objective_backward then recomputes each segment from
- * its checkpoint into a ring of states and sweeps the adjoint kernel backwards, accumulating
+ * its checkpoint into a ring of states and sweeps the adjoint kernel backwards. ckpt = 1 (T even)
+ * keeps every state instead, (T + 1) * q * N storage values in device memory (LBM_ENOMEM if they do
+ * not fit; they stay allocated until the next forward run or lbm_destroy): the forward steps out of
+ * place from each state into the next, and the backward is the reverse sweep alone. Both accumulate
  * dJ/dgamma and dJ/du_in over all T steps in FP64 device arrays (whatever the storage), and writes
  * them to dJ_dgamma (N doubles) and dJ_duin (3*ny*nz doubles), host memory or device memory of the
  * context's device; either may be NULL. The wall model is not differentiated (LBM_ESTATE if it is

@@ -122,6 +122,7 @@ struct lbm_ctx {
   double* red_h = nullptr;
   // adjoint state
   DevBuf lamA, lamB, dgam, duin, plane;
+  DevBuf hist;  // every state of the last forward run (checkpoint interval 1), T + 1 states
   std::vector<DevBuf> ckpts, ring;
   int adj_T = 0, adj_W = 0, adj_xa = 0, adj_xb = 0, adj_ck = 0;
   double adj_wa = 0, adj_wb = 0;
@@ -1347,11 +1348,60 @@ static int adj_check(lbm_ctx* c, int xa, int xb, double* wa, double* wb, int W) 
 int lbm_objective_forward(lbm_ctx* c, int T, int W, int xa, int xb, int ckpt, double* J) {
   if (!c || !J) return fail(LBM_EINVAL, "null argument");
   if (T < 1 || W < 1 || W > T) return fail(LBM_EINVAL, "need 1 <= W <= T");
-  if (ckpt < 2 || (ckpt & 1)) return fail(LBM_EINVAL, "checkpoint interval must be even and >= 2");
+  if (!(ckpt == 1 || (ckpt >= 2 && !(ckpt & 1))))
+    return fail(LBM_EINVAL, "checkpoint interval must be 1 (every state) or even and >= 2");
+  if (ckpt == 1 && (T & 1)) return fail(LBM_EINVAL, "keeping every state needs an even T");
   if (c->t & 1) return fail(LBM_ESTATE, "the forward run must start after an even number of steps");
   double wa, wb;
   int rc = adj_check(c, xa, xb, &wa, &wb, W);
   if (rc != LBM_OK) return rc;
+  if (ckpt == 1) {
+    // Every state kept in HBM (T + 1 states of q * stride values): the forward steps out of place
+    // from state s into state s + 1 (the same one read and one write per population as the in-place
+    // step), and the backward runs the reverse sweep alone, with no recomputation.
+    const size_t sb1 = (size_t)c->q * c->stride * c->ops->elem;
+    cudaError_t e = c->hist.ensure((size_t)(T + 1) * sb1);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      c->hist.release();
+      return fail(e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, "state history (%zu bytes): %s",
+                  (size_t)(T + 1) * sb1, cudaGetErrorString(e));
+    }
+    char* H = static_cast<char*>(c->hist.p);
+    CK(cudaMemsetAsync(c->redout.p, 0, sizeof(double), c->stream));
+    const size_t plane_blocks1 = (2 * (size_t)c->ny * c->nz + 255) / 256;
+    CK(c->plane.ensure(plane_blocks1 * sizeof(double)));
+    cudaEvent_t f0, f1;
+    CK(cudaEventCreate(&f0));
+    CK(cudaEventCreate(&f1));
+    CK(cudaEventRecord(f0, c->stream));
+    CK(cudaMemcpyAsync(H, c->f.p, sb1, cudaMemcpyDeviceToDevice, c->stream));  // even t: natural layout
+    const Args a = make_args(c);
+    for (int s1 = 0; s1 < T; ++s1) {
+      c->ops->step_oop(a, H + (size_t)s1 * sb1, H + (size_t)(s1 + 1) * sb1, c->stream);
+      ++c->launches;
+      if (s1 + 1 > T - W)
+        c->ops->plane_rho(a, H + (size_t)(s1 + 1) * sb1, 0, xa, xb, static_cast<double*>(c->redout.p),
+                          static_cast<double*>(c->plane.p), wa, wb, c->stream);
+    }
+    // T even: the final state in the natural layout is the in-place layout after an even count
+    CK(cudaMemcpyAsync(c->f.p, H + (size_t)T * sb1, sb1, cudaMemcpyDeviceToDevice, c->stream));
+    c->t += T;
+    CK(cudaEventRecord(f1, c->stream));
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(c->red_h, c->redout.p, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if ((rc = read_status(c)) != LBM_OK) return rc;
+    float fms = 0;
+    CK(cudaEventElapsedTime(&fms, f0, f1));
+    c->adj_ms[2] = fms;
+    cudaEventDestroy(f0);
+    cudaEventDestroy(f1);
+    *J = c->red_h[0];
+    c->adj_T = T; c->adj_W = W; c->adj_xa = xa; c->adj_xb = xb; c->adj_ck = 1;
+    c->adj_wa = wa; c->adj_wb = wb;
+    c->adj_t0 = c->t;
+    return status_code(c);
+  }
   const int nck = (T + ckpt - 1) / ckpt;
   const size_t sb = (size_t)c->q * c->stride * c->ops->elem;
   if ((int)c->ckpts.size() < nck) c->ckpts.resize(nck);
@@ -1403,12 +1453,14 @@ int lbm_objective_backward(lbm_ctx* c, double* dJ_dgamma, double* dJ_duin) {
   if (dJ_dgamma && (rc0 = check_ptr(c, dJ_dgamma, "dJ_dgamma")) != LBM_OK) return rc0;
   if (dJ_duin && (rc0 = check_ptr(c, dJ_duin, "dJ_duin")) != LBM_OK) return rc0;
   const int T = c->adj_T, W = c->adj_W, ck = c->adj_ck;
-  const int nck = (T + ck - 1) / ck;
+  const bool keep_all = ck == 1;  // every state kept by the forward run: one segment, no recomputation
+  const int seg_len = keep_all ? T : ck;
+  const int nck = (T + seg_len - 1) / seg_len;
   const size_t sb = (size_t)c->q * c->stride * c->ops->elem;
   const size_t lb = (size_t)c->q * c->stride * c->ops->celem;
   const size_t pl = 3 * (size_t)c->ny * c->nz;
-  if ((int)c->ring.size() < ck) c->ring.resize(ck);
-  for (int k = 1; k < ck; ++k) {
+  if (!keep_all && (int)c->ring.size() < ck) c->ring.resize(ck);
+  for (int k = 1; !keep_all && k < ck; ++k) {
     cudaError_t e = c->ring[k].ensure(sb);
     if (e != cudaSuccess) return fail(e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, "ring: %s", cudaGetErrorString(e));
   }
@@ -1429,14 +1481,18 @@ int lbm_objective_backward(lbm_ctx* c, double* dJ_dgamma, double* dJ_duin) {
   CK(cudaEventCreate(&e2));
   float rec_ms = 0, rev_ms = 0;
   for (int seg = nck - 1; seg >= 0; --seg) {
-    const int t0 = seg * ck;
-    const int L = std::min(T, t0 + ck) - t0;
+    const int t0 = seg * seg_len;
+    const int L = std::min(T, t0 + seg_len) - t0;
     std::vector<const void*> st(L);
-    st[0] = c->ckpts[seg].p;
     CK(cudaEventRecord(e0, s));
-    for (int j = 1; j < L; ++j) {
-      c->ops->step_oop(a, st[j - 1], c->ring[j].p, s);
-      st[j] = c->ring[j].p;
+    if (keep_all) {
+      for (int j = 0; j < L; ++j) st[j] = static_cast<const char*>(c->hist.p) + (size_t)j * sb;
+    } else {
+      st[0] = c->ckpts[seg].p;
+      for (int j = 1; j < L; ++j) {
+        c->ops->step_oop(a, st[j - 1], c->ring[j].p, s);
+        st[j] = c->ring[j].p;
+      }
     }
     CK(cudaEventRecord(e1, s));
     for (int j = L - 1; j >= 0; --j) {

@@ -286,20 +286,29 @@ def test_reverse_step_matches_oracle_transpose(storage, tol):
         assert np.abs(gu.reshape(-1) - ou).max() <= tol * max(np.abs(ou).max(), 1e-30), w.name
 
 
-def test_objective_gradient_fp64_matches_oracle():
+@pytest.mark.parametrize("ckpt", [4, 1])
+def test_objective_gradient_fp64_matches_oracle(ckpt):
+    """Checkpoints every 4 steps (segments recomputed) and every state kept (ckpt = 1, no
+    recomputation) give the oracle's objective and gradients."""
     w = I.duct(n=12, u_in=0.03, tau=0.7, sigma=2.0, cs=0.1, dtype=np.float64)
     T, W = 26, 6
     o = oracle_from(w)
     Jo = o.objective_run(T, W, 1, w.nx - 2)
     go, uo = o.adjoint()
     g = gpu_from(w, lbm.F64)
-    Jg = g.objective_forward(T, W, 1, w.nx - 2, ckpt=4)
+    Jg = g.objective_forward(T, W, 1, w.nx - 2, ckpt=ckpt)
     gg, ug = g.objective_backward()
     assert abs(Jg - Jo) < 1e-12 * max(1.0, abs(Jo))
     assert rel_l2(gg, go) < 1e-10
     assert rel_l2(ug, uo) < 1e-10
     # the state after backward is the one after the forward run
     assert g.info()["t"] == T
+    ro, _ = o.moments()
+    rg, _ = g.moments()
+    assert np.abs(rg - ro).max() < 1e-12
+    if ckpt == 1:
+        with pytest.raises(lbm.LBMError):
+            g.objective_forward(25, 5, 1, w.nx - 2, ckpt=1)  # odd T with every state kept
 
 
 def test_objective_gradient_fp32_32cube_vs_fp64_oracle():
