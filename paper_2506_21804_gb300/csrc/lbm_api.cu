@@ -1520,8 +1520,8 @@ int lbm_objective_backward(lbm_ctx* c, double* dJ_dgamma, double* dJ_duin) {
   cudaEventDestroy(e1);
   cudaEventDestroy(e2);
   CK(cudaGetLastError());
-  c->adj_ms[0] = rec_ms;
-  c->adj_ms[1] = rev_ms;
+  c->adj_ms[0] = keep_all ? 0.0 : rec_ms;  // nothing is recomputed when every state was kept
+  c->adj_ms[1] = keep_all ? rev_ms + rec_ms : rev_ms;
   // the FP64 accumulators go to the caller's arrays as they are (host or device memory)
   if (dJ_dgamma) CK(cudaMemcpyAsync(dJ_dgamma, c->dgam.p, (size_t)c->N * sizeof(double), cudaMemcpyDefault, s));
   if (dJ_duin) CK(cudaMemcpyAsync(dJ_duin, c->duin.p, pl * sizeof(double), cudaMemcpyDefault, s));
