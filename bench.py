@@ -475,16 +475,31 @@ def main():
     clk.start()
     time.sleep(0.3)
     runs = []
-    l0 = lat.launch_count()
+    timed_launches = 0
+    # The canopy with the wall function stays bounded for a few hundred steps from its impulsive
+    # start; between repeats its state is re-initialised (outside the timed region) before it would
+    # pass 300 steps. The channel runs on.
+    since = args.warmup
+    reinit_after = 300 if args.workload == "canopy" else None
+    n_init = 0
     for _ in range(n_rep):
+        if reinit_after is not None and since + args.steps > reinit_after:
+            lat.init_equilibrium(np.asarray(w.rho0, np.float32), np.asarray(w.u0, np.float32))
+            lat.step(args.warmup)
+            lat.sync()
+            since = args.warmup
+            n_init += 1
+        since += args.steps
         barrier(world)
         torch.cuda.synchronize()
+        l0 = lat.launch_count()
         m = lat.step_timed(args.steps)
+        timed_launches += lat.launch_count() - l0
         torch.cuda.synchronize()
         barrier(world)
         runs.append((max_over_ranks(m[2], world), m))
     clocks = clk.stop()
-    launches_per_region = (lat.launch_count() - l0) // n_rep
+    launches_per_region = timed_launches // n_rep
     runs.sort(key=lambda r: r[0])
     ms = runs[len(runs) // 2][1]
 
