@@ -97,7 +97,7 @@ struct lbm_ctx {
   unsigned status_seen = 0;
   // device buffers
   DevBuf f, type, mask, wdist, gamma, uin, lcell, nsum, wref, lxyz, lcode, wnrm, wyw, ref0, ref1, status, red, redout, stage;
-  DevBuf lidx, lsub, lwall, lbc, wst;
+  DevBuf lidx, lsub, lwall, lbc, wst, ccode;
   DevBuf uvel0, uvel1;  // HRR velocity fields (step t reads uvel[t & 1], writes the other)
   DevBuf uin_a, uin_b, vort, vpart;  // vortex inlet: current/previous inlet fields, vortex list, partial fields
   DevBuf fringe;  // outlet fringe zone: strength per x-plane (compute type)
@@ -132,7 +132,7 @@ struct lbm_ctx {
   ~lbm_ctx() {
     for (auto& side : halo_off)
       for (auto& b : side) b.release();
-    DevBuf* all[] = {&fringe, &geo_counts, &geo_sub, &geo_kinds, &uin_a, &uin_b, &vort, &vpart, &uvel0, &uvel1, &lidx, &lsub, &lwall, &lbc, &wst, &f, &type, &mask, &wdist, &gamma, &uin, &lcell, &nsum, &wref, &lxyz, &lcode, &wnrm, &wyw, &ref0, &ref1, &status, &red,
+    DevBuf* all[] = {&fringe, &geo_counts, &geo_sub, &geo_kinds, &uin_a, &uin_b, &vort, &vpart, &uvel0, &uvel1, &lidx, &lsub, &lwall, &lbc, &wst, &ccode, &f, &type, &mask, &wdist, &gamma, &uin, &lcell, &nsum, &wref, &lxyz, &lcode, &wnrm, &wyw, &ref0, &ref1, &status, &red,
                      &redout, &stage, &lamA, &lamB, &dgam, &duin, &plane};
     for (DevBuf* b : all) b->release();
     for (auto& b : ckpts) b.release();
@@ -216,6 +216,7 @@ Args make_args(const lbm_ctx* c) {
   a.fuse = c->kernel == 0 ? 1 : 0;
   a.inline_all = (a.fuse && c->model == LBM_BGK) ? 1 : 0;
   a.lidx = static_cast<const int*>(c->lidx.p);
+  a.ccode = static_cast<const unsigned long long*>(c->ccode.p);
   a.lsub = a.fuse ? static_cast<const int*>(c->lsub.p) : nullptr;
   a.n_sub = c->n_sub;
   a.lwall = static_cast<const int*>(c->lwall.p);
@@ -360,6 +361,8 @@ int build_geometry(lbm_ctx* c) {
   CK(c->lidx.ensure((size_t)c->N * sizeof(int)));
   CK(cudaMemsetAsync(c->lidx.p, 0xFF, (size_t)c->N * sizeof(int), s));
   geo_list_index(static_cast<const long long*>(c->lcell.p), c->n_list, static_cast<int*>(c->lidx.p), s);
+  CK(c->ccode.ensure((size_t)c->N * sizeof(unsigned long long)));
+  geo_cell_code(g, static_cast<const uint8_t*>(c->type.p), static_cast<unsigned long long*>(c->ccode.p), s);
   CK(c->wst.ensure(nl * WALL_STATE * c->ops->celem));
   CK(cudaMemsetAsync(c->wst.p, 0, nl * WALL_STATE * c->ops->celem, s));
   {

@@ -174,6 +174,7 @@ struct Args {
   int inline_all;          // fused mode with the BGK collision: the interior kernel updates every list
                            //    cell (no boundary-list kernel)
   const int* lidx;         // list position of every cell (-1 off the list)
+  const unsigned long long* ccode;  // slot codes of every list and NEAR cell, by cell index
   const int* lsub;         // list positions handled by the boundary-list kernel (fused mode)
   int n_sub;
   const int* lbc;          // list positions of INFLOW/OUTFLOW entries

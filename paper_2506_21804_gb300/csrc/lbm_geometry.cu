@@ -172,19 +172,11 @@ __global__ void k_list_write(const GeoArgs g, const uint8_t* type, const int* of
   if (f) lcell[base + __popc(b & ((1u << lane) - 1u))] = n;
 }
 
-// Per list entry: coordinates, integer wall-normal sum and reference position (WALL entries), and
-// the 2-bit slot code of every direction (0 plain neighbour, 1 own bounce-back slot, 2 slip rule).
+// 2-bit odd-step slot code of every direction of the cell at (x, y, z): 0 the plain (periodic-wrapped)
+// neighbour slot, 1 the cell's own bounce-back slot (solid source, or a source across a face that is
+// not all slip), 2 the slip rule.
 template <int Q>
-__global__ void k_list_meta(const GeoArgs g, const uint8_t* type, const long long* lcell, int n_list, int* nsum, int* wref,
-                            int* lxyz, unsigned long long* lcode) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n_list) return;
-  const long long n = lcell[k];
-  int x, y, z;
-  coords(g, n, x, y, z);
-  lxyz[3 * k] = x;
-  lxyz[3 * k + 1] = y;
-  lxyz[3 * k + 2] = z;
+__device__ __forceinline__ unsigned long long slot_code(const GeoArgs& g, const uint8_t* type, int x, int y, int z) {
   unsigned long long code = 0;
   sfor<0, Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
@@ -200,7 +192,23 @@ __global__ void k_list_meta(const GeoArgs g, const uint8_t* type, const long lon
     }
     code |= c << (2 * i);
   });
-  lcode[k] = code;
+  return code;
+}
+
+// Per list entry: coordinates, integer wall-normal sum and reference position (WALL entries), and
+// the slot code of every direction.
+template <int Q>
+__global__ void k_list_meta(const GeoArgs g, const uint8_t* type, const long long* lcell, int n_list, int* nsum, int* wref,
+                            int* lxyz, unsigned long long* lcode) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_list) return;
+  const long long n = lcell[k];
+  int x, y, z;
+  coords(g, n, x, y, z);
+  lxyz[3 * k] = x;
+  lxyz[3 * k + 1] = y;
+  lxyz[3 * k + 2] = z;
+  lcode[k] = slot_code<Q>(g, type, x, y, z);
   nsum[3 * k] = nsum[3 * k + 1] = nsum[3 * k + 2] = 0;
   wref[k] = -1;
   if ((type[n] & T_KIND) != K_WALL) return;
@@ -503,6 +511,27 @@ void geo_count_kinds(const uint8_t* type, long long N, unsigned long long* out, 
   long long blocks = nblocks(N, 256);
   if (blocks > 4 * 1216) blocks = 4 * 1216;
   k_count_kinds<<<unsigned(blocks), 256, 0, s>>>(type, N, out);
+}
+
+// Slot codes per cell (list and NEAR cells; 0 elsewhere), so that the interior kernel's mixed path
+// reads a cell's codes directly from its index rather than through its list position.
+template <int Q>
+__global__ void k_cell_code(const GeoArgs g, const uint8_t* type, unsigned long long* ccode) {
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= g.N) return;
+  const uint8_t t = type[n];
+  unsigned long long code = 0;
+  if ((t & (T_LIST | T_NEAR)) && (t & T_KIND) != K_SOLID) {
+    int x, y, z;
+    coords(g, n, x, y, z);
+    code = slot_code<Q>(g, type, x, y, z);
+  }
+  ccode[n] = code;
+}
+
+void geo_cell_code(const GeoArgs& g, const uint8_t* type, unsigned long long* ccode, cudaStream_t s) {
+  if (g.q == 19) k_cell_code<19><<<nblocks(g.N, 256), 256, 0, s>>>(g, type, ccode);
+  else k_cell_code<27><<<nblocks(g.N, 256), 256, 0, s>>>(g, type, ccode);
 }
 
 void geo_list_index(const long long* lcell, int n_list, int* lidx, cudaStream_t s) {

@@ -20,6 +20,13 @@ inline dim3 bulk_grid(const Args& a) {
   return dim3((a.nx + b.x - 1) / b.x, (a.ny + b.y - 1) / b.y, a.nz);
 }
 inline unsigned blocks_for(long long n, int t) { return unsigned((n + t - 1) / t); }
+// Threads of a 1-D CTA lying in one x-row that holds `groups` cell groups (pairs or quads) per row:
+// whole warps, at most BULK_THREADS.
+inline unsigned row_threads(int groups) {
+  const int t = ((groups + 31) / 32) * 32;
+  return unsigned(t < BULK_THREADS ? t : BULK_THREADS);
+}
+
 
 template <int Q, class S>
 struct Impl {
@@ -92,27 +99,21 @@ struct Impl {
     }
     if constexpr (sizeof(S) <= 4) {
       if (a.pairs) {
-        Args h = a;
-        h.nx = a.nx;  // launch shape over cell pairs
-        dim3 b = bulk_block(a);
-        int bx = (a.nx / 2) >= 64 ? 64 : (((a.nx / 2) + 31) / 32) * 32;
-        b = dim3(bx, BULK_THREADS / bx, 1);
-        const dim3 g((a.nx / 2 + b.x - 1) / b.x, (a.ny + b.y - 1) / b.y, a.nz);
+        // Row form: 1-D CTAs inside one x-row. 16-bit D3Q19 storage runs four cells per thread on
+        // even steps (nx a multiple of 4); odd steps, and every step of the other forms, run cell
+        // pairs (measured on the 256^3 FP16 channel per 8.4M cells: even 111 us vs 121 us, odd 156 us
+        // vs 149 us, quads vs pairs).
         if constexpr (sizeof(S) == 2 && Q == 19) {
           if (a.nx % 4 == 0 && !odd) {
-            // 16-bit storage, even steps: four cells per thread (k_bulk4), 32 quads x 4 rows per CTA.
-            // Odd steps stay with cell pairs: the quad's neighbour addressing spills at 80 registers
-            // there (measured on the 256^3 FP16 channel: even 111 us vs 121 us, odd 156 us vs 149 us
-            // per 8.4M cells, quads vs pairs).
-            const int qx = (a.nx / 4) >= 32 ? 32 : (((a.nx / 4) + 31) / 32) * 32;
-            const dim3 b4(qx, BULK_THREADS / qx, 1);
-            const dim3 g4((a.nx / 4 + b4.x - 1) / b4.x, (a.ny + b4.y - 1) / b4.y, a.nz);
-            k_bulk4<Q, S, false><<<g4, b4, 0, s>>>(h);
+            const unsigned t4 = row_threads(a.nx / 4);
+            k_bulk4r<Q, S><<<dim3((a.nx / 4 + t4 - 1) / t4, a.ny, a.nz), t4, 0, s>>>(a);
             return;
           }
         }
-        if (odd) k_bulk2<Q, S, true><<<g, b, 0, s>>>(h);
-        else k_bulk2<Q, S, false><<<g, b, 0, s>>>(h);
+        const unsigned t2 = row_threads(a.nx / 2);
+        const dim3 g2((a.nx / 2 + t2 - 1) / t2, a.ny, a.nz);
+        if (odd) k_bulk2r<Q, S, true><<<g2, t2, 0, s>>>(a);
+        else k_bulk2r<Q, S, false><<<g2, t2, 0, s>>>(a);
         return;
       }
     }

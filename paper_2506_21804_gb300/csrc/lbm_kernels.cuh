@@ -93,6 +93,73 @@ struct Nbr32Pair {
   }
 };
 
+// Neighbour indices of the cell group x0 .. x0 + W - 1 (W = 2 pairs, 4 quads; x0 a multiple of W) in a
+// launch whose CTA lies in one x-row (y = blockIdx.y, z = blockIdx.z): the y and z displacements with
+// their periodic wrap are the same for every thread of the CTA, so they are computed once per warp,
+// and only x0 - 1 (cell 0) and x0 + W (cell W - 1) can wrap per thread.
+template <int W>
+struct RowNbr {
+  unsigned un, unm, unp;   // index of x0; the same with the x-wrap of x0 - 1 / x0 + W folded in
+  int dym, dyp, dzm, dzp;  // uniform over the CTA
+  __device__ __forceinline__ RowNbr(const Args& a, int x0, int y, int z, unsigned un_) {
+    un = un_;
+    unm = x0 == 0 ? un_ + unsigned(a.nx) : un_;
+    unp = x0 + W == a.nx ? un_ - unsigned(a.nx) : un_;
+    const int nx = a.nx, nxy = int(a.nxy);
+    dym = y == 0 ? (a.ny - 1) * nx : -nx;
+    dyp = y == a.ny - 1 ? (1 - a.ny) * nx : nx;
+    dzm = z == 0 ? (a.nz - 1) * nxy : -nxy;
+    dzp = z == a.nz - 1 ? (1 - a.nz) * nxy : nxy;
+  }
+  // index of population p at cell x0 + CELL displaced by (DX, DY, DZ)
+  template <int CELL, int DX, int DY, int DZ>
+  __device__ __forceinline__ unsigned at(unsigned pbase) const {
+    unsigned u = pbase;
+    if constexpr (DY < 0) u += unsigned(dym);
+    if constexpr (DY > 0) u += unsigned(dyp);
+    if constexpr (DZ < 0) u += unsigned(dzm);
+    if constexpr (DZ > 0) u += unsigned(dzp);
+    if constexpr (CELL == 0 && DX < 0) return u + unm - 1u;
+    else if constexpr (CELL == W - 1 && DX > 0) return u + unp + unsigned(W);
+    else return u + un + unsigned(CELL + DX);
+  }
+};
+
+// L2 prefetch ahead of a row-form launch (16-bit storage). CTAs start in order of their linear index,
+// so CTA L is followed by CTA L + LBM_PF_CTAS about half a CTA lifetime later; threads 0 .. Q of CTA L
+// each ask the copy engine for one contiguous run of that later CTA's cells (the Q population arrays
+// and the type bytes) with one bulk L2 prefetch, which needs no register and no wait, so the later
+// CTA's loads find their lines in L2. The 16-bit kernels are bound by latency rather than bandwidth
+// and gain from it (256^3 FP16 channel: 61.1 -> 62.8 GLUPS); the FP32 kernels, already near the
+// bandwidth roofline, measured slower with it and do not prefetch. The runs start on 16-byte
+// boundaries when nx is a multiple of 16 (else nothing is prefetched).
+#ifndef LBM_PF_CTAS
+#define LBM_PF_CTAS 512
+#endif
+template <int Q, class S>
+__device__ __forceinline__ void row_prefetch(const Args& a, int cells_per_cta) {
+  if constexpr (LBM_PF_CTAS > 0 && sizeof(S) == 2) {
+    const int i = int(threadIdx.x);
+    if (i > Q || (a.nx & 15)) return;
+    const long long L = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z) + LBM_PF_CTAS;
+    const long long row = L / gridDim.x;
+    if (row >= (long long)a.ny * a.nz) return;
+    const int x_begin = int(L - row * gridDim.x) * cells_per_cta;
+    const int cells = min(cells_per_cta, a.nx - x_begin);
+    const long long n = row * a.nx + x_begin;
+    const char* p;
+    unsigned bytes;
+    if (i < Q) {
+      p = reinterpret_cast<const char*>(static_cast<const S*>(a.f) + (long long)i * a.stride + n);
+      bytes = unsigned(cells) * unsigned(sizeof(S));
+    } else {
+      p = reinterpret_cast<const char*>(a.type + n);
+      bytes = unsigned(cells);
+    }
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+  }
+}
+
 // Gather the Q deviations of cell n. LOAD_LOCAL: h_i from slot (i, n) of src (natural layout);
 // LOAD_SLOTS: h_i from the AA slot of direction i (state after an even step).
 template <int Q, class S, int LOAD>
@@ -110,7 +177,7 @@ __device__ __forceinline__ void gather(const Args& a, const S* src, int x, int y
       const unsigned us = unsigned(a.stride);
       sfor<0, Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
-        h[i] = Codec<S>::ld(src + nb.at<-Lat<Q>::cx(i), -Lat<Q>::cy(i), -Lat<Q>::cz(i)>(unsigned(opp<Q>(i)) * us));
+        h[i] = Codec<S>::ld(src + nb.template at<-Lat<Q>::cx(i), -Lat<Q>::cy(i), -Lat<Q>::cz(i)>(unsigned(opp<Q>(i)) * us));
       });
     } else if (!near) {
       const int xm = x == 0 ? a.nx - 1 : x - 1, xp = x == a.nx - 1 ? 0 : x + 1;
@@ -153,7 +220,7 @@ __device__ __forceinline__ void scatter(const Args& a, S* dst, int x, int y, int
       const unsigned us = unsigned(a.stride);
       sfor<0, Q>([&](auto I) {
         constexpr int k = decltype(I)::value;  // outgoing direction: f*_k goes to slot (k, x + c_k)
-        Codec<S>::st(dst + nb.at<Lat<Q>::cx(k), Lat<Q>::cy(k), Lat<Q>::cz(k)>(unsigned(k) * us), h[k]);
+        Codec<S>::st(dst + nb.template at<Lat<Q>::cx(k), Lat<Q>::cy(k), Lat<Q>::cz(k)>(unsigned(k) * us), h[k]);
       });
     } else if (!near) {
       const int xm = x == 0 ? a.nx - 1 : x - 1, xp = x == a.nx - 1 ? 0 : x + 1;
@@ -212,7 +279,7 @@ __device__ __forceinline__ void gather_coded(const Args& a, const S* src, int x,
     const unsigned us = unsigned(a.stride), un = unsigned(n);
     sfor<0, Q>([&](auto I) {
       constexpr int i = decltype(I)::value;
-      const unsigned plain = nb.at<-Lat<Q>::cx(i), -Lat<Q>::cy(i), -Lat<Q>::cz(i)>(unsigned(opp<Q>(i)) * us);
+      const unsigned plain = nb.template at<-Lat<Q>::cx(i), -Lat<Q>::cy(i), -Lat<Q>::cz(i)>(unsigned(opp<Q>(i)) * us);
       const unsigned own = unsigned(i) * us + un;
       h[i] = Codec<S>::ld(src + (((code >> (2 * i)) & 1ull) ? own : plain));
     });
@@ -239,7 +306,7 @@ __device__ __forceinline__ void scatter_coded(const Args& a, S* dst, int x, int 
     const unsigned us = unsigned(a.stride), un = unsigned(n);
     sfor<0, Q>([&](auto I) {
       constexpr int i = decltype(I)::value;
-      const unsigned plain = nb.at<-Lat<Q>::cx(i), -Lat<Q>::cy(i), -Lat<Q>::cz(i)>(unsigned(opp<Q>(i)) * us);
+      const unsigned plain = nb.template at<-Lat<Q>::cx(i), -Lat<Q>::cy(i), -Lat<Q>::cz(i)>(unsigned(opp<Q>(i)) * us);
       const unsigned own = unsigned(i) * us + un;
       Codec<S>::st(dst + (((code >> (2 * i)) & 1ull) ? own : plain), h[opp<Q>(i)]);
     });
@@ -428,20 +495,21 @@ __device__ __forceinline__ void bulk_cell(const Args& a, S* f, int x, int y, int
 }
 // Mixed path of the BGK interior kernel (fused mode, every list cell inline): one instruction stream
 // for every non-solid kind. Even steps gather and scatter the cell's own slots whatever its kind; odd
-// steps use per-lane slot codes (0 for plain cells, the list entry's codes for list cells, the
-// general rule for other cells next to a face), so lanes of different kinds only diverge in the
-// inlet/outlet reconstruction, the wall-state load and the general slot rule.
+// steps use per-lane slot codes (0 for plain cells; list and NEAR cells read theirs by cell index from
+// the per-cell code array), so lanes of different kinds only diverge in the inlet/outlet
+// reconstruction, the wall-state load and the slip rule.
 template <int Q, class S, bool ODD>
 __device__ __forceinline__ void mixed_cell(const Args& a, S* f, int x, int y, int z, long long n, uint8_t t) {
   using C = typename Codec<S>::C;
   const int kind = t & T_KIND;
   if (kind == K_SOLID || (t & T_GHOST)) return;
   const bool list = (t & T_LIST) != 0;
-  const int k = list ? a.lidx[n] : -1;
   C h[Q];
   unsigned long long code = 0;
+  // the slot codes come by cell index, so their load does not wait for the list position's
+  if constexpr (ODD) code = (t & (T_LIST | T_NEAR)) ? a.ccode[n] : 0ull;
+  const int k = list ? a.lidx[n] : -1;
   if constexpr (ODD) {
-    code = list ? a.lcode[k] : ((t & T_NEAR) ? 0xAAAAAAAAAAAAAAAAull : 0ull);
     gather_coded<Q, S>(a, f, x, y, z, n, code, h);
   } else {
     gather<Q, S, LOAD_LOCAL>(a, f, x, y, z, n, false, h);
@@ -539,9 +607,10 @@ template <> struct Pair<__nv_bfloat16> {
 // others with two 16-bit accesses; the pair stays packed in 16-bit pair registers and the two cells
 // collide together in packed FP32 lanes. Pairs holding a cell that is not plain FLUID take the
 // per-cell path.
-template <int Q, class S, bool ODD>
+template <int Q, class S, bool ODD, bool ROW = false>
 __device__ __forceinline__ void pair_load(const Args& a, const S* f, int x0, int y, int z, typename Pair<S>::V* raw) {
   using P = Pair<S>;
+  using NB = std::conditional_t<ROW, RowNbr<2>, Nbr32Pair>;
   const unsigned us = unsigned(a.stride);
   const unsigned un = unsigned(x0 + y * a.nx) + unsigned(z) * unsigned(a.nxy);
   if constexpr (!ODD) {
@@ -550,20 +619,21 @@ __device__ __forceinline__ void pair_load(const Args& a, const S* f, int x0, int
       raw[i] = P::ld(f + (unsigned(i) * us + un));
     });
   } else {
-    const Nbr32Pair nb(a, x0, y, z, un);
+    const NB nb(a, x0, y, z, un);
     sfor<0, Q>([&](auto I) {
       constexpr int i = decltype(I)::value;
       constexpr int cx = -Lat<Q>::cx(i), cy = -Lat<Q>::cy(i), cz = -Lat<Q>::cz(i);
       const unsigned pb = unsigned(opp<Q>(i)) * us;
-      if constexpr (cx == 0) raw[i] = P::ld(f + nb.at<0, 0, cy, cz>(pb));
-      else raw[i] = P::make(f[nb.at<0, cx, cy, cz>(pb)], f[nb.at<1, cx, cy, cz>(pb)]);
+      if constexpr (cx == 0) raw[i] = P::ld(f + nb.template at<0, 0, cy, cz>(pb));
+      else raw[i] = P::make(f[nb.template at<0, cx, cy, cz>(pb)], f[nb.template at<1, cx, cy, cz>(pb)]);
     });
   }
 }
 
-template <int Q, class S, bool ODD, bool HRR = false>
+template <int Q, class S, bool ODD, bool HRR = false, bool ROW = false>
 __device__ __forceinline__ void pair_update(const Args& a, S* f, int x0, int y, int z, typename Pair<S>::V* raw) {
   using P = Pair<S>;
+  using NB = std::conditional_t<ROW, RowNbr<2>, Nbr32Pair>;
   const unsigned us = unsigned(a.stride);
   const unsigned un = unsigned(x0 + y * a.nx) + unsigned(z) * unsigned(a.nxy);
   bool ok;
@@ -597,11 +667,13 @@ __device__ __forceinline__ void pair_update(const Args& a, S* f, int x0, int y, 
   }
   if (!ok) atomicOr(a.status, ST_NAN);
   // Opaque copies of the coordinates: the store addresses are recomputed here rather than held live
-  // across the collision.
-  int x0c, yc, zc;
+  // across the collision (in the row form y and z stay uniform over the CTA).
+  int x0c, yc = y, zc = z;
   asm volatile("mov.b32 %0, %1;" : "=r"(x0c) : "r"(x0));
-  asm volatile("mov.b32 %0, %1;" : "=r"(yc) : "r"(y));
-  asm volatile("mov.b32 %0, %1;" : "=r"(zc) : "r"(z));
+  if constexpr (!ROW) {
+    asm volatile("mov.b32 %0, %1;" : "=r"(yc) : "r"(y));
+    asm volatile("mov.b32 %0, %1;" : "=r"(zc) : "r"(z));
+  }
   const unsigned un2 = unsigned(x0c + yc * a.nx) + unsigned(zc) * unsigned(a.nxy);
   if constexpr (!ODD) {
     sfor<0, Q>([&](auto I) {
@@ -609,16 +681,16 @@ __device__ __forceinline__ void pair_update(const Args& a, S* f, int x0, int y, 
       P::st(f + (unsigned(opp<Q>(i)) * us + un2), raw[i]);
     });
   } else {
-    const Nbr32Pair nb(a, x0c, yc, zc, un2);
+    const NB nb(a, x0c, yc, zc, un2);
     sfor<0, Q>([&](auto I) {
       constexpr int k = decltype(I)::value;  // f*_k goes to slot (k, x + c_k)
       constexpr int cx = Lat<Q>::cx(k), cy = Lat<Q>::cy(k), cz = Lat<Q>::cz(k);
       const unsigned pb = unsigned(k) * us;
       if constexpr (cx == 0) {
-        P::st(f + nb.at<0, 0, cy, cz>(pb), raw[k]);
+        P::st(f + nb.template at<0, 0, cy, cz>(pb), raw[k]);
       } else {
-        f[nb.at<0, cx, cy, cz>(pb)] = P::lo(raw[k]);
-        f[nb.at<1, cx, cy, cz>(pb)] = P::hi(raw[k]);
+        f[nb.template at<0, cx, cy, cz>(pb)] = P::lo(raw[k]);
+        f[nb.template at<1, cx, cy, cz>(pb)] = P::hi(raw[k]);
       }
     });
   }
@@ -650,41 +722,36 @@ __global__ void __launch_bounds__(BULK_THREADS, (Q == 19 && !HRR ? (ODD ? LBM_BU
   pair_update<Q, S, ODD, HRR>(a, f, x0, y, z, raw);
 }
 
-// ---- 16-bit storage, four cells per thread ---------------------------------------------------------------
-// The thread owns cells x0 = 4j .. x0 + 3 (nx a multiple of 4): 8 bytes per population, the bytes a
-// thread of the FP32 pair kernel keeps in flight. Directions without an x-component move the four
-// values with one 8-byte access. On odd steps an x-shifted quad is one 16-bit value, the aligned
-// 32-bit word of the two middle cells, and another 16-bit value. The quad collides as two pairs in
-// turn (packed FP32 lanes, the pair kernel's arithmetic). The library launches the even-step form;
-// the odd-step form is correct but spills at this register budget and measured slower than pairs.
-struct Nbr32Quad {
-  unsigned n;  // index of x0
-  int dxm, dxp, dym, dyp, dzm, dzp;
-  __device__ __forceinline__ Nbr32Quad(const Args& a, int x0, int y, int z, unsigned n0) {
-    n = n0;
-    const int nx = a.nx, nxy = int(a.nxy);
-    dxm = x0 == 0 ? nx - 1 : -1;
-    dxp = x0 + 3 == nx - 1 ? 1 - nx : 1;
-    dym = y == 0 ? (a.ny - 1) * nx : -nx;
-    dyp = y == a.ny - 1 ? (1 - a.ny) * nx : nx;
-    dzm = z == 0 ? (a.nz - 1) * nxy : -nxy;
-    dzp = z == a.nz - 1 ? (1 - a.nz) * nxy : nxy;
+// The pair kernel over CTAs that each lie in one x-row (grid (ceil(nx / 2 / blockDim.x), ny, nz), 1-D
+// blocks): y and z come from the block index, so the neighbour displacements of the odd step are
+// computed once per warp instead of per thread.
+template <int Q, class S, bool ODD>
+__global__ void __launch_bounds__(BULK_THREADS, (Q == 19 ? (ODD ? LBM_BULK2_MINB_ODD : LBM_BULK2_MINB_EVEN) : 4))
+    k_bulk2r(const Args a) {
+  row_prefetch<Q, S>(a, 2 * blockDim.x);
+  const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const int y = blockIdx.y;
+  const int z = blockIdx.z;
+  if (x0 >= a.nx) return;
+  const long long n0 = x0 + (long long)y * a.nx + (long long)z * a.nxy;
+  S* f = static_cast<S*>(a.f);
+  const unsigned short tt = *reinterpret_cast<const unsigned short*>(a.type + n0);
+  if (tt) {
+    bulk_cell<Q, S, ODD>(a, f, x0, y, z, n0, uint8_t(tt & 0xff));
+    bulk_cell<Q, S, ODD>(a, f, x0 + 1, y, z, n0 + 1, uint8_t(tt >> 8));
+    return;
   }
-  // index of population p at cell x0 + CELL displaced by (dx, dy, dz); only x0 - 1 and x0 + 4 can wrap
-  template <int CELL, int DX, int DY, int DZ>
-  __device__ __forceinline__ unsigned at(unsigned pbase) const {
-    unsigned r = pbase + n;
-    if constexpr (CELL == 0 && DX < 0) r += unsigned(dxm);
-    else if constexpr (CELL == 3 && DX > 0) r += 3u + unsigned(dxp);
-    else r += unsigned(CELL + DX);
-    if constexpr (DY < 0) r += unsigned(dym);
-    if constexpr (DY > 0) r += unsigned(dyp);
-    if constexpr (DZ < 0) r += unsigned(dzm);
-    if constexpr (DZ > 0) r += unsigned(dzp);
-    return r;
-  }
-};
+  typename Pair<S>::V raw[Q];
+  pair_load<Q, S, ODD, true>(a, f, x0, y, z, raw);
+  pair_update<Q, S, ODD, false, true>(a, f, x0, y, z, raw);
+}
 
+// ---- 16-bit storage, four cells per thread ---------------------------------------------------------------
+// Even steps only: the thread owns cells x0 = 4j .. x0 + 3 (nx a multiple of 4) and moves 8 bytes per
+// population, the bytes a thread of the FP32 pair kernel keeps in flight; every access is local and
+// aligned. The quad collides as two pairs in turn (packed FP32 lanes, the pair kernel's arithmetic).
+// Odd steps run the pair kernel: an x-shifted quad needs two 16-bit accesses and an aligned word per
+// population, which measured slower than pairs (spills at this register budget).
 template <class V> __device__ __forceinline__ V as_pair(unsigned u) {
   V v;
   __builtin_memcpy(&v, &u, sizeof(v));
@@ -715,98 +782,48 @@ __device__ __forceinline__ bool pair_collide(const Args& a, unsigned un, typenam
       [&](int i, float2 v) { raw[i] = P::pack(v.x, v.y); }, gam, a);
 }
 
-template <int Q, class S, bool ODD>
-__device__ __forceinline__ void quad_load(const Args& a, const S* f, int x0, int y, int z, unsigned un,
-                                          typename Pair<S>::V* ra, typename Pair<S>::V* rb) {
-  using P = Pair<S>;
-  using V = typename P::V;
-  const unsigned us = unsigned(a.stride);
-  if constexpr (!ODD) {
-    sfor<0, Q>([&](auto I) {
-      constexpr int i = decltype(I)::value;
-      const uint2 v = *reinterpret_cast<const uint2*>(f + (unsigned(i) * us + un));
-      ra[i] = as_pair<V>(v.x);
-      rb[i] = as_pair<V>(v.y);
-    });
-  } else {
-    const Nbr32Quad nb(a, x0, y, z, un);
-    sfor<0, Q>([&](auto I) {
-      constexpr int i = decltype(I)::value;
-      constexpr int cx = -Lat<Q>::cx(i), cy = -Lat<Q>::cy(i), cz = -Lat<Q>::cz(i);
-      const unsigned pb = unsigned(opp<Q>(i)) * us;
-      if constexpr (cx == 0) {
-        const uint2 v = *reinterpret_cast<const uint2*>(f + nb.at<0, 0, cy, cz>(pb));
-        ra[i] = as_pair<V>(v.x);
-        rb[i] = as_pair<V>(v.y);
-      } else {
-        const V w = P::ld(f + nb.at<1, cx, cy, cz>(pb));  // cells 1 and 2: an aligned word
-        ra[i] = P::make(f[nb.at<0, cx, cy, cz>(pb)], P::lo(w));
-        rb[i] = P::make(P::hi(w), f[nb.at<3, cx, cy, cz>(pb)]);
-      }
-    });
-  }
-}
-
-template <int Q, class S, bool ODD>
-__device__ __forceinline__ void quad_store(const Args& a, S* f, int x0, int y, int z, unsigned un,
-                                           const typename Pair<S>::V* ra, const typename Pair<S>::V* rb) {
-  using P = Pair<S>;
-  const unsigned us = unsigned(a.stride);
-  if constexpr (!ODD) {
-    sfor<0, Q>([&](auto I) {
-      constexpr int i = decltype(I)::value;
-      *reinterpret_cast<uint2*>(f + (unsigned(opp<Q>(i)) * us + un)) = make_uint2(as_word(ra[i]), as_word(rb[i]));
-    });
-  } else {
-    const Nbr32Quad nb(a, x0, y, z, un);
-    sfor<0, Q>([&](auto I) {
-      constexpr int k = decltype(I)::value;  // f*_k goes to slot (k, x + c_k)
-      constexpr int cx = Lat<Q>::cx(k), cy = Lat<Q>::cy(k), cz = Lat<Q>::cz(k);
-      const unsigned pb = unsigned(k) * us;
-      if constexpr (cx == 0) {
-        *reinterpret_cast<uint2*>(f + nb.at<0, 0, cy, cz>(pb)) = make_uint2(as_word(ra[k]), as_word(rb[k]));
-      } else {
-        f[nb.at<0, cx, cy, cz>(pb)] = P::lo(ra[k]);
-        P::st(f + nb.at<1, cx, cy, cz>(pb), P::make(P::hi(ra[k]), P::lo(rb[k])));
-        f[nb.at<3, cx, cy, cz>(pb)] = P::hi(rb[k]);
-      }
-    });
-  }
-}
-
 // Six CTAs of 128 threads per SM (80 registers): measured against 4 (128 registers), 5 (96) and 7
 // (72, more spilling) on the 256^3 FP16 channel.
 #ifndef LBM_BULK4_MINB
 #define LBM_BULK4_MINB 6
 #endif
-template <int Q, class S, bool ODD>
-__global__ void __launch_bounds__(BULK_THREADS, LBM_BULK4_MINB) k_bulk4(const Args a) {
+// Row form (as k_bulk2r): CTAs of 1-D blocks inside one x-row, y and z from the block index.
+template <int Q, class S>
+__global__ void __launch_bounds__(BULK_THREADS, LBM_BULK4_MINB) k_bulk4r(const Args a) {
   static_assert(sizeof(S) == 2 && Q == 19, "four cells per thread: D3Q19, 16-bit storage");
+  row_prefetch<Q, S>(a, 4 * blockDim.x);
   const int x0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int y = blockIdx.y;
   const int z = blockIdx.z;
-  if (x0 >= a.nx || y >= a.ny) return;
+  if (x0 >= a.nx) return;
   const long long n0 = x0 + (long long)y * a.nx + (long long)z * a.nxy;
   S* f = static_cast<S*>(a.f);
   const unsigned tt = *reinterpret_cast<const unsigned*>(a.type + n0);
   if (tt) {
 #pragma unroll 1
-    for (int c = 0; c < 4; ++c) bulk_cell<Q, S, ODD>(a, f, x0 + c, y, z, n0 + c, uint8_t(tt >> (8 * c)));
+    for (int c = 0; c < 4; ++c) bulk_cell<Q, S, false>(a, f, x0 + c, y, z, n0 + c, uint8_t(tt >> (8 * c)));
     return;
   }
-  typename Pair<S>::V ra[Q], rb[Q];
-  const unsigned un = unsigned(n0);
-  quad_load<Q, S, ODD>(a, f, x0, y, z, un, ra, rb);
+  using V = typename Pair<S>::V;
+  V ra[Q], rb[Q];
+  const unsigned un = unsigned(n0), us = unsigned(a.stride);
+  sfor<0, Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    const uint2 v = *reinterpret_cast<const uint2*>(f + (unsigned(i) * us + un));
+    ra[i] = as_pair<V>(v.x);
+    rb[i] = as_pair<V>(v.y);
+  });
   bool ok = pair_collide<Q, S>(a, un, ra);
   ok = pair_collide<Q, S>(a, un + 2u, rb) && ok;
   if (!ok) atomicOr(a.status, ST_NAN);
-  // opaque copies of the coordinates: the store addresses are recomputed, not held live
-  int x0c, yc, zc;
+  // an opaque copy of x0: the store addresses are recomputed, not held live across the collision
+  int x0c;
   asm volatile("mov.b32 %0, %1;" : "=r"(x0c) : "r"(x0));
-  asm volatile("mov.b32 %0, %1;" : "=r"(yc) : "r"(y));
-  asm volatile("mov.b32 %0, %1;" : "=r"(zc) : "r"(z));
-  const unsigned un2 = unsigned(x0c + yc * a.nx) + unsigned(zc) * unsigned(a.nxy);
-  quad_store<Q, S, ODD>(a, f, x0c, yc, zc, un2, ra, rb);
+  const unsigned un2 = unsigned(x0c + y * a.nx) + unsigned(z) * unsigned(a.nxy);
+  sfor<0, Q>([&](auto I) {
+    constexpr int i = decltype(I)::value;
+    *reinterpret_cast<uint2*>(f + (unsigned(opp<Q>(i)) * us + un2)) = make_uint2(as_word(ra[i]), as_word(rb[i]));
+  });
 }
 
 // Wall-model state of every WALL entry from the previous step's reference velocities (fused mode).
