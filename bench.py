@@ -203,9 +203,9 @@ def interior_kernel_name(code, q, storage, hrr):
     if code == 2:
         return f"k_bulk_tma<{q}, {s}>"
     if code == 3:
-        return f"k_bulk4<{q}, {s}> (even steps) + k_bulk2<{q}, {s}> (odd steps)"
+        return f"k_bulk4r<{q}, {s}> (even steps) + k_bulk2r<{q}, {s}> (odd steps)"
     if code == 1:
-        return f"k_bulk2<{q}, {s}{', HRR' if hrr else ''}>"
+        return f"k_bulk2r<{q}, {s}, HRR>" if hrr else f"k_bulk2r<{q}, {s}>"
     return f"k_bulk_hrr<{q}, {s}>" if hrr else f"k_bulk<{q}, {s}>"
 
 

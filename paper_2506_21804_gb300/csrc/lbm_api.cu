@@ -263,6 +263,21 @@ int check_ptr(const lbm_ctx* c, const void* p, const char* what) {
 
 size_t dsize(int dtype) { return dtype == LBM_DTYPE_F64 ? 8 : 4; }
 
+// Device address of page-locked host memory that kernels may read and write directly (over the
+// CPU-GPU link, one pass, no staging copy), or null for any other pointer.
+#ifndef LBM_MAPPED_HOST
+#define LBM_MAPPED_HOST 1
+#endif
+void* mapped_host(const void* p) {
+  if (!LBM_MAPPED_HOST || !p) return nullptr;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 int read_status(lbm_ctx* c) {
   CK(cudaMemcpyAsync(c->status_h, c->status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
@@ -990,13 +1005,20 @@ int lbm_init_equilibrium_ex(lbm_ctx* c, const void* rho, const void* u, int dtyp
   if ((rc = check_ptr(c, u, "u")) != LBM_OK) return rc;
   const size_t es = dsize(dtype);
   const size_t bytes = (size_t)c->N * es;
-  CK(c->stage.ensure(4 * bytes));
-  CK(cudaMemcpyAsync(c->stage.p, rho, bytes, cudaMemcpyDefault, c->stream));
-  CK(cudaMemcpyAsync(static_cast<char*>(c->stage.p) + bytes, u, 3 * bytes, cudaMemcpyDefault, c->stream));
+  // page-locked host fields are read by the kernel in place; other memory is staged on the device
+  const void* src_rho = mapped_host(rho);
+  const void* src_u = mapped_host(u);
+  if (!src_rho || !src_u) {
+    CK(c->stage.ensure(4 * bytes));
+    CK(cudaMemcpyAsync(c->stage.p, rho, bytes, cudaMemcpyDefault, c->stream));
+    CK(cudaMemcpyAsync(static_cast<char*>(c->stage.p) + bytes, u, 3 * bytes, cudaMemcpyDefault, c->stream));
+    src_rho = c->stage.p;
+    src_u = static_cast<char*>(c->stage.p) + bytes;
+  }
   c->t = 0;
   c->adj_t0 = -1;
   Args a = make_args(c);
-  c->ops->init_eq(a, c->stage.p, static_cast<char*>(c->stage.p) + bytes, dtype, c->stream);
+  c->ops->init_eq(a, src_rho, src_u, dtype, c->stream);
   CK(cudaGetLastError());
   CK(cudaMemsetAsync(c->status.p, 0, sizeof(unsigned), c->stream));
   c->status_seen = 0;
@@ -1061,8 +1083,14 @@ int lbm_moments_ex(lbm_ctx* c, void* rho, void* u, int dtype) {
   Args a = make_args(c);
   const int sw = int(c->t & 1);
   const bool dev = is_device_ptr(rho, c->device) && is_device_ptr(u, c->device);
+  void* mrho = mapped_host(rho);
+  void* mu = mapped_host(u);
   if (dev) {
     c->ops->moments(a, sw, rho, u, dtype, c->stream);
+    CK(cudaGetLastError());
+  } else if (mrho && mu) {
+    // page-locked host fields: the kernel writes them in place
+    c->ops->moments(a, sw, mrho, mu, dtype, c->stream);
     CK(cudaGetLastError());
   } else {
     CK(c->stage.ensure(4 * bytes));

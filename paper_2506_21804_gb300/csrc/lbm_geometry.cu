@@ -110,7 +110,14 @@ __global__ void k_classify(const GeoArgs g, const uint8_t* mask, uint8_t* type, 
   }
   if (m == 1) { type[n] = K_SOLID | ((z < g.gh_lo || z >= g.nz - g.gh_hi) ? T_GHOST : 0); return; }
   bool wall = false, near = false;
-  sfor<1, Q>([&](auto I) {
+  if (x > 0 && x < g.nx - 1 && y > 0 && y < g.ny - 1 && z > 0 && z < g.nz - 1) {
+    // away from the faces no source position wraps or leaves the domain: plain index offsets
+    sfor<1, Q>([&](auto I) {
+      constexpr int i = decltype(I)::value;
+      if (mask[n + Lat<Q>::cx(i) + (long long)g.nx * Lat<Q>::cy(i) + g.nxy * Lat<Q>::cz(i)] == 1) wall = true;
+    });
+    near = wall;
+  } else sfor<1, Q>([&](auto I) {
     constexpr int i = decltype(I)::value;
     // neighbour x + c_i (solid neighbour => WALL)
     const Pos p = wrap(g, x + Lat<Q>::cx(i), y + Lat<Q>::cy(i), z + Lat<Q>::cz(i));

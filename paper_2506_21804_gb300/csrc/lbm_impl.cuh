@@ -81,11 +81,10 @@ struct Impl {
     if (a.model != 0) {
       if constexpr (sizeof(S) <= 4) {
         if (a.pairs && a.N % 2 == 0) {
-          const int bx = (a.nx / 2) >= 64 ? 64 : (((a.nx / 2) + 31) / 32) * 32;
-          const dim3 b(bx, BULK_THREADS / bx, 1);
-          const dim3 g((a.nx / 2 + b.x - 1) / b.x, (a.ny + b.y - 1) / b.y, a.nz);
-          if (odd) k_bulk2<Q, S, true, true><<<g, b, 0, s>>>(a);
-          else k_bulk2<Q, S, false, true><<<g, b, 0, s>>>(a);
+          const unsigned t2 = row_threads(a.nx / 2);
+          const dim3 g2((a.nx / 2 + t2 - 1) / t2, a.ny, a.nz);
+          if (odd) k_bulk2r<Q, S, true, true><<<g2, t2, 0, s>>>(a);
+          else k_bulk2r<Q, S, false, true><<<g2, t2, 0, s>>>(a);
           return;
         }
       }

@@ -62,37 +62,6 @@ struct Nbr32 {
   }
 };
 
-// Neighbour offsets of the cell pair (x0, x0 + 1), x0 even and nx even: only x0 - 1 and x0 + 2 can
-// wrap in x, so one x-delta per side serves both cells.
-struct Nbr32Pair {
-  unsigned n;  // index of x0
-  int dxm, dxp, dym, dyp, dzm, dzp;
-  __device__ __forceinline__ Nbr32Pair(const Args& a, int x0, int y, int z, long long n0) {
-    n = unsigned(n0);
-    const int nx = a.nx, nxy = int(a.nxy);
-    dxm = x0 == 0 ? nx - 1 : -1;
-    dxp = x0 + 1 == nx - 1 ? 1 - nx : 1;
-    dym = y == 0 ? (a.ny - 1) * nx : -nx;
-    dyp = y == a.ny - 1 ? (1 - a.ny) * nx : nx;
-    dzm = z == 0 ? (a.nz - 1) * nxy : -nxy;
-    dzp = z == a.nz - 1 ? (1 - a.nz) * nxy : nxy;
-  }
-  // index of population p at cell x0 + CELL displaced by (dx, dy, dz)
-  template <int CELL, int DX, int DY, int DZ>
-  __device__ __forceinline__ unsigned at(unsigned pbase) const {
-    unsigned r = pbase + n;
-    if constexpr (CELL == 0 && DX < 0) r += unsigned(dxm);
-    if constexpr (CELL == 0 && DX > 0) r += 1u;
-    if constexpr (CELL == 1 && DX == 0) r += 1u;
-    if constexpr (CELL == 1 && DX > 0) r += 1u + unsigned(dxp);
-    if constexpr (DY < 0) r += unsigned(dym);
-    if constexpr (DY > 0) r += unsigned(dyp);
-    if constexpr (DZ < 0) r += unsigned(dzm);
-    if constexpr (DZ > 0) r += unsigned(dzp);
-    return r;
-  }
-};
-
 // Neighbour indices of the cell group x0 .. x0 + W - 1 (W = 2 pairs, 4 quads; x0 a multiple of W) in a
 // launch whose CTA lies in one x-row (y = blockIdx.y, z = blockIdx.z): the y and z displacements with
 // their periodic wrap are the same for every thread of the CTA, so they are computed once per warp,
@@ -325,11 +294,10 @@ __device__ __forceinline__ void scatter_coded(const Args& a, S* dst, int x, int 
   });
 }
 
-// Slot code of a cell for the adjoint and recompute passes: list cells carry theirs; other cells
-// use plain slots unless they are NEAR (then the general rule, returned as all-2 codes).
+// Slot code of a cell for the adjoint and recompute passes: list and NEAR cells read theirs from the
+// per-cell code array; other cells use plain slots.
 __device__ __forceinline__ unsigned long long cell_code(const Args& a, long long n, uint8_t t) {
-  if (t & T_LIST) return a.lcode[a.lidx[n]];
-  return (t & T_NEAR) ? 0xAAAAAAAAAAAAAAAAull : 0ull;
+  return (t & (T_LIST | T_NEAR)) ? a.ccode[n] : 0ull;
 }
 
 template <class C> __device__ __forceinline__ const C* cptr(const void* p) { return static_cast<const C*>(p); }
@@ -607,10 +575,10 @@ template <> struct Pair<__nv_bfloat16> {
 // others with two 16-bit accesses; the pair stays packed in 16-bit pair registers and the two cells
 // collide together in packed FP32 lanes. Pairs holding a cell that is not plain FLUID take the
 // per-cell path.
-template <int Q, class S, bool ODD, bool ROW = false>
+template <int Q, class S, bool ODD>
 __device__ __forceinline__ void pair_load(const Args& a, const S* f, int x0, int y, int z, typename Pair<S>::V* raw) {
   using P = Pair<S>;
-  using NB = std::conditional_t<ROW, RowNbr<2>, Nbr32Pair>;
+  using NB = RowNbr<2>;
   const unsigned us = unsigned(a.stride);
   const unsigned un = unsigned(x0 + y * a.nx) + unsigned(z) * unsigned(a.nxy);
   if constexpr (!ODD) {
@@ -630,10 +598,10 @@ __device__ __forceinline__ void pair_load(const Args& a, const S* f, int x0, int
   }
 }
 
-template <int Q, class S, bool ODD, bool HRR = false, bool ROW = false>
+template <int Q, class S, bool ODD, bool HRR = false>
 __device__ __forceinline__ void pair_update(const Args& a, S* f, int x0, int y, int z, typename Pair<S>::V* raw) {
   using P = Pair<S>;
-  using NB = std::conditional_t<ROW, RowNbr<2>, Nbr32Pair>;
+  using NB = RowNbr<2>;
   const unsigned us = unsigned(a.stride);
   const unsigned un = unsigned(x0 + y * a.nx) + unsigned(z) * unsigned(a.nxy);
   bool ok;
@@ -666,14 +634,11 @@ __device__ __forceinline__ void pair_update(const Args& a, S* f, int x0, int y, 
     sfor<0, Q>([&](auto I) { raw[I] = P::pack(h[I].x, h[I].y); });
   }
   if (!ok) atomicOr(a.status, ST_NAN);
-  // Opaque copies of the coordinates: the store addresses are recomputed here rather than held live
-  // across the collision (in the row form y and z stay uniform over the CTA).
-  int x0c, yc = y, zc = z;
+  // An opaque copy of x0: the store addresses are recomputed here rather than held live across the
+  // collision (y and z are uniform over the CTA).
+  int x0c;
+  const int yc = y, zc = z;
   asm volatile("mov.b32 %0, %1;" : "=r"(x0c) : "r"(x0));
-  if constexpr (!ROW) {
-    asm volatile("mov.b32 %0, %1;" : "=r"(yc) : "r"(y));
-    asm volatile("mov.b32 %0, %1;" : "=r"(zc) : "r"(z));
-  }
   const unsigned un2 = unsigned(x0c + yc * a.nx) + unsigned(zc) * unsigned(a.nxy);
   if constexpr (!ODD) {
     sfor<0, Q>([&](auto I) {
@@ -702,13 +667,17 @@ __device__ __forceinline__ void pair_update(const Args& a, S* f, int x0, int y, 
 #ifndef LBM_BULK2_MINB_ODD
 #define LBM_BULK2_MINB_ODD 7
 #endif
+// The pair kernel (BGK or HRR collision) over CTAs that each lie in one x-row (grid
+// (ceil(nx / 2 / blockDim.x), ny, nz), 1-D blocks): y and z come from the block index, so the
+// neighbour displacements of the odd step are computed once per warp instead of per thread.
 template <int Q, class S, bool ODD, bool HRR = false>
 __global__ void __launch_bounds__(BULK_THREADS, (Q == 19 && !HRR ? (ODD ? LBM_BULK2_MINB_ODD : LBM_BULK2_MINB_EVEN) : 4))
-    k_bulk2(const Args a) {
+    k_bulk2r(const Args a) {
+  row_prefetch<Q, S>(a, 2 * blockDim.x);
   const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
-  const int y = blockIdx.y * blockDim.y + threadIdx.y;
+  const int y = blockIdx.y;
   const int z = blockIdx.z;
-  if (x0 >= a.nx || y >= a.ny) return;
+  if (x0 >= a.nx) return;
   const long long n0 = x0 + (long long)y * a.nx + (long long)z * a.nxy;
   S* f = static_cast<S*>(a.f);
   const unsigned short tt = *reinterpret_cast<const unsigned short*>(a.type + n0);
@@ -720,30 +689,6 @@ __global__ void __launch_bounds__(BULK_THREADS, (Q == 19 && !HRR ? (ODD ? LBM_BU
   typename Pair<S>::V raw[Q];
   pair_load<Q, S, ODD>(a, f, x0, y, z, raw);
   pair_update<Q, S, ODD, HRR>(a, f, x0, y, z, raw);
-}
-
-// The pair kernel over CTAs that each lie in one x-row (grid (ceil(nx / 2 / blockDim.x), ny, nz), 1-D
-// blocks): y and z come from the block index, so the neighbour displacements of the odd step are
-// computed once per warp instead of per thread.
-template <int Q, class S, bool ODD>
-__global__ void __launch_bounds__(BULK_THREADS, (Q == 19 ? (ODD ? LBM_BULK2_MINB_ODD : LBM_BULK2_MINB_EVEN) : 4))
-    k_bulk2r(const Args a) {
-  row_prefetch<Q, S>(a, 2 * blockDim.x);
-  const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
-  const int y = blockIdx.y;
-  const int z = blockIdx.z;
-  if (x0 >= a.nx) return;
-  const long long n0 = x0 + (long long)y * a.nx + (long long)z * a.nxy;
-  S* f = static_cast<S*>(a.f);
-  const unsigned short tt = *reinterpret_cast<const unsigned short*>(a.type + n0);
-  if (tt) {
-    bulk_cell<Q, S, ODD>(a, f, x0, y, z, n0, uint8_t(tt & 0xff));
-    bulk_cell<Q, S, ODD>(a, f, x0 + 1, y, z, n0 + 1, uint8_t(tt >> 8));
-    return;
-  }
-  typename Pair<S>::V raw[Q];
-  pair_load<Q, S, ODD, true>(a, f, x0, y, z, raw);
-  pair_update<Q, S, ODD, false, true>(a, f, x0, y, z, raw);
 }
 
 // ---- 16-bit storage, four cells per thread ---------------------------------------------------------------

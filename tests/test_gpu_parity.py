@@ -244,6 +244,63 @@ def test_16bit_multi_cell_kernels_match_oracle_storage_emulation(storage):
             assert err <= k * 2.0 ** -mant * hmax, (w.name, t, err, hmax)
 
 
+@pytest.mark.parametrize("nx", [520, 544])
+def test_row_form_kernels_several_ctas_per_row(nx):
+    """Rows wider than one CTA of the row-form interior kernels, so that a row spans several CTAs and
+    the last one is partial (nx = 520: 260 pairs, 130 quads per row; nx = 544 also runs the 16-bit L2
+    prefetch ahead of the later CTAs, which needs nx a multiple of 16). FP32 cell pairs against the
+    FP64 oracle after 20 steps (1e-5), and the 16-bit kernels (four cells per thread on even steps,
+    pairs on odd steps) against the oracle's 16-bit storage emulation over three steps, with the bound
+    of the multi-cell test above."""
+    w = I.random_box(nx, 3, 4, seed=nx, q=19, solid_frac=0.0, tau=0.7, cs=0.1)
+    fl = w.mask != 1
+    g = gpu_from(w, lbm.F32)
+    assert g.interior_kernel() == 1
+    o = oracle_from(w, cast32=True)
+    g.step(20)
+    o.step(20)
+    ro, uo = o.moments()
+    rg, ug = g.moments()
+    assert np.abs(rg[fl] - ro[fl]).max() < 1e-5
+    assert rel_l2(ug[:, fl], uo[:, fl]) < 1e-5
+    c, wts, *_ = O.lattice(19)
+    for storage, mant in ((lbm.F16, 10), (lbm.BF16, 7)):
+        g = gpu_from(w, storage)
+        assert g.interior_kernel() == 3
+        o = oracle_from(w, storage=int(storage))
+        for t in (1, 2, 3):
+            g.step(1)
+            o.step(1)
+            fg = g.get_populations()[:, fl]
+            fo = o.populations()[:, fl]
+            hmax = np.abs(fo - wts[:, None]).max()
+            k = 4 if t == 1 else 8
+            assert np.abs(fg - fo).max() <= k * 2.0 ** -mant * hmax, (storage, t)
+
+
+def test_page_locked_host_fields_match_pageable():
+    """Initial fields and moments through page-locked host buffers (read and written by the kernels in
+    place) give the same bits as through pageable host arrays (staged through device memory), for
+    FP32 and FP64 fields."""
+    torch = pytest.importorskip("torch")
+    w = I.channel(nx=32, ny=12, nz=8, seed=550, dtype=np.float64)
+    for dt, tdt in ((np.float32, torch.float32), (np.float64, torch.float64)):
+        a = gpu_from(w, lbm.F32)
+        a.init_equilibrium(np.asarray(w.rho0, dt), np.asarray(w.u0, dt))
+        a.step(5)
+        ra, ua = a.moments(dt)
+        b = gpu_from(w, lbm.F32)
+        rho_h = torch.from_numpy(np.ascontiguousarray(w.rho0, dt)).pin_memory()
+        u_h = torch.from_numpy(np.ascontiguousarray(w.u0, dt)).pin_memory()
+        b.init_equilibrium(rho_h, u_h)
+        b.step(5)
+        rho_o = torch.full((w.N,), float("nan"), dtype=tdt).pin_memory()
+        u_o = torch.full((3, w.N), float("nan"), dtype=tdt).pin_memory()
+        b.moments(dt, rho_o, u_o)
+        assert np.array_equal(rho_o.numpy(), ra)
+        assert np.array_equal(u_o.numpy(), ua)
+
+
 def test_interior_kernel_selection():
     """The library's choice of interior kernel: pairs for the FP32 channel, four cells per thread
     (even steps) for its 16-bit forms, pairs for 16-bit D3Q27 and for the HRR collision, one cell per
@@ -519,6 +576,26 @@ def test_full_size_channel_256_sampled():
     w = I.channel(nx=256, ny=256, nz=256, seed=550, dtype=np.float32)
     er, eu = _sampled_full_size(w, lbm.F32, steps=4, samples=48, R=7, seed=1)
     assert er < 1e-6 and eu < 1e-5, (er, eu)
+
+
+def test_full_size_channel_256_every_cell_100_steps():
+    """The 256^3 turbulent channel of the benchmark (D3Q19, Smagorinsky C_S = 0.1, wall function,
+    body force), FP32 in the benchmark's launch shape, against the FP64 oracle on the full grid after
+    100 steps: every non-solid cell, rho within 1e-5 and u within 1e-5 relative L2 (the oracle runs on
+    all host cores, about a minute)."""
+    w = I.channel(nx=256, ny=256, nz=256, seed=550, dtype=np.float64)
+    g = gpu_from(w, lbm.F32)
+    assert g.interior_kernel() == 1
+    g.step(100)
+    rg, ug = g.moments()
+    g.close()
+    o = oracle_from(w, cast32=True)
+    o.step(100)
+    ro, uo = o.moments()
+    del o
+    fl = w.mask != 1
+    assert np.abs(rg[fl] - ro[fl]).max() < 1e-5
+    assert rel_l2(ug[:, fl], uo[:, fl]) < 1e-5
 
 
 @pytest.mark.parametrize("q", [19, 27])
