@@ -520,20 +520,18 @@ void geo_count_kinds(const uint8_t* type, long long N, unsigned long long* out, 
   k_count_kinds<<<unsigned(blocks), 256, 0, s>>>(type, N, out);
 }
 
-// Slot codes per cell (list and NEAR cells; 0 elsewhere), so that the interior kernel's mixed path
-// reads a cell's codes directly from its index rather than through its list position.
+// Slot codes of the list and NEAR cells, by cell index, so that the interior kernel's mixed path reads
+// a cell's codes directly from its index rather than through its list position. Only those entries
+// are written (and read); the others keep whatever they held.
 template <int Q>
 __global__ void k_cell_code(const GeoArgs g, const uint8_t* type, unsigned long long* ccode) {
   const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (n >= g.N) return;
   const uint8_t t = type[n];
-  unsigned long long code = 0;
-  if ((t & (T_LIST | T_NEAR)) && (t & T_KIND) != K_SOLID) {
-    int x, y, z;
-    coords(g, n, x, y, z);
-    code = slot_code<Q>(g, type, x, y, z);
-  }
-  ccode[n] = code;
+  if (!(t & (T_LIST | T_NEAR)) || (t & T_KIND) == K_SOLID) return;
+  int x, y, z;
+  coords(g, n, x, y, z);
+  ccode[n] = slot_code<Q>(g, type, x, y, z);
 }
 
 void geo_cell_code(const GeoArgs& g, const uint8_t* type, unsigned long long* ccode, cudaStream_t s) {

@@ -66,7 +66,7 @@ void geo_list_meta(const GeoArgs&, const uint8_t* type, const long long* lcell, 
                    int* lxyz, unsigned long long* lcode, cudaStream_t);
 // list position of every cell (-1 off the list)
 void geo_list_index(const long long* lcell, int n_list, int* lidx, cudaStream_t);
-// odd-step slot codes of every list and NEAR cell (0 for the other cells)
+// odd-step slot codes of every list and NEAR cell (the other entries are not written)
 void geo_cell_code(const GeoArgs&, const uint8_t* type, unsigned long long* ccode, cudaStream_t);
 // inline (fused-mode) flags per 32-cell x-group; sub-lists of the boundary list (3 per-block counts,
 // then writes at offsets: not-inline, WALL, INFLOW/OUTFLOW); counts of WALL, reference,
