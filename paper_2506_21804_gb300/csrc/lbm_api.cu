@@ -234,6 +234,19 @@ Args make_args(const lbm_ctx* c) {
   a.pairs = pairs_selected(c) ? 1 : 0;
   a.fringe = c->fr_L > 0 ? c->fringe.p : nullptr;
   a.ghost = (c->gh_lo > 0 || c->gh_hi > 0) ? 1 : 0;
+  // HRR one-cell kernel: CTAs of whole warps along x, the x-face planes in columns of their own when
+  // the x faces are not periodic (their cells are inlet, outlet, wall or slip cells)
+  a.xcols = (c->face[0] != F_PERIODIC && c->nx >= 3) ? 1 : 0;
+  {
+    const unsigned t = unsigned(std::min(128, (c->nx + 31) / 32 * 32));
+    a.lc_t = t;
+    a.lc_gx = (unsigned(c->nx) + t - 1) / t;
+    a.lc_gy = (unsigned(c->ny) + t - 1) / t;
+    a.lc_cols = a.xcols ? 2u * a.lc_gy * unsigned(c->nz) : 0u;
+    a.lc_dgx = FastDiv::make(a.lc_gx);
+    a.lc_dny = FastDiv::make(unsigned(c->ny));
+    a.lc_dgy = FastDiv::make(a.lc_gy);
+  }
   a.fr_x0 = c->nx - c->fr_L;
   return a;
 }

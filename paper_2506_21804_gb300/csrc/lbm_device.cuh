@@ -140,6 +140,21 @@ struct Param {
   }
 };
 
+// Division of n < 2^31 by a fixed d >= 1 with a precomputed multiplier (Granlund and Montgomery,
+// "Division by invariant integers using multiplication", 1994): n / d = (umulhi(m, n) + n) >> l with
+// l = ceil(log2 d) and m = floor(2^32 (2^l - d) / d) + 1; the sum stays below 2^32 for n < 2^31.
+struct FastDiv {
+  unsigned m;
+  int l;
+  static FastDiv make(unsigned d) {
+    FastDiv f{0u, 0};
+    while ((1ull << f.l) < d) ++f.l;
+    f.m = unsigned(((1ull << 32) * ((1ull << f.l) - d)) / d + 1);
+    return f;
+  }
+  __device__ __forceinline__ unsigned div(unsigned n) const { return (__umulhi(m, n) + n) >> l; }
+};
+
 struct Args {
   void* f;                 // population deviations, population p of cell m at f + p*stride + m
   long long stride;        // elements between population arrays
@@ -197,6 +212,12 @@ struct Args {
   const void* fringe;
   int fr_x0;               // first plane of the layer
   int ghost;               // slab sub-domain with ghost planes (cells flagged T_GHOST are skipped)
+  // launch shape of the HRR one-cell kernel (cell_at): 1-D CTAs of lc_t threads; when xcols (x faces
+  // not periodic) the first lc_cols CTAs update the planes x = 0 and x = nx - 1 column by column and
+  // the row CTAs after them skip those planes, so no row warp carries a face cell
+  int xcols;
+  unsigned lc_t, lc_gx, lc_gy, lc_cols;
+  FastDiv lc_dgx, lc_dny, lc_dgy;
 };
 
 // ---- AA-pattern slot map ------------------------------------------------------------------------------

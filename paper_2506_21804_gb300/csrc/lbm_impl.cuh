@@ -20,6 +20,8 @@ inline dim3 bulk_grid(const Args& a) {
   return dim3((a.nx + b.x - 1) / b.x, (a.ny + b.y - 1) / b.y, a.nz);
 }
 inline unsigned blocks_for(long long n, int t) { return unsigned((n + t - 1) / t); }
+// Grid of the HRR one-cell kernel (cell_at): the column CTAs of the x-face planes, then the row CTAs.
+inline unsigned cell_grid(const Args& a) { return a.lc_cols + a.lc_gx * unsigned(a.ny) * unsigned(a.nz); }
 // Threads of a 1-D CTA lying in one x-row that holds `groups` cell groups (pairs or quads) per row:
 // whole warps, at most BULK_THREADS.
 inline unsigned row_threads(int groups) {
@@ -88,8 +90,8 @@ struct Impl {
           return;
         }
       }
-      if (odd) k_bulk_hrr<Q, S, true><<<bulk_grid(a), bulk_block(a), 0, s>>>(a);
-      else k_bulk_hrr<Q, S, false><<<bulk_grid(a), bulk_block(a), 0, s>>>(a);
+      if (odd) k_bulk_hrr<Q, S, true><<<cell_grid(a), a.lc_t, 0, s>>>(a);
+      else k_bulk_hrr<Q, S, false><<<cell_grid(a), a.lc_t, 0, s>>>(a);
       return;
     }
     const TmaLayout L = tma_layout(a);
