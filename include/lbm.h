@@ -30,7 +30,9 @@
  * lbm_create) and frees them in lbm_destroy. Caller buffers are never retained after a call returns.
  * Array arguments may be host or device pointers (detected with cudaPointerGetAttributes); a call
  * that reads or writes host memory synchronises the context's stream before it returns, a call on
- * device memory is ordered on that stream.
+ * device memory is ordered on that stream. Page-locked (pinned) host fields given to
+ * lbm_init_equilibrium and lbm_moments are read and written by the kernels in place over the
+ * CPU-GPU link; other host memory is staged through device memory.
  *
  * Errors. Every int-returning call returns LBM_OK or an error code and leaves a message for
  * lbm_last_error() (thread-local). Invalid sizes, codes or pointers give LBM_EINVAL and change

@@ -443,8 +443,10 @@ __device__ __forceinline__ void list_cell_inline(const Args& a, S* f, int x, int
 // list cells, where the extra path costs little divergence). Threads map to (x, y, z).
 //
 // Occupancy target (CTAs of 128 threads per SM): D3Q19 10 on even steps (<= 51 registers) and 8 on
-// odd steps (<= 64), D3Q27 8 and 6; the register cap falls on the rarely taken list-cell path. The
-// FP64 (reference) form is left unconstrained.
+// odd steps (<= 64), D3Q27 8 and 7 (measured on the 512x512x256 canopy with every odd-step warp on the
+// mixed path: D3Q27 odd 5, 6, 7, 8 gave 24.0, 24.8, 25.3, 25.0 GLUPS; D3Q19 odd 7, 8, 10 gave 34.4,
+// 35.1, 34.0); the register cap falls on the rarely taken list-cell path. The FP64 (reference) form
+// is left unconstrained.
 #ifndef LBM_BULK_MINB19_EVEN
 #define LBM_BULK_MINB19_EVEN 10
 #endif
@@ -455,7 +457,7 @@ __device__ __forceinline__ void list_cell_inline(const Args& a, S* f, int x, int
 #define LBM_BULK_MINB27_EVEN 8
 #endif
 #ifndef LBM_BULK_MINB27_ODD
-#define LBM_BULK_MINB27_ODD 6
+#define LBM_BULK_MINB27_ODD 7
 #endif
 template <int Q, class S, bool ODD> constexpr int bulk_min_blocks() {
   return sizeof(S) == 8 ? 1
